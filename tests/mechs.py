@@ -1,0 +1,45 @@
+"""Tiny hand-written mechanisms for the pin tests (JSON-able dicts)."""
+import json
+
+
+def mech(species, reactions, phase=None, sections=0, atoms=None):
+    d = {"name": "test",
+         "species": [{"name": s, "atoms": (atoms or {}).get(s, 1)} for s in species],
+         "reactions": reactions}
+    if phase is not None:
+        d["phases"] = {"aqueous": [{"name": p, "atoms": 1} for p in phase]}
+        d["aerosol"] = {"phase": "aqueous", "sections": sections}
+    return json.dumps(d)
+
+
+def arrhenius(reactants, products, A, B=0.0, C=0.0, D=300.0, E=0.0):
+    return {"type": "ARRHENIUS", "reactants": reactants, "products": products,
+            "A": A, "B": B, "C": C, "D": D, "E": E}
+
+
+def troe(reactants, products, k0_A, kinf_A, k0_B=0.0, k0_C=0.0, kinf_B=0.0, kinf_C=0.0, Fc=0.6, N=1.0):
+    return {"type": "TROE", "reactants": reactants, "products": products,
+            "k0_A": k0_A, "k0_B": k0_B, "k0_C": k0_C, "kinf_A": kinf_A, "kinf_B": kinf_B,
+            "kinf_C": kinf_C, "Fc": Fc, "N": N}
+
+
+def photolysis(x, products, value=1e-3):
+    return {"type": "PHOTOLYSIS", "reactants": {x: 1}, "products": products, "value": value}
+
+
+def emission(x, value=1e-3):
+    return {"type": "EMISSION", "species": x, "value": value}
+
+
+def loss(x, value=1e-3):
+    return {"type": "FIRST_ORDER_LOSS", "species": x, "value": value}
+
+
+def henry(gas, aq, H298, C_H=0.0, alpha=0.5, Dg=1e-5, MW=0.05):
+    return {"type": "HL_PHASE_TRANSFER", "gas": gas, "aqueous": aq, "H298": H298, "C_H": C_H,
+            "alpha": alpha, "Dg": Dg, "MW": MW}
+
+
+def aqrev(reactants, products, A, kr, C=0.0):
+    return {"type": "AQUEOUS_REVERSIBLE", "reactants": reactants, "products": products,
+            "A": A, "C": C, "kr": kr}

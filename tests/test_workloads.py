@@ -1,0 +1,79 @@
+"""The seeded input generator (no GPU)."""
+import json
+
+import numpy as np
+
+from paper_2111_07436_gb300 import workloads as w
+
+
+def test_deterministic():
+    for k in (1, 2, 3):
+        a, b = w.workload(k), w.workload(k)
+        assert a.json() == b.json()
+        ya, ea = a.inputs(8)
+        yb, eb = b.inputs(8)
+        assert np.array_equal(ya, yb) and np.array_equal(ea, eb)
+
+
+def test_large_gas_mechanism_shape():
+    m = w.large_gas_mechanism()
+    types = [r["type"] for r in m["reactions"]]
+    assert len(m["species"]) == 72 and len(types) == 186
+    assert (types.count("ARRHENIUS"), types.count("TROE"), types.count("PHOTOLYSIS"),
+            types.count("EMISSION"), types.count("FIRST_ORDER_LOSS")) == (112, 28, 28, 9, 9)
+    occ = {s["name"]: 0 for s in m["species"]}
+    for r in m["reactions"]:
+        names = set(r.get("reactants", {})) | set(r.get("products", {}))
+        if "species" in r:
+            names.add(r["species"])
+        for s in names:
+            occ[s] += 1
+    assert max(occ.values()) <= 12
+
+
+def test_chemistry_conserves_atoms():
+    for mj in (w.small_gas_mechanism(), w.multiphase_mechanism()):
+        lay = w.layout(mj)
+        atoms = dict(zip(lay.species, lay.atoms))
+        phase_atoms = {p["name"]: p["atoms"] for p in mj.get("phases", {}).get("aqueous", [])}
+        for r in mj["reactions"]:
+            t = r["type"]
+            if t in ("ARRHENIUS", "TROE", "PHOTOLYSIS"):
+                lhs = sum(atoms[s] * c for s, c in r["reactants"].items())
+                rhs = sum(atoms[s] * c for s, c in r["products"].items())
+                assert abs(lhs - rhs) < 1e-12
+            elif t == "AQUEOUS_REVERSIBLE":
+                lhs = sum(phase_atoms[s] * c for s, c in r["reactants"].items())
+                rhs = sum(phase_atoms[s] * c for s, c in r["products"].items())
+                assert lhs == rhs
+            elif t == "HL_PHASE_TRANSFER":
+                assert atoms[r["gas"]] == phase_atoms[r["aqueous"]]
+
+
+def test_multiphase_sizes_and_env():
+    mj = w.multiphase_mechanism()
+    lay = w.layout(mj)
+    assert len(lay.species) == 232
+    y, env = w.cells(mj, 16, seed=5)
+    assert env.shape == (16, len(lay.env)) and (y[:, 72:] == 0).all()
+    base = 2 + len(lay.runtime_defaults)
+    r = env[:, base::3]
+    np.testing.assert_allclose(r[0], w.SECTION_RADII)
+    N, L = env[:, base + 1::3], env[:, base + 2::3]
+    np.testing.assert_allclose(L, N * 4.0 / 3.0 * np.pi * r ** 3)
+    assert ((N >= 1e7) & (N <= 1e10)).all()
+
+
+def test_night_and_cloud_options():
+    mj = w.multiphase_mechanism()
+    lay = w.layout(mj)
+    y, env = w.cells(mj, 2000, seed=6, night_fraction=0.5, cloud_fraction=0.1)
+    jcols = [2 + k for k, kind in enumerate(lay.runtime_kind) if kind == "PHOTOLYSIS"]
+    night = (env[:, jcols] == 0).all(axis=1)
+    assert 0.4 < night.mean() < 0.7  # half forced dark plus SZA > 90 deg
+    base = 2 + len(lay.runtime_defaults)
+    lwc = env[:, base + 2::3].sum(axis=1)
+    cloudy = lwc > 0
+    assert 0.07 < cloudy.mean() < 0.13
+    assert ((lwc[cloudy] >= 1e-7) & (lwc[cloudy] <= 1e-6 + 1e-18)).all()
+    json.dumps(mj)
