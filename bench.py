@@ -1,0 +1,279 @@
+#!/usr/bin/env python
+"""Benchmark of the batched chemistry solve: cell-steps/s at rtol 1e-4.
+
+One step = one call of the whole hot path (rate constants, BDF + Newton +
+sparse LU for every cell over one outer step) on the full workload, with the
+inputs resident in HBM; a fresh copy of the initial state is taken at the
+start of every step and L2 is flushed (256 MB write) between timed steps.
+Default workload: 16384 cells of the 72-species / 186-process gas mechanism,
+one 180 s step.  Prints one JSON line (rank 0).
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--workload gas72]
+    python bench.py --impl reference   # the FP64 CPU oracle on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {"small": 1, "gas72": 2, "multiphase232": 3}
+FP64_PEAK_NOMINAL_GFLOPS = 1250.0  # GB300 dense FP64, nominal
+
+
+def args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="camp", choices=["camp", "reference"])
+    p.add_argument("--workload", default="gas72", choices=sorted(WORKLOADS))
+    p.add_argument("--cells", type=int, default=0, help="override the workload's cell count")
+    p.add_argument("--variant", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--cpb", type=int, default=0, help="cells per block (0: library default)")
+    p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        rows = [r for r in self.rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ----------------------------------------------------------------- CPU oracle
+def oracle_rate(wl, seconds, rank_seed=0):
+    """Oracle cell-steps/s on this host's cores over a bounded sample of the
+    workload's cells (about `seconds` of work)."""
+    import numpy as np
+    import oracle
+    om = oracle.Mechanism(wl.json())
+    y0, env = wl.inputs()
+    threads = os.cpu_count() or 1
+    probe = min(wl.n_cells, 8 * threads)
+    t = time.perf_counter()
+    om.solve(y0[:probe], env[:probe], wl.dt, wl.rtol, wl.atol, threads=threads)
+    per_cell = (time.perf_counter() - t) / probe
+    n = int(min(wl.n_cells, max(probe, seconds / max(per_cell, 1e-9))))
+    idx = np.random.default_rng(rank_seed + 17).choice(wl.n_cells, n, replace=False)
+    t = time.perf_counter()
+    _, st, _ = om.solve(y0[idx], env[idx], wl.dt, wl.rtol, wl.atol, threads=threads)
+    dt = time.perf_counter() - t
+    return {"value": n * wl.n_outer / dt, "unit": "cell-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} of {wl.n_cells} cells (seeded random), {wl.n_outer} outer step(s), "
+                      f"{threads} threads, {dt:.1f} s", "ok_cells": int((st == 0).sum())}
+
+
+# ----------------------------------------------------------------- main
+def main():
+    a = args()
+    from paper_2111_07436_gb300 import workloads as w
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = w.workload(WORKLOADS[a.workload])
+    if a.cells:
+        wl.n_cells = a.cells
+    metric = f"cell-steps/s at rtol {wl.rtol:g}"
+    config = {"workload": f"{wl.mech['name']} x {wl.n_cells} cells, dt {wl.dt:g} s",
+              "cells_per_gpu": wl.n_cells, "species": None, "dt_s": wl.dt, "rtol": wl.rtol,
+              "atol_ppb": wl.atol, "parallelism": f"replicas x{a.gpus} (cells split, no collective)",
+              "l2": "flushed between timed steps (256 MB write)"}
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        cpu = oracle_rate(wl, a.cpu_seconds)
+        steps_t = []
+        for _ in range(a.warmup + a.steps):
+            r = oracle_rate(wl, a.cpu_seconds / 2)
+            steps_t.append(r["value"])
+        v = statistics.mean(steps_t[a.warmup:])
+        cpu["value"] = v
+        print(json.dumps({"impl": "reference", "metric": metric, "value": v, "unit": "cell-steps/s",
+                          "n_gpus": 0, "steps": a.steps, "warmup": a.warmup,
+                          "ms_per_step": 1e3 * wl.n_cells * wl.n_outer / v, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": config, "cpu_baseline": cpu,
+                          "e2e": {"value": v, "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    import numpy as np
+    import torch
+    from paper_2111_07436_gb300 import build, camp
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    gm = camp.Mechanism(wl.json())
+    config["species"] = gm.n
+    wl.cell_seed += 1000 * rank  # each replica solves its own cells (weak scaling)
+    y0, env = wl.inputs()
+    C = wl.n_cells
+    y0_d = torch.tensor(y0, device=dev)
+    env_d = torch.tensor(env, device=dev)
+    state = torch.empty_like(y0_d)
+    status = torch.empty(C, dtype=torch.int32, device=dev)
+    atol = torch.full((1,), wl.atol, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    variant = camp.VARIANT_MIXED if a.variant == "mixed" else camp.VARIANT_FP64
+    persistent = variant == camp.VARIANT_MIXED
+
+    def run(var, pers, K, W, stats=None):
+        times = []
+        for i in range(W + K):
+            flush.zero_()
+            state.copy_(y0_d)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gm.solve(state, env_d, wl.dt, wl.rtol, atol, status=status, variant=var, persistent=pers,
+                     cells_per_block=a.cpb, stats=stats if i == 0 else None, stream=stream)
+            e1.record(stream)
+            if i >= W:
+                times.append((e0, e1))
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) for e0, e1 in times]
+
+    # algorithmic work from one instrumented (untimed) solve
+    stats = torch.zeros((C, camp.NSTATS), dtype=torch.int32, device=dev)
+    run(variant, persistent, 0, 1, stats=stats)
+    st = stats.cpu().numpy().astype(np.float64)
+    ok = int((status.cpu().numpy() == 0).sum())
+    inf = gm.info
+    n = gm.n
+    steps, newton, jac, ordsum = st[:, 0].sum(), st[:, 1].sum(), st[:, 2].sum(), st[:, 4].sum()
+    qbar = ordsum / max(steps, 1)
+    f_evals = newton + 2 * C  # Newton iterations plus the two of the starting step
+    fp64 = f_evals * inf.flops_forcing + newton * 8 * n + steps * (qbar * (qbar + 1) / 2 + 2 * (qbar + 1) + 8) * n
+    lu = jac * (inf.flops_jacobian + inf.flops_factor) + newton * inf.flops_solve
+    if variant == camp.VARIANT_FP64:
+        fp64 += lu
+
+    # timed region
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        times = run(variant, persistent, a.steps, a.warmup)
+    if dist:
+        dist.barrier()
+    total = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(total, op=dist.ReduceOp.MAX)
+    ms = total.item() / a.steps
+    value = world * C * wl.n_outer / (ms / 1e3)
+
+    # plain FP64 form, one launch per outer step, for the mixed-vs-plain ratio
+    plain = None
+    if not a.no_plain and variant == camp.VARIANT_MIXED:
+        pt = run(camp.VARIANT_FP64, False, max(1, a.steps // 2), 1)
+        pms = sum(pt) / len(pt)
+        plain = {"value": C * wl.n_outer / (pms / 1e3), "ms_per_step": pms, "form": "fp64 static grid"}
+
+    # end to end through the host-pointer C-ABI call, pinned host buffers
+    y_h = torch.empty((C, n), dtype=torch.float64).pin_memory()
+    e_h = torch.tensor(env, dtype=torch.float64).pin_memory()
+    st_h = None
+    e2e_t = []
+    for i in range(a.warmup + a.steps):
+        y_h.copy_(torch.from_numpy(y0))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st_h = gm.solve_host(y_h, e_h, wl.dt, wl.rtol, wl.atol, variant=variant, persistent=persistent,
+                             cells_per_block=a.cpb)
+        if i >= a.warmup:
+            e2e_t.append(time.perf_counter() - t)
+    e2e_s = torch.tensor([sum(e2e_t)], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * C * wl.n_outer * a.steps / e2e_s.item(), "unit": "cell-steps/s",
+           "h2d_bytes_per_step": int(y_h.numel() * 8 + e_h.numel() * 8 + 8),
+           "d2h_bytes_per_step": int(y_h.numel() * 8 + C * 4),
+           "ok_cells": int((st_h == 0).sum())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu = oracle_rate(wl, a.cpu_seconds)
+
+    if rank != 0:
+        return
+    achieved = fp64 / (ms / 1e3) / 1e9
+    roof = {"bound": "alu", "unit": "GFLOP/s (fp64)", "achieved": achieved,
+            "peak": FP64_PEAK_NOMINAL_GFLOPS, "peak_source": "nominal GB300 dense FP64",
+            "frac": achieved / FP64_PEAK_NOMINAL_GFLOPS, "traffic": None,
+            "kernel": "k_solve", "fp64_flops_per_launch": fp64, "lu_flops_per_launch": lu,
+            "lu_dtype": "f32" if variant == camp.VARIANT_MIXED else "f64"}
+    hbm = (y0.nbytes * 2 + env.nbytes + C * 4) / (ms / 1e3) / 1e9
+    out = {"metric": metric, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64 state / f32 J+LU" if variant == camp.VARIANT_MIXED else "f64",
+           "data": "synthetic (seeded generator shaped like the paper's gas mechanism)",
+           "config": config, "form": f"{a.variant} {'persistent' if persistent else 'static'}",
+           "ok_cells": ok, "gpu_launches": a.steps,
+           "work": {"bdf_steps": steps, "newton_iters": newton, "lu_setups": jac, "mean_order": qbar,
+                    "steps_per_cell": steps / C},
+           "plain_fp64": plain, "mixed_over_plain": (value / world / plain["value"]) if plain else None,
+           "roofline": roof, "hbm_io_gbs": hbm, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * camp.h -- C ABI of libcamp.so: batched integration of CAMP's coupled stiff
+ * multiphase chemistry ODE system for many independent grid cells on one GPU.
+ *
+ * Paper: M. Dawson et al., "Chemistry Across Multiple Phases (CAMP) version
+ * 1.0", arXiv 2111.07436.  The calls follow the paper's statement of the
+ * interface (Sect. 2.1 and 2.4.2): a core object is created once per
+ * mechanism from its JSON description; the host then passes, per time step,
+ * the state (species concentrations), the environment (temperature,
+ * pressure, externally computed rates such as photolysis, aerosol state) and
+ * the step length, and gets the new state back.
+ *
+ * Conventions
+ *   - Return values: CAMP_OK (0) or a negative CAMP_E_* code; a message for
+ *     the calling thread is available from camp_last_error().
+ *   - Pointers documented as "device" must be CUDA device (or managed)
+ *     memory on the device the mechanism was loaded on; "host" pointers are
+ *     ordinary host memory.  The caller owns every array it passes.  The
+ *     library owns camp_mech and camp_server handles until the matching
+ *     free/destroy call.
+ *   - Arrays are row-major with the cell index outermost:
+ *       state  [n_cells][n_species]  ppb-equivalent of air, declaration order
+ *                                   (gas species, then section b = 0.. of
+ *                                   every aerosol-phase species);
+ *       env    [n_cells][n_env]      T (K), P (Pa), one entry per
+ *                                   PHOTOLYSIS (s^-1) / EMISSION (ppb s^-1)
+ *                                   / FIRST_ORDER_LOSS (s^-1) process in
+ *                                   declaration order, then per section:
+ *                                   radius (m), number (m^-3), water volume
+ *                                   fraction (m^3 m^-3);
+ *       status [n_cells]             per-cell status (CAMP_CELL_*).
+ *   - Calls taking a `stream` are asynchronous on that cudaStream_t (NULL =
+ *     legacy default stream); they validate arguments on the host and return
+ *     CAMP_E_CUDA if a launch fails.
+ */
+#ifndef CAMP_H
+#define CAMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define CAMP_OK 0
+#define CAMP_E_INVAL (-1)       /* bad argument */
+#define CAMP_E_PARSE (-2)       /* malformed mechanism description */
+#define CAMP_E_NOMEM (-3)       /* device or host allocation failed */
+#define CAMP_E_CUDA (-4)        /* CUDA runtime error */
+#define CAMP_E_UNSUPPORTED (-5) /* mechanism too large for the device kernels */
+#define CAMP_E_BUDGET (-6)      /* request larger than the server's memory budget */
+#define CAMP_E_TIMEOUT (-7)     /* bounded wait expired */
+
+/* ---- per-cell status ---------------------------------------------------- */
+#define CAMP_CELL_OK 0          /* integrated to dt */
+#define CAMP_CELL_MAXSTEPS 1    /* max_steps internal steps taken before dt */
+#define CAMP_CELL_ERRTEST 2     /* repeated error-test failures or h < h_min */
+#define CAMP_CELL_NEWTON 3      /* repeated Newton failures */
+#define CAMP_CELL_SINGULAR 4    /* tiny or non-finite LU pivot, repeatedly */
+#define CAMP_CELL_NONFINITE 5   /* non-finite input or result */
+/* A cell with status != 0 keeps its input state. */
+
+typedef struct camp_mech camp_mech;
+
+/* Sizes of a compiled mechanism. */
+typedef struct {
+    int32_t n_species;      /* state entries per cell */
+    int32_t n_rxn;          /* process instances (section processes once per section) */
+    int32_t n_env;          /* env entries per cell */
+    int32_t n_sections;     /* aerosol sections (instances of the aerosol phase) */
+    int32_t nnz_jac;        /* structural non-zeros of df/dy, diagonal included */
+    int32_t nnz_lu;         /* non-zeros of L+U after fill */
+    int32_t rxn_map_len;    /* entries of the process -> Jacobian map */
+    int32_t dense_block;    /* order of the dense trailing block of the LU (0: none) */
+    int32_t lu_storage;     /* LU values stored per cell on the device */
+    int32_t smem_per_cell_mixed; /* shared-memory bytes per cell, FP32 J/LU */
+    int32_t smem_per_cell_fp64;  /* shared-memory bytes per cell, FP64 J/LU */
+    int64_t factor_updates; /* multiply-adds one device LU factorisation executes
+                               (sparse part plus the dense block) */
+    /* algorithmic floating-point operations of the method's steps, from
+       the symbolic structure (independent of how the device stores it) */
+    int64_t flops_forcing;  /* one f(y) */
+    int64_t flops_jacobian; /* one assembly of I - gamma J */
+    int64_t flops_factor;   /* one sparse LU factorisation */
+    int64_t flops_solve;    /* one forward + backward substitution */
+} camp_mech_info;
+
+/*
+ * Compile a mechanism (paper Sect. 2.3: JSON configuration, no recompilation
+ * of the library; Sect. 2.2: processes, aerosol phases and their instances;
+ * Table 1: get_used_jacobian_elements / update_ids are done here, once).
+ * json/len: UTF-8 text, not necessarily NUL-terminated.  On success *out is
+ * a new handle whose tables live on the current CUDA device.  On failure
+ * *out is NULL, a message is copied to err (if errlen > 0) and
+ * CAMP_E_PARSE / CAMP_E_UNSUPPORTED / CAMP_E_CUDA is returned.
+ * Schema: see paper_2111_07436_gb300/workloads.py (module docstring).
+ */
+int camp_mech_load(const char *json, size_t len, camp_mech **out, char *err, size_t errlen);
+
+/* Compile only, on the host: the handle serves camp_mech_info_get,
+ * camp_mech_species_index and camp_mech_structure (no GPU needed); solving
+ * with it returns CAMP_E_INVAL.  Same arguments and errors as
+ * camp_mech_load. */
+int camp_mech_compile(const char *json, size_t len, camp_mech **out, char *err, size_t errlen);
+
+/* Release a mechanism and its device tables.  NULL is ignored. */
+void camp_mech_free(camp_mech *m);
+
+/* Fill *out with the mechanism's sizes (host struct). */
+int camp_mech_info_get(const camp_mech *m, camp_mech_info *out);
+
+/* State index of a species ("O3", or "bin3.a7" for section 3's instance of
+ * phase species a7); -1 if unknown. */
+int camp_mech_species_index(const camp_mech *m, const char *name);
+
+/*
+ * Integer structure of the mechanism, for bit-exact checks (host arrays the
+ * caller allocates with the sizes from camp_mech_info; any may be NULL):
+ *   rowptr [n+1], colidx [nnz_jac]: CSR pattern of df/dy in declaration
+ *       order, columns sorted: the diagonal plus, for every process k, the
+ *       rows R_k u P_k times the species D_k its rate depends on
+ *       (D_k = R_k, or R_k u P_k for reversible processes);
+ *   rxn_map [rxn_map_len]: for every process k, every j in D_k, every i in
+ *       R_k u P_k (declaration order, reactants first, each species once):
+ *       the CSR position of (i, j);
+ *   perm [n]: elimination order (position p holds species perm[p]): exact
+ *       minimum degree on pattern u pattern^T, ties to the smallest index;
+ *   lu_rowptr [n+1], lu_colidx [nnz_lu]: fill pattern of the permuted matrix
+ *       under elimination without pivoting;
+ *   level_fwd [n], level_bwd [n]: dependency levels of the LU rows.
+ */
+int camp_mech_structure(const camp_mech *m, int32_t *rowptr, int32_t *colidx, int32_t *rxn_map,
+                        int32_t *perm, int32_t *lu_rowptr, int32_t *lu_colidx,
+                        int32_t *level_fwd, int32_t *level_bwd);
+
+/* ---- the solve ---------------------------------------------------------- */
+#define CAMP_VARIANT_MIXED 0   /* FP32 Jacobian assembly and LU; FP64 state,
+                                  residual, Nordsieck history, error test */
+#define CAMP_VARIANT_FP64 1    /* everything FP64 */
+#define CAMP_NSTATS 5
+
+typedef struct {
+    int32_t variant;         /* CAMP_VARIANT_* (default MIXED) */
+    int32_t persistent;      /* 1: one resident grid takes cells from a work
+                                counter; 0: one group of lanes per cell, static
+                                grid (default 1 for MIXED, 0 for FP64) */
+    int32_t max_steps;       /* internal steps per cell (default 10000) */
+    int32_t cells_per_block; /* 0: library default */
+    double hmin_frac;        /* minimum step = hmin_frac * dt (default 1e-10) */
+    int32_t *stats;          /* optional device [n_cells][CAMP_NSTATS]: steps,
+                                Newton iterations, Jacobian/LU setups,
+                                error-test failures, sum of the BDF order
+                                over accepted steps */
+    void *workspace;         /* optional device scratch of
+                                camp_workspace_bytes() bytes; NULL: the
+                                mechanism's own (then calls on one mechanism
+                                must not overlap on the GPU) */
+} camp_solve_opts;
+
+/* Fill *o with the defaults for `variant`. */
+void camp_solve_opts_default(camp_solve_opts *o, int variant);
+
+/* Scratch bytes one concurrent camp_solve needs (the work counter). */
+size_t camp_workspace_bytes(void);
+
+/*
+ * Integrate every cell over [0, dt] with the variable-order BDF + Newton +
+ * sparse LU method (paper Sect. 2.4.1, CVODE's method class; Sect. 2.4.2:
+ * f and its Jacobian assembled from per-process contributions), each cell an
+ * independent cold start.
+ *   state  device [n_cells][n_species], in/out;
+ *   env    device [n_cells][n_env];
+ *   dt > 0 (s), rtol > 0;
+ *   atol   device [atol_len], atol_len = 1 (all species) or n_species, > 0;
+ *   status device [n_cells], out;
+ *   opts   may be NULL (defaults for CAMP_VARIANT_MIXED).
+ * n_cells = 0 is a no-op.  Asynchronous on `stream` (a cudaStream_t).
+ */
+int camp_solve(const camp_mech *m, int64_t n_cells, double *state, const double *env, double dt,
+               double rtol, const double *atol, int32_t atol_len, int32_t *status,
+               const camp_solve_opts *opts, void *stream);
+
+/*
+ * Same as camp_solve with HOST arrays: copies state/env/atol to the device,
+ * solves and copies state/status back, synchronously, on `stream`.  Device
+ * staging buffers are kept per mechanism between calls (grown as needed);
+ * concurrent camp_solve_host calls on one mechanism are serialised.  Pinned
+ * host memory gives asynchronous DMA copies; pageable memory works too.
+ */
+int camp_solve_host(const camp_mech *m, int64_t n_cells, double *state, const double *env,
+                    double dt, double rtol, const double *atol, int32_t atol_len, int32_t *status,
+                    const camp_solve_opts *opts, void *stream);
+
+/* ---- single steps of the method, for testing ----------------------------- */
+/* Rate constants (paper Table 2) in ppb units: device env [n_cells][n_env]
+ * -> kf, kr device [n_cells][n_rxn] (process order).  The rate of process k
+ * is kf_k prod_{reactants} y^s - kr_k prod_{products} y^nu. */
+int camp_rate_constants(const camp_mech *m, int64_t n_cells, const double *env, double *kf,
+                        double *kr, void *stream);
+
+/* Forcing f(y) = sum_k (dy/dt)_k (paper Sect. 2.4.2): device state, env ->
+ * device f [n_cells][n_species], FP64. */
+int camp_forcing(const camp_mech *m, int64_t n_cells, const double *state, const double *env,
+                 double *f, void *stream);
+
+/* Jacobian df_i/dy_j = sum_k (df_i/dy_j)_k (paper Sect. 2.4.2) at the CSR
+ * non-zeros of camp_mech_structure: device jac [n_cells][nnz_jac], values
+ * computed in the variant's assembly precision. */
+int camp_jacobian(const camp_mech *m, int64_t n_cells, const double *state, const double *env,
+                  double *jac, int32_t variant, void *stream);
+
+/* Solve (I - gamma J(y)) x = b per cell with the device's static-pivot LU in
+ * the variant's precision: device b, x [n_cells][n_species]; device status
+ * [n_cells] = CAMP_CELL_SINGULAR on a tiny pivot (x unwritten), else 0. */
+int camp_lu_solve(const camp_mech *m, int64_t n_cells, const double *state, const double *env,
+                  double gamma, const double *b, double *x, int32_t *status, int32_t variant,
+                  void *stream);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char *camp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAMP_H */

@@ -1,0 +1,253 @@
+"""Thin Python binding of libcamp.so (C ABI in include/camp.h).
+
+Argument marshalling only: every step of the solve runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcamp.so")
+
+VARIANT_MIXED = 0
+VARIANT_FP64 = 1
+NSTATS = 5  # steps, Newton iterations, J/LU setups, error-test failures, sum of orders
+
+CELL_STATUS = {0: "ok", 1: "max_steps", 2: "error_test", 3: "newton", 4: "singular", 5: "nonfinite"}
+
+_lib = None
+
+
+class CampError(RuntimeError):
+    pass
+
+
+class MechInfo(ctypes.Structure):
+    _fields_ = [("n_species", ctypes.c_int32), ("n_rxn", ctypes.c_int32),
+                ("n_env", ctypes.c_int32), ("n_sections", ctypes.c_int32),
+                ("nnz_jac", ctypes.c_int32), ("nnz_lu", ctypes.c_int32),
+                ("rxn_map_len", ctypes.c_int32), ("dense_block", ctypes.c_int32),
+                ("lu_storage", ctypes.c_int32), ("smem_per_cell_mixed", ctypes.c_int32),
+                ("smem_per_cell_fp64", ctypes.c_int32), ("factor_updates", ctypes.c_int64),
+                ("flops_forcing", ctypes.c_int64), ("flops_jacobian", ctypes.c_int64),
+                ("flops_factor", ctypes.c_int64), ("flops_solve", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("max_steps", ctypes.c_int32), ("cells_per_block", ctypes.c_int32),
+                ("hmin_frac", ctypes.c_double), ("stats", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p)]
+
+
+EXPORTS = ["camp_mech_load", "camp_mech_compile", "camp_mech_free", "camp_mech_info_get", "camp_mech_species_index",
+           "camp_mech_structure", "camp_solve_opts_default", "camp_workspace_bytes", "camp_solve",
+           "camp_solve_host", "camp_rate_constants", "camp_forcing", "camp_jacobian",
+           "camp_lu_solve", "camp_last_error"]
+
+
+def lib():
+    """Load libcamp.so (raises CampError if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise CampError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    L.camp_mech_load.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(vp),
+                                 ctypes.c_char_p, ctypes.c_size_t]
+    L.camp_mech_load.restype = ctypes.c_int
+    L.camp_mech_compile.argtypes = L.camp_mech_load.argtypes
+    L.camp_mech_compile.restype = ctypes.c_int
+    L.camp_mech_free.argtypes = [vp]
+    L.camp_mech_free.restype = None
+    L.camp_mech_info_get.argtypes = [vp, ctypes.POINTER(MechInfo)]
+    L.camp_mech_species_index.argtypes = [vp, ctypes.c_char_p]
+    L.camp_mech_structure.argtypes = [vp] + [vp] * 8
+    L.camp_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts), ctypes.c_int]
+    L.camp_solve_opts_default.restype = None
+    L.camp_workspace_bytes.restype = ctypes.c_size_t
+    L.camp_solve.argtypes = [vp, i64, vp, vp, dbl, dbl, vp, i32, vp, ctypes.POINTER(SolveOpts), vp]
+    L.camp_solve_host.argtypes = L.camp_solve.argtypes
+    L.camp_rate_constants.argtypes = [vp, i64, vp, vp, vp, vp]
+    L.camp_forcing.argtypes = [vp, i64, vp, vp, vp, vp]
+    L.camp_jacobian.argtypes = [vp, i64, vp, vp, vp, i32, vp]
+    L.camp_lu_solve.argtypes = [vp, i64, vp, vp, dbl, vp, vp, vp, i32, vp]
+    L.camp_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise CampError(f"camp error {rc}: {lib().camp_last_error().decode()}")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_f64(t, shape, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise CampError(f"{name} must be a contiguous float64 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise CampError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+class Mechanism:
+    """A compiled mechanism whose tables live on the current CUDA device
+    (device=False: compiled on the host only, for info and structure)."""
+
+    def __init__(self, json_text: str, device: bool = True):
+        L = lib()
+        b = json_text.encode() if isinstance(json_text, str) else json_text
+        h = ctypes.c_void_p()
+        err = ctypes.create_string_buffer(1024)
+        load = L.camp_mech_load if device else L.camp_mech_compile
+        rc = load(b, len(b), ctypes.byref(h), err, len(err))
+        if rc != 0:
+            raise CampError(f"mechanism load failed ({rc}): {err.value.decode()}")
+        self._h = h
+        self.info = MechInfo()
+        _check(L.camp_mech_info_get(self._h, ctypes.byref(self.info)))
+        self.n = self.info.n_species
+        self.n_env = self.info.n_env
+        self.n_rxn = self.info.n_rxn
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.camp_mech_free(self._h)
+            self._h = None
+
+    def species_index(self, name):
+        return lib().camp_mech_species_index(self._h, name.encode())
+
+    def structure(self):
+        inf = self.info
+        n = self.n
+        arrs = {"rowptr": n + 1, "colidx": inf.nnz_jac, "rxn_map": inf.rxn_map_len, "perm": n,
+                "lu_rowptr": n + 1, "lu_colidx": inf.nnz_lu, "level_fwd": n, "level_bwd": n}
+        out = {k: np.zeros(v, dtype=np.int32) for k, v in arrs.items()}
+        _check(lib().camp_mech_structure(self._h, *[ctypes.c_void_p(out[k].ctypes.data) for k in arrs]))
+        return out
+
+    def _atol(self, atol, device):
+        import torch
+        a = torch.as_tensor(np.atleast_1d(np.asarray(atol, dtype=np.float64)), device=device)
+        if a.numel() not in (1, self.n):
+            raise CampError("atol must be a scalar or one value per species")
+        return a.contiguous()
+
+    def solve(self, state, env, dt, rtol, atol, status=None, variant=VARIANT_MIXED,
+              persistent=None, max_steps=10000, cells_per_block=0, stats=None, workspace=None,
+              stream=None):
+        """Integrate every cell over [0, dt] in place (asynchronous on `stream`).
+
+        state [C, n] / env [C, n_env]: float64 CUDA tensors; status: int32
+        CUDA tensor [C] (allocated if None); stats: optional int32 [C, NSTATS].
+        Returns status.
+        """
+        import torch
+        C = state.shape[0]
+        _dev_f64(state, (C, self.n), "state")
+        _dev_f64(env, (C, self.n_env), "env")
+        if status is None:
+            status = torch.empty(C, dtype=torch.int32, device=state.device)
+        a = atol if isinstance(atol, torch.Tensor) else self._atol(atol, state.device)
+        o = self.opts(variant, persistent, max_steps, cells_per_block, stats, workspace)
+        _check(lib().camp_solve(self._h, C, _ptr(state), _ptr(env), float(dt), float(rtol), _ptr(a),
+                                a.numel(), _ptr(status), ctypes.byref(o), _stream(stream)))
+        return status
+
+    def opts(self, variant=VARIANT_MIXED, persistent=None, max_steps=10000, cells_per_block=0,
+             stats=None, workspace=None):
+        o = SolveOpts()
+        lib().camp_solve_opts_default(ctypes.byref(o), variant)
+        if persistent is not None:
+            o.persistent = int(persistent)
+        o.max_steps = max_steps
+        o.cells_per_block = cells_per_block
+        o.stats = stats.data_ptr() if stats is not None else None
+        o.workspace = workspace.data_ptr() if workspace is not None else None
+        return o
+
+    def solve_host(self, state, env, dt, rtol, atol, variant=VARIANT_MIXED, persistent=None,
+                   max_steps=10000, cells_per_block=0, stats=None, stream=None):
+        """Host arrays (numpy float64, C-contiguous; pinned torch tensors also
+        work): state is updated in place; returns the status array."""
+        st = state if isinstance(state, np.ndarray) else state.numpy()
+        ev = env if isinstance(env, np.ndarray) else env.numpy()
+        if st.dtype != np.float64 or not st.flags.c_contiguous or st.shape[1] != self.n:
+            raise CampError("state must be C-contiguous float64 [C, n]")
+        if ev.dtype != np.float64 or not ev.flags.c_contiguous or ev.shape != (st.shape[0], self.n_env):
+            raise CampError("env must be C-contiguous float64 [C, n_env]")
+        a = np.ascontiguousarray(np.atleast_1d(np.asarray(atol, dtype=np.float64)))
+        status = np.zeros(st.shape[0], dtype=np.int32)
+        o = SolveOpts()
+        lib().camp_solve_opts_default(ctypes.byref(o), variant)
+        if persistent is not None:
+            o.persistent = int(persistent)
+        o.max_steps = max_steps
+        o.cells_per_block = cells_per_block
+        o.stats = stats.ctypes.data if stats is not None else None
+        _check(lib().camp_solve_host(self._h, st.shape[0], ctypes.c_void_p(st.ctypes.data),
+                                     ctypes.c_void_p(ev.ctypes.data), float(dt), float(rtol),
+                                     ctypes.c_void_p(a.ctypes.data), a.size,
+                                     ctypes.c_void_p(status.ctypes.data), ctypes.byref(o),
+                                     _stream(stream)))
+        return status
+
+    # ---- single steps of the method (test entry points) ----
+    def rate_constants(self, env, stream=None):
+        import torch
+        C = env.shape[0]
+        _dev_f64(env, (C, self.n_env), "env")
+        kf = torch.empty((C, self.n_rxn), dtype=torch.float64, device=env.device)
+        kr = torch.empty_like(kf)
+        _check(lib().camp_rate_constants(self._h, C, _ptr(env), _ptr(kf), _ptr(kr), _stream(stream)))
+        return kf, kr
+
+    def forcing(self, state, env, stream=None):
+        import torch
+        C = state.shape[0]
+        f = torch.empty((C, self.n), dtype=torch.float64, device=state.device)
+        _check(lib().camp_forcing(self._h, C, _ptr(_dev_f64(state, (C, self.n), "state")),
+                                  _ptr(_dev_f64(env, (C, self.n_env), "env")), _ptr(f), _stream(stream)))
+        return f
+
+    def jacobian(self, state, env, variant=VARIANT_FP64, stream=None):
+        import torch
+        C = state.shape[0]
+        J = torch.empty((C, self.info.nnz_jac), dtype=torch.float64, device=state.device)
+        _check(lib().camp_jacobian(self._h, C, _ptr(_dev_f64(state, (C, self.n), "state")),
+                                   _ptr(_dev_f64(env, (C, self.n_env), "env")), _ptr(J), variant,
+                                   _stream(stream)))
+        return J
+
+    def lu_solve(self, state, env, gamma, b, variant=VARIANT_FP64, stream=None):
+        import torch
+        C = state.shape[0]
+        x = torch.empty((C, self.n), dtype=torch.float64, device=state.device)
+        st = torch.empty(C, dtype=torch.int32, device=state.device)
+        _check(lib().camp_lu_solve(self._h, C, _ptr(_dev_f64(state, (C, self.n), "state")),
+                                   _ptr(_dev_f64(env, (C, self.n_env), "env")), float(gamma),
+                                   _ptr(_dev_f64(b, (C, self.n), "b")), _ptr(x), _ptr(st), variant,
+                                   _stream(stream)))
+        return x, st

@@ -1,0 +1,403 @@
+// C ABI of libcamp.so (declared in include/camp.h): argument checking,
+// mechanism handles, launch configuration.  No arithmetic of the method lives
+// here; every step of the solve runs in the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "camp.h"
+#include "kernels.cuh"
+#include "launch.h"
+#include "mech.hpp"
+
+struct camp_mech {
+    camp::HostMech h;
+    DevMech dm;
+    void *dev_tables = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    unsigned long long *own_ws = nullptr;
+    std::mutex mu;           // guards own_ws creation and the staging buffers
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    bool on_device = false;
+};
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CUDA_TRY(x)                                                                   \
+    do {                                                                              \
+        cudaError_t e_ = (x);                                                         \
+        if (e_ != cudaSuccess)                                                        \
+            return fail(CAMP_E_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+const int kMaxSmem = 227 * 1024;
+
+int check_device(const camp_mech *m) {
+    if (!m->on_device) return fail(CAMP_E_INVAL, "mechanism was compiled without device tables");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(CAMP_E_CUDA, "cudaGetDevice failed");
+    if (dev != m->device)
+        return fail(CAMP_E_INVAL, "current device differs from the mechanism's device");
+    return CAMP_OK;
+}
+
+template <int NPL>
+cudaError_t forcing_npl(const DevMech &m, long long n_cells, const double *state, const double *env,
+                        double *f, cudaStream_t s) {
+    auto kern = campdev::k_forcing<32, NPL, double>;
+    int smem = camp_cell_smem_bytes(m, 8);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)n_cells, 32, smem, s>>>(m, n_cells, state, env, f);
+    return cudaGetLastError();
+}
+}  // namespace
+
+int camp_pick_npl(int n) {
+    const int need = (n + 31) / 32;
+    const int avail[] = {1, 2, 3, 4, 6, 8};
+    for (int a : avail)
+        if (a >= need) return a;
+    return -1;
+}
+
+int camp_cell_smem_bytes(const DevMech &m, int lu_elem) {
+    return campdev::cell_smem(m.n, m.R, m.nlu, lu_elem).bytes;
+}
+
+cudaError_t camp_launch_rates(const DevMech &m, long long n_cells, const double *env, double *kf,
+                              double *kr, cudaStream_t s) {
+    const int per = 4;
+    campdev::k_rates<32><<<(unsigned)((n_cells + per - 1) / per), 32 * per, 0, s>>>(m, n_cells, env, kf, kr);
+    return cudaGetLastError();
+}
+
+cudaError_t camp_launch_forcing(const DevMech &m, long long n_cells, const double *state,
+                                const double *env, double *f, cudaStream_t s) {
+    switch (camp_pick_npl(m.n)) {
+    case 1: return forcing_npl<1>(m, n_cells, state, env, f, s);
+    case 2: return forcing_npl<2>(m, n_cells, state, env, f, s);
+    case 3: return forcing_npl<3>(m, n_cells, state, env, f, s);
+    case 4: return forcing_npl<4>(m, n_cells, state, env, f, s);
+    case 6: return forcing_npl<6>(m, n_cells, state, env, f, s);
+    case 8: return forcing_npl<8>(m, n_cells, state, env, f, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+extern "C" {
+
+const char *camp_last_error(void) { return g_err.c_str(); }
+
+static int mech_build(const char *json, size_t len, camp_mech **out, char *err, size_t errlen,
+                      bool upload) {
+    auto report = [&](int code, const std::string &msg) {
+        if (err && errlen) {
+            size_t k = std::min(errlen - 1, msg.size());
+            std::memcpy(err, msg.data(), k);
+            err[k] = 0;
+        }
+        return fail(code, msg);
+    };
+    if (!out) return report(CAMP_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!json) return report(CAMP_E_INVAL, "json is NULL");
+    camp_mech *m = new camp_mech();
+    try {
+        m->h = camp::compile_mechanism(json, len);
+    } catch (const std::exception &e) {
+        delete m;
+        return report(CAMP_E_PARSE, e.what());
+    }
+    if (camp_pick_npl(m->h.n) < 0) {
+        delete m;
+        return report(CAMP_E_UNSUPPORTED, "more than 256 species");
+    }
+    DevMech probe{};
+    std::vector<unsigned char> img = camp::pack_tables(m->h, probe, nullptr);
+    if (camp_cell_smem_bytes(probe, 8) > kMaxSmem) {
+        delete m;
+        return report(CAMP_E_UNSUPPORTED, "per-cell working set exceeds shared memory");
+    }
+    if (!upload) {
+        m->dm = probe;
+        *out = m;
+        g_err.clear();
+        return CAMP_OK;
+    }
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, m->device);
+    if (e == cudaSuccess) e = cudaMalloc(&m->dev_tables, img.size());
+    if (e == cudaSuccess) {
+        img = camp::pack_tables(m->h, m->dm, (const unsigned char *)m->dev_tables);
+        e = cudaMemcpy(m->dev_tables, img.data(), img.size(), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        if (m->dev_tables) cudaFree(m->dev_tables);
+        delete m;
+        return report(e == cudaErrorMemoryAllocation ? CAMP_E_NOMEM : CAMP_E_CUDA,
+                      std::string("loading tables: ") + cudaGetErrorString(e));
+    }
+    m->on_device = true;
+    *out = m;
+    g_err.clear();
+    return CAMP_OK;
+}
+
+int camp_mech_load(const char *json, size_t len, camp_mech **out, char *err, size_t errlen) {
+    return mech_build(json, len, out, err, errlen, true);
+}
+
+int camp_mech_compile(const char *json, size_t len, camp_mech **out, char *err, size_t errlen) {
+    return mech_build(json, len, out, err, errlen, false);
+}
+
+void camp_mech_free(camp_mech *m) {
+    if (!m) return;
+    if (!m->on_device) {
+        delete m;
+        return;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->device);
+    if (m->dev_tables) cudaFree(m->dev_tables);
+    if (m->own_ws) cudaFree(m->own_ws);
+    if (m->stage) cudaFree(m->stage);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete m;
+}
+
+int camp_mech_info_get(const camp_mech *m, camp_mech_info *o) {
+    if (!m || !o) return fail(CAMP_E_INVAL, "NULL argument");
+    const camp::HostMech &h = m->h;
+    o->n_species = h.n;
+    o->n_rxn = (int32_t)h.procs.size();
+    o->n_env = h.n_env;
+    o->n_sections = h.n_sections;
+    o->nnz_jac = (int32_t)h.colidx.size();
+    o->nnz_lu = (int32_t)h.lu_colidx.size();
+    o->rxn_map_len = (int32_t)h.rxn_map.size();
+    o->dense_block = h.D;
+    o->lu_storage = h.nlu;
+    o->smem_per_cell_mixed = camp_cell_smem_bytes(m->dm, 4);
+    o->smem_per_cell_fp64 = camp_cell_smem_bytes(m->dm, 8);
+    o->factor_updates = h.factor_updates;
+    o->flops_forcing = h.flops_forcing;
+    o->flops_jacobian = h.flops_jacobian;
+    o->flops_factor = h.flops_factor;
+    o->flops_solve = h.flops_solve;
+    return CAMP_OK;
+}
+
+int camp_mech_species_index(const camp_mech *m, const char *name) {
+    if (!m || !name) return -1;
+    for (int i = 0; i < m->h.n; i++)
+        if (m->h.species[i] == name) return i;
+    return -1;
+}
+
+int camp_mech_structure(const camp_mech *m, int32_t *rowptr, int32_t *colidx, int32_t *rxn_map,
+                        int32_t *perm, int32_t *lu_rowptr, int32_t *lu_colidx, int32_t *level_fwd,
+                        int32_t *level_bwd) {
+    if (!m) return fail(CAMP_E_INVAL, "NULL mechanism");
+    const camp::HostMech &h = m->h;
+    auto cp = [](int32_t *dst, const std::vector<int> &v) {
+        if (dst) std::copy(v.begin(), v.end(), dst);
+    };
+    cp(rowptr, h.rowptr);
+    cp(colidx, h.colidx);
+    cp(rxn_map, h.rxn_map);
+    cp(perm, h.perm);
+    cp(lu_rowptr, h.lu_rowptr);
+    cp(lu_colidx, h.lu_colidx);
+    cp(level_fwd, h.level_fwd);
+    cp(level_bwd, h.level_bwd);
+    return CAMP_OK;
+}
+
+void camp_solve_opts_default(camp_solve_opts *o, int variant) {
+    if (!o) return;
+    o->variant = variant;
+    o->persistent = variant == CAMP_VARIANT_MIXED ? 1 : 0;
+    o->max_steps = 10000;
+    o->cells_per_block = 0;
+    o->hmin_frac = 1e-10;
+    o->stats = nullptr;
+    o->workspace = nullptr;
+}
+
+size_t camp_workspace_bytes(void) { return 256; }
+
+int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double *env, double dt,
+               double rtol, const double *atol, int32_t atol_len, int32_t *status,
+               const camp_solve_opts *opts, void *stream) {
+    camp_mech *m = const_cast<camp_mech *>(mc);
+    if (!m) return fail(CAMP_E_INVAL, "NULL mechanism");
+    if (n_cells < 0) return fail(CAMP_E_INVAL, "n_cells < 0");
+    if (n_cells == 0) return CAMP_OK;
+    if (!state || !env || !atol || !status) return fail(CAMP_E_INVAL, "NULL array");
+    if (!(dt > 0.0) || !(dt < 1e300)) return fail(CAMP_E_INVAL, "dt must be positive and finite");
+    if (!(rtol > 0.0) || !(rtol < 1.0)) return fail(CAMP_E_INVAL, "rtol must be in (0, 1)");
+    if (atol_len != 1 && atol_len != m->h.n) return fail(CAMP_E_INVAL, "atol_len must be 1 or n_species");
+    camp_solve_opts o;
+    camp_solve_opts_default(&o, opts ? opts->variant : CAMP_VARIANT_MIXED);
+    if (opts) o = *opts;
+    if (o.variant != CAMP_VARIANT_MIXED && o.variant != CAMP_VARIANT_FP64)
+        return fail(CAMP_E_INVAL, "unknown variant");
+    if (o.max_steps <= 0) o.max_steps = 10000;
+    if (!(o.hmin_frac > 0.0)) o.hmin_frac = 1e-10;
+    if (int rc = check_device(m)) return rc;
+
+    const bool f32 = o.variant == CAMP_VARIANT_MIXED;
+    const int smem_cell = camp_cell_smem_bytes(m->dm, f32 ? 4 : 8);
+    int cpb = o.cells_per_block > 0 ? o.cells_per_block : (smem_cell > 8192 ? 1 : 2);
+    cpb = std::min(cpb, 8);
+    while (cpb > 1 && cpb * smem_cell > kMaxSmem) cpb--;
+
+    SolveArgs a;
+    a.n_cells = n_cells;
+    a.state = state;
+    a.env = env;
+    a.dt = dt;
+    a.rtol = rtol;
+    a.atol = atol;
+    a.atol_len = atol_len;
+    a.status = status;
+    a.stats = o.stats;
+    a.max_steps = o.max_steps;
+    a.hmin_frac = o.hmin_frac;
+    a.cpb = cpb;
+    a.queue = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    long long grid;
+    if (o.persistent) {
+        unsigned long long *q = (unsigned long long *)o.workspace;
+        if (!q) {
+            std::lock_guard<std::mutex> lk(m->mu);
+            if (!m->own_ws) CUDA_TRY(cudaMalloc(&m->own_ws, camp_workspace_bytes()));
+            q = m->own_ws;
+        }
+        int per_sm = 0;
+        CUDA_TRY(f32 ? camp_occupancy_f32(m->dm, cpb, &per_sm) : camp_occupancy_f64(m->dm, cpb, &per_sm));
+        if (per_sm < 1) return fail(CAMP_E_UNSUPPORTED, "kernel does not fit on an SM");
+        grid = std::min<long long>((long long)per_sm * m->sm_count, (n_cells + cpb - 1) / cpb);
+        CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(unsigned long long), s));
+        a.queue = q;
+    } else {
+        grid = (n_cells + cpb - 1) / cpb;
+        if (grid > 0x7fffffffLL) return fail(CAMP_E_INVAL, "too many cells for one launch");
+    }
+    CUDA_TRY(f32 ? camp_launch_solve_f32(m->dm, a, (int)grid, s) : camp_launch_solve_f64(m->dm, a, (int)grid, s));
+    return CAMP_OK;
+}
+
+int camp_solve_host(const camp_mech *mc, int64_t n_cells, double *state, const double *env,
+                    double dt, double rtol, const double *atol, int32_t atol_len, int32_t *status,
+                    const camp_solve_opts *opts, void *stream) {
+    camp_mech *m = const_cast<camp_mech *>(mc);
+    if (!m) return fail(CAMP_E_INVAL, "NULL mechanism");
+    if (n_cells <= 0) return n_cells == 0 ? CAMP_OK : fail(CAMP_E_INVAL, "n_cells < 0");
+    if (!state || !env || !atol || !status) return fail(CAMP_E_INVAL, "NULL array");
+    if (atol_len != 1 && atol_len != m->h.n) return fail(CAMP_E_INVAL, "atol_len must be 1 or n_species");
+    if (int rc = check_device(m)) return rc;
+    const size_t n = m->h.n, ne = m->h.n_env;
+    const size_t b_state = (size_t)n_cells * n * 8, b_env = (size_t)n_cells * ne * 8;
+    const size_t b_stat = ((size_t)n_cells * 4 + 15) & ~(size_t)15, b_atol = (n * 8 + 15) & ~(size_t)15;
+    const size_t b_stats = (size_t)n_cells * 4 * CAMP_NSTATS;
+    int32_t *host_stats = opts ? opts->stats : nullptr;
+    const size_t need = b_state + b_env + b_stat + b_atol + (host_stats ? b_stats : 0);
+    std::lock_guard<std::mutex> lk(m->mu);
+    if (m->stage_bytes < need) {
+        if (m->stage) cudaFree(m->stage);
+        m->stage = nullptr;
+        m->stage_bytes = 0;
+        CUDA_TRY(cudaMalloc(&m->stage, need));
+        m->stage_bytes = need;
+    }
+    char *base = (char *)m->stage;
+    double *d_state = (double *)base;
+    double *d_env = (double *)(base + b_state);
+    int32_t *d_status = (int32_t *)(base + b_state + b_env);
+    double *d_atol = (double *)(base + b_state + b_env + b_stat);
+    int32_t *d_stats = host_stats ? (int32_t *)(base + b_state + b_env + b_stat + b_atol) : nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(d_state, state, b_state, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d_env, env, b_env, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d_atol, atol, (size_t)atol_len * 8, cudaMemcpyHostToDevice, s));
+    camp_solve_opts o;
+    camp_solve_opts_default(&o, opts ? opts->variant : CAMP_VARIANT_MIXED);
+    if (opts) o = *opts;
+    o.stats = d_stats;
+    o.workspace = nullptr;
+    int rc = camp_solve(m, n_cells, d_state, d_env, dt, rtol, d_atol, atol_len, d_status, &o, stream);
+    if (rc != CAMP_OK) return rc;
+    CUDA_TRY(cudaMemcpyAsync(state, d_state, b_state, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(status, d_status, (size_t)n_cells * 4, cudaMemcpyDeviceToHost, s));
+    if (host_stats)
+        CUDA_TRY(cudaMemcpyAsync(host_stats, d_stats, b_stats, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return CAMP_OK;
+}
+
+int camp_rate_constants(const camp_mech *m, int64_t n_cells, const double *env, double *kf,
+                        double *kr, void *stream) {
+    if (!m || n_cells < 0 || (n_cells && (!env || !kf || !kr))) return fail(CAMP_E_INVAL, "bad argument");
+    if (!n_cells) return CAMP_OK;
+    if (int rc = check_device(m)) return rc;
+    CUDA_TRY(camp_launch_rates(m->dm, n_cells, env, kf, kr, (cudaStream_t)stream));
+    return CAMP_OK;
+}
+
+int camp_forcing(const camp_mech *m, int64_t n_cells, const double *state, const double *env,
+                 double *f, void *stream) {
+    if (!m || n_cells < 0 || (n_cells && (!state || !env || !f))) return fail(CAMP_E_INVAL, "bad argument");
+    if (!n_cells) return CAMP_OK;
+    if (n_cells > 0x7fffffffLL) return fail(CAMP_E_INVAL, "too many cells");
+    if (int rc = check_device(m)) return rc;
+    CUDA_TRY(camp_launch_forcing(m->dm, n_cells, state, env, f, (cudaStream_t)stream));
+    return CAMP_OK;
+}
+
+int camp_jacobian(const camp_mech *m, int64_t n_cells, const double *state, const double *env,
+                  double *jac, int32_t variant, void *stream) {
+    if (!m || n_cells < 0 || (n_cells && (!state || !env || !jac))) return fail(CAMP_E_INVAL, "bad argument");
+    if (variant != CAMP_VARIANT_MIXED && variant != CAMP_VARIANT_FP64) return fail(CAMP_E_INVAL, "unknown variant");
+    if (!n_cells) return CAMP_OK;
+    if (n_cells > 0x7fffffffLL) return fail(CAMP_E_INVAL, "too many cells");
+    if (int rc = check_device(m)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(variant == CAMP_VARIANT_MIXED ? camp_launch_jacobian_f32(m->dm, n_cells, state, env, jac, s)
+                                           : camp_launch_jacobian_f64(m->dm, n_cells, state, env, jac, s));
+    return CAMP_OK;
+}
+
+int camp_lu_solve(const camp_mech *m, int64_t n_cells, const double *state, const double *env,
+                  double gamma, const double *b, double *x, int32_t *status, int32_t variant,
+                  void *stream) {
+    if (!m || n_cells < 0 || (n_cells && (!state || !env || !b || !x || !status)))
+        return fail(CAMP_E_INVAL, "bad argument");
+    if (variant != CAMP_VARIANT_MIXED && variant != CAMP_VARIANT_FP64) return fail(CAMP_E_INVAL, "unknown variant");
+    if (!n_cells) return CAMP_OK;
+    if (n_cells > 0x7fffffffLL) return fail(CAMP_E_INVAL, "too many cells");
+    if (int rc = check_device(m)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(variant == CAMP_VARIANT_MIXED
+                 ? camp_launch_lu_solve_f32(m->dm, n_cells, state, env, gamma, b, x, status, s)
+                 : camp_launch_lu_solve_f64(m->dm, n_cells, state, env, gamma, b, x, status, s));
+    return CAMP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,669 @@
+// Per-cell device routines of the batched chemistry solve (sm_103a).
+//
+// One group of G lanes (G = 32: one warp) owns one grid cell.  Lane l holds
+// the FP64 Nordsieck rows, error weights and corrections of positions
+// p = l + G*s (s < NPL) in registers.  Shared memory per cell holds the
+// current iterate y, the process rates, the rate constants, the LU values and
+// the substitution vector.  Every decision of the step controller is taken on
+// group-reduced (hence identical) values, so the lanes of a cell never
+// diverge from each other; different cells never synchronise.
+//
+// Paper references (CAMP, arXiv 2111.07436): rate constants, Table 2;
+// forcing f_i = sum_k (dy_i/dt)_k and Jacobian df_i/dy_j = sum_k (...)_k,
+// Sect. 2.4.2; the implicit BDF + Newton + sparse LU solve, Sect. 2.4.1.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "devmech.h"
+
+namespace campdev {
+
+// ---- controller constants (identical meaning to the oracle's) ------------
+constexpr int QMAX = CAMP_QMAX;
+constexpr int NEWTON_MAXIT = 3;
+constexpr double NEWTON_TOL = 0.1;
+constexpr double RHO_DIV = 2.0;
+constexpr double DGMAX = 0.3;
+constexpr int MSBJ = 20;
+constexpr double ETA_MAX = 10.0;
+constexpr double ETA_THRESH = 1.5;
+constexpr double ETA_CF = 0.25;
+constexpr int MAX_NEF = 7;
+constexpr int MAX_NCF = 10;
+
+enum { ST_OK = 0, ST_MAXSTEPS = 1, ST_ERRTEST = 2, ST_NEWTON = 3, ST_SINGULAR = 4, ST_NONFINITE = 5 };
+
+// ---- physical constants (SI 2019, exact) ----------------------------------
+constexpr double KB = 1.380649e-23;
+constexpr double NAV = 6.02214076e23;
+constexpr double RG = KB * NAV;
+constexpr double PI_D = 3.14159265358979323846;
+
+// ---- shared-memory layout of one cell --------------------------------------
+struct CellSmem {
+    int ys, rs, kf, kr, x, lu, bytes;
+};
+__host__ __device__ inline int align16(int b) { return (b + 15) & ~15; }
+__host__ __device__ inline CellSmem cell_smem(int n, int R, int nlu, int lu_elem) {
+    CellSmem c;
+    int o = 0;
+    c.ys = o; o = align16(o + 8 * n);
+    c.rs = o; o = align16(o + 8 * R);
+    c.kf = o; o = align16(o + 8 * R);
+    c.kr = o; o = align16(o + 8 * R);
+    c.x = o;  o = align16(o + lu_elem * n);
+    c.lu = o; o = align16(o + lu_elem * nlu);
+    c.bytes = o;
+    return c;
+}
+
+template <typename LT>
+struct CellPtr {
+    double *ys, *rs, *kf, *kr;
+    LT *x, *lu;
+    __device__ CellPtr(char *base, const DevMech &m) {
+        CellSmem c = cell_smem(m.n, m.R, m.nlu, (int)sizeof(LT));
+        ys = (double *)(base + c.ys);
+        rs = (double *)(base + c.rs);
+        kf = (double *)(base + c.kf);
+        kr = (double *)(base + c.kr);
+        x = (LT *)(base + c.x);
+        lu = (LT *)(base + c.lu);
+    }
+};
+
+// ---- group primitives --------------------------------------------------------
+template <int G>
+__device__ __forceinline__ double gsum(double v, unsigned gm) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gm, v, o, G);
+    return __shfl_sync(gm, v, 0, G);
+}
+
+// ---- rate constants (Table 2), per process, from the cell's env ------------
+__device__ __forceinline__ double ipowd(double x, int k) {
+    double r = 1.0;
+    for (int i = 0; i < k; i++) r *= x;
+    return r;
+}
+
+__device__ inline void rate_constant(const DevMech &m, int k, const double *__restrict__ env,
+                                     double &kf, double &kr) {
+    const double T = env[0], P = env[1];
+    const double Mair = P / (KB * T) * 1e-6;  // molec cm^-3
+    const double mppb = Mair * 1e-9;          // molec cm^-3 per ppb
+    const double *par = m.rpar + 8 * k;
+    const int nr = __ldg(m.rnr + k);
+    kf = 0.0;
+    kr = 0.0;
+    switch (__ldg(m.rtype + k)) {
+    case CAMP_P_ARRHENIUS: {
+        // k = A exp(C/T) (T/D)^B (1 + E P)
+        double kk = __ldg(par) * exp(__ldg(par + 2) / T) * pow(T / __ldg(par + 3), __ldg(par + 1)) *
+                    (1.0 + __ldg(par + 4) * P);
+        kf = kk * ipowd(mppb, nr - 1);
+        break;
+    }
+    case CAMP_P_TROE: {
+        // k0[M] / (1 + k0[M]/kinf) * Fc^(1 / (1 + (log10(k0[M]/kinf)/N)^2))
+        double k0 = __ldg(par) * exp(__ldg(par + 2) / T) * pow(T / 300.0, __ldg(par + 1));
+        double ki = __ldg(par + 3) * exp(__ldg(par + 5) / T) * pow(T / 300.0, __ldg(par + 4));
+        double x = k0 * Mair / ki;
+        double lg = log10(x) / __ldg(par + 7);
+        double kk = k0 * Mair / (1.0 + x) * pow(__ldg(par + 6), 1.0 / (1.0 + lg * lg));
+        kf = kk * ipowd(mppb, nr - 1);
+        break;
+    }
+    case CAMP_P_PHOTOLYSIS:
+    case CAMP_P_EMISSION:
+    case CAMP_P_LOSS:
+        kf = env[__ldg(m.rslot + k)];
+        break;
+    case CAMP_P_HENRY: {
+        // H(T) [M/Pa]; k_c = 4 pi r Dg f_fs(Kn, alpha) per particle, times N;
+        // evaporation constant k_c / (H_cc L) with H_cc = 1000 H R T
+        const int b = __ldg(m.rslot + k);
+        const double rad = env[m.env_sec_base + 3 * b];
+        const double Np = env[m.env_sec_base + 3 * b + 1];
+        const double L = env[m.env_sec_base + 3 * b + 2];
+        if (!(L > 0.0 && Np > 0.0 && rad > 0.0)) break;
+        double H = __ldg(par) * exp(__ldg(par + 1) * (1.0 / T - 1.0 / 298.0));
+        double alpha = __ldg(par + 2), Dg = __ldg(par + 3), MW = __ldg(par + 4);
+        double Hcc = 1000.0 * H * RG * T;
+        double cbar = sqrt(8.0 * RG * T / (PI_D * MW));
+        double Kn = 3.0 * Dg / cbar / rad;
+        double ffs = 0.75 * alpha * (1.0 + Kn) / (Kn * Kn + Kn + 0.283 * Kn * alpha + 0.75 * alpha);
+        double kb = Np * 4.0 * PI_D * rad * Dg * ffs;
+        kf = kb;
+        kr = kb / (Hcc * L);
+        break;
+    }
+    case CAMP_P_AQREV: {
+        // K_eq = A exp(C (1/T - 1/298)); rates in M/s, molarity = y * phi,
+        // phi = 1e-9 P / (R T 1000 L) M per ppb
+        const int b = __ldg(m.rslot + k);
+        const double L = env[m.env_sec_base + 3 * b + 2];
+        if (!(L > 0.0)) break;
+        double Keq = __ldg(par) * exp(__ldg(par + 1) * (1.0 / T - 1.0 / 298.0));
+        double krev = __ldg(par + 2);
+        double phi = 1e-9 * P / (RG * T * 1000.0 * L);
+        kf = Keq * krev * ipowd(phi, nr - 1);
+        kr = krev * ipowd(phi, __ldg(m.rnp + k) - 1);
+        break;
+    }
+    }
+}
+
+// ---- forcing f(y): rates of all processes, then a per-position gather --------
+__device__ __forceinline__ double rate_term(const DevMech &m, int k, const double *ys, double kf,
+                                            double kr) {
+    const int *fac = m.rfac + 6 * k;
+    int a0 = __ldg(fac), a1 = __ldg(fac + 1), a2 = __ldg(fac + 2);
+    double a = kf;
+    if (a0 >= 0) a *= ys[a0];
+    if (a1 >= 0) a *= ys[a1];
+    if (a2 >= 0) a *= ys[a2];
+    if (kr != 0.0) {
+        int b0 = __ldg(fac + 3), b1 = __ldg(fac + 4), b2 = __ldg(fac + 5);
+        double b = kr;
+        if (b0 >= 0) b *= ys[b0];
+        if (b1 >= 0) b *= ys[b1];
+        if (b2 >= 0) b *= ys[b2];
+        a -= b;
+    }
+    return a;
+}
+
+// y (own positions, registers) -> f (own positions).  Leaves ys = y.
+template <int G, int NPL, typename LT>
+__device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, const double (&y)[NPL],
+                                       double (&f)[NPL], int lane, unsigned gm) {
+#pragma unroll
+    for (int s = 0; s < NPL; s++) {
+        int p = lane + G * s;
+        if (p < m.n) c.ys[p] = y[s];
+    }
+    __syncwarp(gm);
+    for (int k = lane; k < m.R; k += G) c.rs[k] = rate_term(m, k, c.ys, c.kf[k], c.kr[k]);
+    __syncwarp(gm);
+#pragma unroll
+    for (int s = 0; s < NPL; s++) {
+        int p = lane + G * s;
+        double acc = 0.0;
+        if (p < m.n) {
+            int b = __ldg(m.fptr + p), e = __ldg(m.fptr + p + 1);
+            for (int q = b; q < e; q++) acc += __ldg(m.fc + q) * c.rs[__ldg(m.fk + q)];
+        }
+        f[s] = acc;
+    }
+}
+
+// ---- Jacobian gather: J (or M = I - gamma J) at ys into LU storage -----------
+// mode 0: write M = I - gamma J into c.lu (zeroing fill and block entries)
+// mode 1: write J values to out[nnzJ] (species-CSR order)
+template <int G, typename LT>
+__device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c, double gamma,
+                                         int lane, unsigned gm, int mode, double *out) {
+    if (mode == 0) {
+        for (int i = lane; i < m.nlu; i += G) c.lu[i] = (LT)0;
+        __syncwarp(gm);
+    }
+    for (int t = lane; t < m.nnzJ; t += G) {
+        LT acc = (LT)0;
+        int b = __ldg(m.jptr + t), e = __ldg(m.jptr + t + 1);
+        for (int q = b; q < e; q++) {
+            int k = __ldg(m.jk + q);
+            LT v = (LT)__ldg(m.jc + q) * (LT)(k >= 0 ? c.kf[k] : c.kr[-k - 1]);
+            int o1 = __ldg(m.jo + 2 * q), o2 = __ldg(m.jo + 2 * q + 1);
+            if (o1 >= 0) v *= (LT)c.ys[o1];
+            if (o2 >= 0) v *= (LT)c.ys[o2];
+            acc += v;
+        }
+        if (mode == 0)
+            c.lu[__ldg(m.jdst + t)] = (__ldg(m.jdiag + t) ? (LT)1 : (LT)0) - (LT)gamma * acc;
+        else
+            out[t] = (double)acc;
+    }
+    __syncwarp(gm);
+}
+
+template <typename LT> __device__ __forceinline__ LT tiny_pivot();
+template <> __device__ __forceinline__ float tiny_pivot<float>() { return 1e-30f; }
+template <> __device__ __forceinline__ double tiny_pivot<double>() { return 1e-300; }
+
+// ---- LU factorisation in place; returns true if every pivot is usable -------
+template <int G, typename LT>
+__device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigned gm) {
+    LT *lu = c.lu;
+    bool bad = false;
+    // sparse rows (and the sparse-pivot updates of the block rows), by level
+    for (int L = 0; L < m.n_flev; L++) {
+        int b = __ldg(m.flev_ptr + L), e = __ldg(m.flev_ptr + L + 1);
+        for (int r = b + lane; r < e; r += G) {
+            int i = __ldg(m.frow + r);
+            int qb = __ldg(m.fops_ptr + i), qe = __ldg(m.fops_ptr + i + 1);
+            LT l = (LT)0;
+            for (int q = qb; q < qe; q++) {
+                uint32_t op = __ldg(m.fops + q);
+                int t = CAMP_OP_TGT(op), s = CAMP_OP_SRC(op);
+                if (op & CAMP_OP_DIV) {
+                    l = lu[t] / lu[s];
+                    lu[t] = l;
+                } else {
+                    lu[t] -= l * lu[s];
+                }
+            }
+            if (i < m.d) {
+                LT u = lu[__ldg(m.udiag + i)];
+                bad |= !(fabs((double)u) > (double)tiny_pivot<LT>()) || !isfinite((double)u);
+            }
+        }
+        __syncwarp(gm);
+    }
+    // dense trailing block, right-looking: multipliers by row, updates by column
+    const int D = m.D, LD = m.LD;
+    LT *A = lu + m.dbase;
+    for (int k = 0; k < D; k++) {
+        LT piv = A[k * LD + k];
+        if (lane == 0) bad |= !(fabs((double)piv) > (double)tiny_pivot<LT>()) || !isfinite((double)piv);
+        for (int i = k + 1 + lane; i < D; i += G) A[i * LD + k] = A[i * LD + k] / piv;
+        __syncwarp(gm);
+        for (int j = k + 1 + lane; j < D; j += G) {
+            LT ukj = A[k * LD + j];
+            for (int i = k + 1; i < D; i++) A[i * LD + j] -= A[i * LD + k] * ukj;
+        }
+        __syncwarp(gm);
+    }
+    return !__any_sync(gm, bad);
+}
+
+// ---- substitution: solves (LU) x = x in place (c.x holds the right side) -----
+template <int G, typename LT>
+__device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, unsigned gm) {
+    LT *x = c.x;
+    const LT *lu = c.lu;
+    __syncwarp(gm);
+    // forward, sparse rows and the L21 part of block rows
+    for (int L = 0; L < m.n_flev; L++) {
+        int b = __ldg(m.flev_ptr + L), e = __ldg(m.flev_ptr + L + 1);
+        for (int r = b + lane; r < e; r += G) {
+            int i = __ldg(m.frow + r);
+            LT s = x[i];
+            int qb = __ldg(m.sl_ptr + i), qe = __ldg(m.sl_ptr + i + 1);
+            for (int q = qb; q < qe; q++) s -= lu[__ldg(m.sl_off + q)] * x[__ldg(m.sl_col + q)];
+            x[i] = s;
+        }
+        __syncwarp(gm);
+    }
+    // dense block forward (unit lower) and backward
+    const int D = m.D, LD = m.LD, d = m.d;
+    const LT *A = lu + m.dbase;
+    LT *xb = x + d;
+    for (int k = 0; k < D; k++) {
+        LT xk = xb[k];
+        for (int i = k + 1 + lane; i < D; i += G) xb[i] -= A[i * LD + k] * xk;
+        __syncwarp(gm);
+    }
+    for (int k = D - 1; k >= 0; k--) {
+        LT xk = xb[k] / A[k * LD + k];
+        __syncwarp(gm);
+        if (lane == 0) xb[k] = xk;
+        for (int i = lane; i < k; i += G) xb[i] -= A[i * LD + k] * xk;
+        __syncwarp(gm);
+    }
+    // backward, sparse rows by level
+    for (int L = 0; L < m.n_blev; L++) {
+        int b = __ldg(m.blev_ptr + L), e = __ldg(m.blev_ptr + L + 1);
+        for (int r = b + lane; r < e; r += G) {
+            int i = __ldg(m.brow + r);
+            LT s = x[i];
+            int qb = __ldg(m.su_ptr + i), qe = __ldg(m.su_ptr + i + 1);
+            for (int q = qb; q < qe; q++) s -= lu[__ldg(m.su_off + q)] * x[__ldg(m.su_col + q)];
+            x[i] = s / lu[__ldg(m.udiag + i)];
+        }
+        __syncwarp(gm);
+    }
+}
+
+template <int G, int NPL>
+__device__ __forceinline__ double wrms(const DevMech &m, const double (&v)[NPL], const double (&w)[NPL],
+                                       unsigned gm) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < NPL; i++) {
+        double a = v[i] * w[i];
+        s += a * a;
+    }
+    return sqrt(gsum<G>(s, gm) / (double)m.n);
+}
+
+// ---- Nordsieck array operations (q uniform per cell; rows in registers) -----
+template <int NPL>
+__device__ __forceinline__ void nord_predict(double (&z)[QMAX + 1][NPL], int q) {
+#pragma unroll
+    for (int k = 0; k < QMAX; k++) {
+        if (k < q) {
+#pragma unroll
+            for (int j = QMAX; j > k; j--) {
+                if (j <= q) {
+#pragma unroll
+                    for (int s = 0; s < NPL; s++) z[j - 1][s] += z[j][s];
+                }
+            }
+        }
+    }
+}
+template <int NPL>
+__device__ __forceinline__ void nord_retract(double (&z)[QMAX + 1][NPL], int q) {
+#pragma unroll
+    for (int k = QMAX - 1; k >= 0; k--) {
+        if (k < q) {
+#pragma unroll
+            for (int j = 1; j <= QMAX; j++) {
+                if (j > k && j <= q) {
+#pragma unroll
+                    for (int s = 0; s < NPL; s++) z[j - 1][s] -= z[j][s];
+                }
+            }
+        }
+    }
+}
+template <int NPL>
+__device__ __forceinline__ void nord_rescale(double (&z)[QMAX + 1][NPL], int q, double eta) {
+    double f = 1.0;
+#pragma unroll
+    for (int j = 1; j <= QMAX; j++) {
+        if (j <= q) {
+            f *= eta;
+#pragma unroll
+            for (int s = 0; s < NPL; s++) z[j][s] *= f;
+        }
+    }
+}
+
+struct CellStats {
+    int steps, newton, jac, errfail, ordsum;
+};
+
+// ---- one cell over [0, dt] ---------------------------------------------------
+// y_cell/env_cell: this cell's rows (declaration order).  Returns the status;
+// the state is written back only on success.
+template <int G, int NPL, typename LT>
+__device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__restrict__ y_cell,
+                              const double *__restrict__ env_cell, double dt, double rtol,
+                              const double *__restrict__ atol, int atol_len, int max_steps,
+                              double hmin_frac, int lane, unsigned gm, CellStats &st) {
+    const int n = m.n;
+    st.steps = st.newton = st.jac = st.errfail = st.ordsum = 0;
+
+    // inputs must be finite
+    bool bad = false;
+    for (int i = lane; i < m.n_env; i += G) bad |= !isfinite(env_cell[i]);
+    double z[QMAX + 1][NPL], e[NPL], ep[NPL], w[NPL], f[NPL], t1[NPL];
+    double atl[NPL];
+#pragma unroll
+    for (int s = 0; s < NPL; s++) {
+        int p = lane + G * s;
+        double v = 0.0, a = 1.0;
+        if (p < n) {
+            int sp = __ldg(m.perm + p);
+            v = y_cell[sp];
+            a = atol[atol_len == 1 ? 0 : sp];
+        }
+        bad |= !isfinite(v);
+#pragma unroll
+        for (int j = 0; j <= QMAX; j++) z[j][s] = 0.0;
+        z[0][s] = v;
+        atl[s] = a;
+        e[s] = ep[s] = 0.0;
+    }
+    if (__any_sync(gm, bad)) return ST_NONFINITE;
+
+    for (int k = lane; k < m.R; k += G) {
+        double a, b;
+        rate_constant(m, k, env_cell, a, b);
+        c.kf[k] = a;
+        c.kr[k] = b;
+    }
+    __syncwarp(gm);
+
+    auto set_weights = [&]() {
+#pragma unroll
+        for (int s = 0; s < NPL; s++) {
+            int p = lane + G * s;
+            w[s] = (p < n) ? 1.0 / (rtol * fabs(z[0][s]) + atl[s]) : 0.0;
+        }
+    };
+    auto any_nonfinite = [&](const double(&v)[NPL]) {
+        bool b2 = false;
+#pragma unroll
+        for (int s = 0; s < NPL; s++) b2 |= !isfinite(v[s]);
+        return __any_sync(gm, b2) != 0;
+    };
+
+    const double T = dt, hmin = hmin_frac * dt;
+    set_weights();
+    eval_f<G, NPL, LT>(m, c, z[0], f, lane, gm);
+    if (any_nonfinite(f)) return ST_NONFINITE;
+
+    // initial step: Hairer, Norsett & Wanner's starting-step estimate for order 1
+    double h;
+    {
+        double d0 = wrms<G, NPL>(m, z[0], w, gm), d1 = wrms<G, NPL>(m, f, w, gm);
+        double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+        if (h0 > T) h0 = T;
+#pragma unroll
+        for (int s = 0; s < NPL; s++) t1[s] = z[0][s] + h0 * f[s];
+        eval_f<G, NPL, LT>(m, c, t1, e, lane, gm);
+#pragma unroll
+        for (int s = 0; s < NPL; s++) t1[s] = e[s] - f[s];
+        double d2 = wrms<G, NPL>(m, t1, w, gm) / h0;
+        double dm = d1 > d2 ? d1 : d2;
+        double h1 = (dm <= 1e-15) ? fmax(1e-6, h0 * 1e-3) : sqrt(0.01 / dm);
+        h = fmin(100.0 * h0, h1);
+        if (!(h <= T)) h = T;
+    }
+#pragma unroll
+    for (int s = 0; s < NPL; s++) {
+        z[1][s] = h * f[s];
+        e[s] = 0.0;
+    }
+
+    int q = 1, qwait = 2, nst = 0, nst_lu = 0;
+    bool have_lu = false, need_setup = true, ep_valid = false;
+    double t = 0.0, gamma_lu = 0.0;
+    int status = ST_OK;
+
+    while (t < T) {
+        if (nst >= max_steps) { status = ST_MAXSTEPS; break; }
+        set_weights();
+        int nef = 0, ncf = 0;
+        bool last = false;
+        double err = 0.0;
+        bool accepted = false;
+        while (!accepted) {
+            last = false;
+            if (t + h >= T) {
+                if (t + h > T) {
+                    double eta = (T - t) / h;
+                    nord_rescale<NPL>(z, q, eta);
+                    h = T - t;
+                }
+                last = true;
+            }
+            nord_predict<NPL>(z, q);
+            const double l1 = m.lcoef[q][1];
+            const double gamma = h / l1;
+            bool jcur = false, lu_fail = false;
+            if (!have_lu || need_setup || nst >= nst_lu + MSBJ || fabs(gamma / gamma_lu - 1.0) > DGMAX) {
+#pragma unroll
+                for (int s = 0; s < NPL; s++) {
+                    int p = lane + G * s;
+                    if (p < n) c.ys[p] = z[0][s];
+                }
+                __syncwarp(gm);
+                assemble<G, LT>(m, c, gamma, lane, gm, 0, nullptr);
+                lu_fail = !factor<G, LT>(m, c, lane, gm);
+                st.jac++;
+                gamma_lu = gamma;
+                nst_lu = nst;
+                have_lu = !lu_fail;
+                need_setup = false;
+                jcur = true;
+            }
+            // modified Newton on G(e) = e - gamma f(z0 + e) + z1 / l1
+            bool conv = false;
+            if (!lu_fail) {
+                double dprev = 0.0;
+#pragma unroll
+                for (int s = 0; s < NPL; s++) e[s] = 0.0;
+                const double scale = (gamma != gamma_lu) ? 2.0 / (1.0 + gamma / gamma_lu) : 1.0;
+                for (int it = 0; it < NEWTON_MAXIT; it++) {
+#pragma unroll
+                    for (int s = 0; s < NPL; s++) t1[s] = z[0][s] + e[s];
+                    eval_f<G, NPL, LT>(m, c, t1, f, lane, gm);
+                    st.newton++;
+                    if (any_nonfinite(f)) break;
+#pragma unroll
+                    for (int s = 0; s < NPL; s++) {
+                        int p = lane + G * s;
+                        if (p < n) c.x[p] = (LT)(-(e[s] - gamma * f[s] + z[1][s] / l1));
+                    }
+                    substitute<G, LT>(m, c, lane, gm);
+                    double dsq = 0.0;
+                    bool nf = false;
+#pragma unroll
+                    for (int s = 0; s < NPL; s++) {
+                        int p = lane + G * s;
+                        double dl = (p < n) ? (double)c.x[p] : 0.0;
+                        if (scale != 1.0) dl *= scale;
+                        e[s] += dl;
+                        double a = dl * w[s];
+                        dsq += a * a;
+                        nf |= !isfinite(dl);
+                    }
+                    double dn = sqrt(gsum<G>(dsq, gm) / (double)n);
+                    if (__any_sync(gm, nf) || !isfinite(dn)) break;
+                    double test = dn;
+                    if (it > 0) {
+                        double rho = dn / dprev;
+                        if (rho > RHO_DIV) break;
+                        if (rho < 1.0) test = dn * rho;
+                    }
+                    if (test <= NEWTON_TOL) { conv = true; break; }
+                    dprev = dn;
+                }
+            }
+            if (!conv) {
+                nord_retract<NPL>(z, q);
+                if (!jcur) { need_setup = true; continue; }
+                if (++ncf >= MAX_NCF) { status = lu_fail ? ST_SINGULAR : ST_NEWTON; break; }
+                h *= ETA_CF;
+                if (h < hmin) { status = ST_ERRTEST; break; }
+                nord_rescale<NPL>(z, q, ETA_CF);
+                need_setup = true;
+                qwait = q + 1;
+                continue;
+            }
+            err = m.ecoef[q] * wrms<G, NPL>(m, e, w, gm);
+            if (err > 1.0) {
+                nord_retract<NPL>(z, q);
+                st.errfail++;
+                if (++nef >= MAX_NEF) { status = ST_ERRTEST; break; }
+                if (nef >= 3) {
+                    h *= 0.1;
+                    if (h < hmin) { status = ST_ERRTEST; break; }
+                    q = 1;
+                    eval_f<G, NPL, LT>(m, c, z[0], f, lane, gm);
+#pragma unroll
+                    for (int s = 0; s < NPL; s++) z[1][s] = h * f[s];
+                } else {
+                    double eta = 0.9 * pow(err, -1.0 / (q + 1));
+                    if (eta < 0.2) eta = 0.2;
+                    h *= eta;
+                    if (h < hmin) { status = ST_ERRTEST; break; }
+                    nord_rescale<NPL>(z, q, eta);
+                }
+                qwait = q + 1;
+                continue;
+            }
+            accepted = true;
+        }
+        if (status != ST_OK) break;
+
+        // accept: z += l (x) e
+#pragma unroll
+        for (int j = 0; j <= QMAX; j++) {
+            if (j <= q) {
+                const double lj = m.lcoef[q][j];
+#pragma unroll
+                for (int s = 0; s < NPL; s++) z[j][s] += lj * e[s];
+            }
+        }
+        t = last ? T : t + h;
+        nst++;
+        st.ordsum += q;
+        if (any_nonfinite(z[0])) { status = ST_NONFINITE; break; }
+
+        if (--qwait <= 0 && t < T) {
+            double eta_q = 1.0 / (pow(1.2 * err, 1.0 / (q + 1)) + 1e-6);
+            double eta_m = 0.0, eta_p = 0.0;
+            if (q > 1) {
+                double zs = 0.0;
+#pragma unroll
+                for (int j = 1; j <= QMAX; j++) {
+                    if (j == q) {
+#pragma unroll
+                        for (int s = 0; s < NPL; s++) { double a = z[j][s] * w[s]; zs += a * a; }
+                    }
+                }
+                double em = m.ecoef[q - 1] * m.fact[q] * sqrt(gsum<G>(zs, gm) / (double)n);
+                eta_m = 1.0 / (pow(1.3 * em, 1.0 / q) + 1e-6);
+            }
+            if (q < QMAX && ep_valid) {
+#pragma unroll
+                for (int s = 0; s < NPL; s++) t1[s] = e[s] - ep[s];
+                double epl = m.ecoef[q + 1] * wrms<G, NPL>(m, t1, w, gm);
+                eta_p = 1.0 / (pow(1.4 * epl, 1.0 / (q + 2)) + 1e-6);
+            }
+            double eta = eta_q;
+            int qn = q;
+            if (eta_m > eta) { eta = eta_m; qn = q - 1; }
+            if (eta_p > eta) { eta = eta_p; qn = q + 1; }
+            if (eta < ETA_THRESH) {
+                qwait = 2;
+            } else {
+                if (eta > ETA_MAX) eta = ETA_MAX;
+                if (qn == q + 1) {
+                    const double c_up = m.lcoef[q][q] / (double)(q + 1);
+#pragma unroll
+                    for (int j = 2; j <= QMAX; j++) {
+                        if (j == q + 1) {
+#pragma unroll
+                            for (int s = 0; s < NPL; s++) z[j][s] = e[s] * c_up;
+                        }
+                    }
+                }
+                q = qn;
+                h *= eta;
+                nord_rescale<NPL>(z, q, eta);
+                qwait = q + 1;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < NPL; s++) ep[s] = e[s];
+        ep_valid = true;
+    }
+    st.steps = nst;
+    if (status == ST_OK) {
+#pragma unroll
+        for (int s = 0; s < NPL; s++) {
+            int p = lane + G * s;
+            if (p < n) y_cell[__ldg(m.perm + p)] = z[0][s];
+        }
+    }
+    return status;
+}
+
+}  // namespace campdev

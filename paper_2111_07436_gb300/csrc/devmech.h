@@ -1,0 +1,95 @@
+// Device-side mechanism tables, shared by the host compiler (mech.cpp) and the
+// CUDA kernels.  Every array lives in one device allocation; the struct is
+// passed to kernels by value (it sits in the kernel-parameter constant bank).
+//
+// All species indices here are POSITIONS in the elimination order chosen by
+// the compiler (position p holds species perm[p]); only the state/env/atol
+// loads and stores translate back to declaration order.
+#pragma once
+#include <stdint.h>
+
+#define CAMP_QMAX 5
+#define CAMP_MAXFAC 3  // at most 3 factors (with multiplicity) per rate term
+
+enum {
+    CAMP_P_ARRHENIUS = 0,
+    CAMP_P_TROE = 1,
+    CAMP_P_PHOTOLYSIS = 2,
+    CAMP_P_EMISSION = 3,
+    CAMP_P_LOSS = 4,
+    CAMP_P_HENRY = 5,
+    CAMP_P_AQREV = 6
+};
+
+// LU op encoding for the sparse (row-wise) part of the factorisation
+#define CAMP_OP_DIV 0x80000000u
+#define CAMP_OP_TGT(op) ((int)((op)&0xFFFFu))
+#define CAMP_OP_SRC(op) ((int)(((op) >> 16) & 0x7FFFu))
+
+struct DevMech {
+    int n;            // species
+    int R;            // process instances
+    int n_env;
+    int env_sec_base; // env index of section 0's radius
+    int npl32;        // ceil(n / 32)
+
+    // --- rate constants (process order) ---
+    const int *rtype;     // [R]
+    const double *rpar;   // [R][8]
+    const int *rslot;     // [R] env slot (runtime types) or section (section types)
+    const int *rnr;       // [R] total reactant multiplicity
+    const int *rnp;       // [R] total product multiplicity (reversible types)
+
+    // --- rate terms r_k = kf prod(fwd) - kr prod(rev), positions, -1 = none ---
+    const int *rfac;      // [R][6]: 3 forward then 3 reverse
+
+    // --- forcing gather, by position ---
+    const int *fptr;      // [n+1]
+    const int *fk;        // [nf] process index
+    const double *fc;     // [nf] net stoichiometric coefficient
+
+    // --- Jacobian gather, by Jacobian non-zero ---
+    int nnzJ;
+    const int *jptr;      // [nnzJ+1]
+    const int *jdst;      // [nnzJ] LU storage offset; the diagonal is flagged by jdiag
+    const int *jdiag;     // [nnzJ] 1 on the diagonal
+    const int *jk;        // [nj] process k (forward constant) or -(k+1) (reverse constant)
+    const int *jo;        // [nj][2] other factor positions, -1 = none
+    const double *jc;     // [nj] coefficient (net stoich x multiplicity, signed)
+
+    // --- LU storage: sparse rows [0, nsp) then a dense trailing block ---
+    int nlu;              // storage entries
+    int d;                // first position of the dense block (= n when there is none)
+    int D;                // dense block size n - d
+    int LD;               // dense block row stride (odd, to spread shared-memory banks)
+    int dbase;            // storage offset of the dense block
+
+    // factorisation of the sparse part, row by row (up-looking), by level
+    int n_flev;
+    const int *flev_ptr;  // [n_flev+1] into frow
+    const int *frow;      // rows (positions)
+    const int *fops_ptr;  // [n+1]
+    const uint32_t *fops; // encoded DIV/UPD ops
+
+    // forward substitution of the sparse part: rows by level (flev), entries
+    const int *sl_ptr;    // [n+1]
+    const int *sl_off;    // storage offset of L(i,k)
+    const int *sl_col;    // k
+
+    // backward substitution of the sparse rows (i < d), by level
+    int n_blev;
+    const int *blev_ptr;  // [n_blev+1] into brow
+    const int *brow;
+    const int *su_ptr;    // [n+1]
+    const int *su_off;    // storage offset of U(i,j), j > i
+    const int *su_col;    // j
+    const int *udiag;     // [n] storage offset of U(i,i) for sparse rows
+
+    const int *perm;      // [n] position -> species (declaration order)
+
+    // BDF coefficients: l-vector of prod_{i=1..q}(1 + x/i), local-error
+    // constants 1/((q+1) l_1(q)), factorials
+    double lcoef[CAMP_QMAX + 2][CAMP_QMAX + 2];
+    double ecoef[CAMP_QMAX + 2];
+    double fact[CAMP_QMAX + 2];
+};

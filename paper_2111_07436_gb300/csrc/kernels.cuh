@@ -1,0 +1,149 @@
+// Kernels of the batched solve and of its per-step test entry points,
+// templated on the LU precision LT (float: mixed form, double: plain form),
+// the lanes per cell G and the register slots per lane NPL.
+#pragma once
+#include "cellsolve.cuh"
+#include "launch.h"
+
+namespace campdev {
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if (G == 32) return 0xffffffffu;
+    const int sub = (threadIdx.x & 31) / G;
+    return ((1u << G) - 1u) << (sub * G);
+}
+
+// The whole solve: each group of G lanes integrates one cell at a time.  With
+// `queue` null the mapping is static (cell = block * cpb + group); otherwise
+// the groups take cells from the counter until it passes n_cells.
+template <int G, int NPL, typename LT>
+__global__ void __launch_bounds__(256) k_solve(DevMech m, SolveArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    const int group = threadIdx.x / G, lane = threadIdx.x % G;
+    const unsigned gm = group_mask<G>();
+    const CellSmem L = cell_smem(m.n, m.R, m.nlu, (int)sizeof(LT));
+    CellPtr<LT> c(smem + group * L.bytes, m);
+    long long cell = a.queue ? 0 : (long long)blockIdx.x * a.cpb + group;
+    for (;;) {
+        if (a.queue) {
+            unsigned long long v = 0;
+            if (lane == 0) v = atomicAdd(a.queue, 1ull);
+            cell = (long long)__shfl_sync(gm, v, 0, G);
+        }
+        if (cell >= a.n_cells) break;
+        CellStats st;
+        int s = integrate_cell<G, NPL, LT>(m, c, a.state + cell * m.n, a.env + cell * m.n_env, a.dt,
+                                           a.rtol, a.atol, a.atol_len, a.max_steps, a.hmin_frac,
+                                           lane, gm, st);
+        if (lane == 0) {
+            a.status[cell] = s;
+            if (a.stats) {
+                int32_t *o = a.stats + 5 * cell;
+                o[0] = st.steps;
+                o[1] = st.newton;
+                o[2] = st.jac;
+                o[3] = st.errfail;
+                o[4] = st.ordsum;
+            }
+        }
+        if (!a.queue) break;
+        __syncwarp(gm);
+    }
+}
+
+// Rate constants of every process of every cell, [cell][R] in process order.
+template <int G>
+__global__ void k_rates(DevMech m, long long n_cells, const double *env, double *kf, double *kr) {
+    const long long cell = (long long)blockIdx.x * (blockDim.x / G) + threadIdx.x / G;
+    const int lane = threadIdx.x % G;
+    if (cell >= n_cells) return;
+    for (int k = lane; k < m.R; k += G) {
+        double a, b;
+        rate_constant(m, k, env + cell * m.n_env, a, b);
+        kf[cell * m.R + k] = a;
+        kr[cell * m.R + k] = b;
+    }
+}
+
+template <int G, int NPL, typename LT>
+__device__ __forceinline__ void load_cell(const DevMech &m, const CellPtr<LT> &c, const double *y,
+                                          const double *env, double (&yr)[NPL], int lane, unsigned gm) {
+    for (int k = lane; k < m.R; k += G) {
+        double a, b;
+        rate_constant(m, k, env, a, b);
+        c.kf[k] = a;
+        c.kr[k] = b;
+    }
+#pragma unroll
+    for (int s = 0; s < NPL; s++) {
+        int p = lane + G * s;
+        yr[s] = p < m.n ? y[__ldg(m.perm + p)] : 0.0;
+        if (p < m.n) c.ys[p] = yr[s];
+    }
+    __syncwarp(gm);
+}
+
+// f(y) of every cell, [cell][n] in declaration order.
+template <int G, int NPL, typename LT>
+__global__ void k_forcing(DevMech m, long long n_cells, const double *state, const double *env,
+                          double *f_out) {
+    extern __shared__ __align__(16) char smem[];
+    const int group = threadIdx.x / G, lane = threadIdx.x % G;
+    const unsigned gm = group_mask<G>();
+    const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
+    if (cell >= n_cells) return;
+    const CellSmem L = cell_smem(m.n, m.R, m.nlu, (int)sizeof(LT));
+    CellPtr<LT> c(smem + group * L.bytes, m);
+    double y[NPL], f[NPL];
+    load_cell<G, NPL, LT>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
+    eval_f<G, NPL, LT>(m, c, y, f, lane, gm);
+#pragma unroll
+    for (int s = 0; s < NPL; s++) {
+        int p = lane + G * s;
+        if (p < m.n) f_out[cell * m.n + __ldg(m.perm + p)] = f[s];
+    }
+}
+
+// Jacobian values of every cell, [cell][nnzJ] in species-CSR order, computed
+// in precision LT (the assembly precision of the corresponding solve form).
+template <int G, int NPL, typename LT>
+__global__ void k_jacobian(DevMech m, long long n_cells, const double *state, const double *env,
+                           double *jac) {
+    extern __shared__ __align__(16) char smem[];
+    const int group = threadIdx.x / G, lane = threadIdx.x % G;
+    const unsigned gm = group_mask<G>();
+    const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
+    if (cell >= n_cells) return;
+    const CellSmem L = cell_smem(m.n, m.R, m.nlu, (int)sizeof(LT));
+    CellPtr<LT> c(smem + group * L.bytes, m);
+    double y[NPL];
+    load_cell<G, NPL, LT>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
+    assemble<G, LT>(m, c, 0.0, lane, gm, 1, jac + cell * (long long)m.nnzJ);
+}
+
+// Solve (I - gamma J(y)) x = b for every cell with the device LU in
+// precision LT; b and x [cell][n] in declaration order; status 4 on a
+// tiny pivot (x then left unwritten).
+template <int G, int NPL, typename LT>
+__global__ void k_lu_solve(DevMech m, long long n_cells, const double *state, const double *env,
+                           double gamma, const double *b, double *x, int *status) {
+    extern __shared__ __align__(16) char smem[];
+    const int group = threadIdx.x / G, lane = threadIdx.x % G;
+    const unsigned gm = group_mask<G>();
+    const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
+    if (cell >= n_cells) return;
+    const CellSmem L = cell_smem(m.n, m.R, m.nlu, (int)sizeof(LT));
+    CellPtr<LT> c(smem + group * L.bytes, m);
+    double y[NPL];
+    load_cell<G, NPL, LT>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
+    assemble<G, LT>(m, c, gamma, lane, gm, 0, nullptr);
+    bool ok = factor<G, LT>(m, c, lane, gm);
+    if (lane == 0) status[cell] = ok ? 0 : ST_SINGULAR;
+    if (!ok) return;
+    for (int p = lane; p < m.n; p += G) c.x[p] = (LT)b[cell * m.n + __ldg(m.perm + p)];
+    substitute<G, LT>(m, c, lane, gm);
+    for (int p = lane; p < m.n; p += G) x[cell * m.n + __ldg(m.perm + p)] = (double)c.x[p];
+}
+
+}  // namespace campdev

@@ -1,0 +1,50 @@
+// Host-side launch interface between the C ABI (capi.cu) and the kernels,
+// which are compiled in one translation unit per LU precision.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "devmech.h"
+
+struct SolveArgs {
+    long long n_cells;
+    double *state;
+    const double *env;
+    double dt, rtol;
+    const double *atol;
+    int atol_len;
+    int32_t *status;
+    int32_t *stats;
+    int max_steps;
+    double hmin_frac;
+    int cpb;                        // cells per block
+    unsigned long long *queue;      // work counter (persistent form) or null
+};
+
+// Register slots per lane instantiated for G = 32: a mechanism with n species
+// uses the smallest entry >= ceil(n / 32); n <= 256.
+int camp_pick_npl(int n);
+
+// Shared-memory bytes per cell for LU element size 4 or 8.
+int camp_cell_smem_bytes(const DevMech &m, int lu_elem);
+
+// Launchers (return a cudaError_t).  `lu_elem` 4 = FP32 J/LU, 8 = FP64.
+cudaError_t camp_launch_solve_f32(const DevMech &m, const SolveArgs &a, int grid, cudaStream_t s);
+cudaError_t camp_launch_solve_f64(const DevMech &m, const SolveArgs &a, int grid, cudaStream_t s);
+cudaError_t camp_occupancy_f32(const DevMech &m, int cpb, int *blocks_per_sm);
+cudaError_t camp_occupancy_f64(const DevMech &m, int cpb, int *blocks_per_sm);
+
+cudaError_t camp_launch_rates(const DevMech &m, long long n_cells, const double *env, double *kf,
+                              double *kr, cudaStream_t s);
+cudaError_t camp_launch_forcing(const DevMech &m, long long n_cells, const double *state,
+                                const double *env, double *f, cudaStream_t s);
+cudaError_t camp_launch_jacobian_f32(const DevMech &m, long long n_cells, const double *state,
+                                     const double *env, double *jac, cudaStream_t s);
+cudaError_t camp_launch_jacobian_f64(const DevMech &m, long long n_cells, const double *state,
+                                     const double *env, double *jac, cudaStream_t s);
+cudaError_t camp_launch_lu_solve_f32(const DevMech &m, long long n_cells, const double *state,
+                                     const double *env, double gamma, const double *b, double *x,
+                                     int *status, cudaStream_t s);
+cudaError_t camp_launch_lu_solve_f64(const DevMech &m, long long n_cells, const double *state,
+                                     const double *env, double gamma, const double *b, double *x,
+                                     int *status, cudaStream_t s);

@@ -1,0 +1,570 @@
+// Mechanism compiler (host, once per mechanism).
+//
+// CAMP paper Sect. 2.2: a mechanism is a set of processes over the gas phase
+// and over every instance of an aerosol phase (Sect. 2.2.3: a process
+// declared on a phase is applied to each instance of it; here one instance per
+// section).  Table 1: each process declares the Jacobian elements it touches
+// (get_used_jacobian_elements) and receives the ids of its species and
+// Jacobian elements (update_ids).  This file does both, then orders the
+// unknowns, computes the LU fill and emits flat device tables.
+#include "mech.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+
+#include "json.hpp"
+
+namespace camp {
+using campjson::Value;
+
+static const double kBoltzmann = 1.380649e-23;
+
+static int type_code(const std::string &t) {
+    if (t == "ARRHENIUS") return CAMP_P_ARRHENIUS;
+    if (t == "TROE") return CAMP_P_TROE;
+    if (t == "PHOTOLYSIS") return CAMP_P_PHOTOLYSIS;
+    if (t == "EMISSION") return CAMP_P_EMISSION;
+    if (t == "FIRST_ORDER_LOSS") return CAMP_P_LOSS;
+    if (t == "HL_PHASE_TRANSFER") return CAMP_P_HENRY;
+    if (t == "AQUEOUS_REVERSIBLE") return CAMP_P_AQREV;
+    throw std::runtime_error("unknown reaction type '" + t + "'");
+}
+
+static bool is_runtime(int t) {
+    return t == CAMP_P_PHOTOLYSIS || t == CAMP_P_EMISSION || t == CAMP_P_LOSS;
+}
+static bool is_sectioned(int t) { return t == CAMP_P_HENRY || t == CAMP_P_AQREV; }
+
+template <class T>
+static void add_coef(std::vector<std::pair<int, T>> &v, int idx, T c) {
+    for (auto &e : v)
+        if (e.first == idx) { e.second += c; return; }
+    v.emplace_back(idx, c);
+}
+
+static int as_multiplicity(double v, const char *what) {
+    if (!(v >= 1.0) || v != std::floor(v) || v > 3.0)
+        throw std::runtime_error(std::string(what) + " must be an integer in 1..3");
+    return (int)v;
+}
+
+// ---- species and processes -------------------------------------------------
+static void read_processes(const Value &root, HostMech &h) {
+    const Value &sp = root.at("species");
+    if (sp.kind != Value::Array) throw std::runtime_error("'species' must be an array");
+    for (auto &s : sp.arr) h.species.push_back(s.string("name"));
+    h.n_gas = (int)h.species.size();
+    std::vector<std::string> phase;
+    if (const Value *a = root.find("aerosol")) {
+        h.n_sections = (int)a->number("sections");
+        if (h.n_sections < 0 || h.n_sections > 1024) throw std::runtime_error("bad section count");
+        const Value &ph = root.at("phases").at(a->string("phase"));
+        for (auto &p : ph.arr) phase.push_back(p.string("name"));
+        for (int b = 0; b < h.n_sections; b++)
+            for (auto &p : phase) h.species.push_back("bin" + std::to_string(b) + "." + p);
+    }
+    h.n = (int)h.species.size();
+    std::unordered_map<std::string, int> index;
+    for (int i = 0; i < h.n; i++)
+        if (!index.emplace(h.species[i], i).second)
+            throw std::runtime_error("duplicate species '" + h.species[i] + "'");
+    auto idx = [&](const std::string &name) {
+        auto it = index.find(name);
+        if (it == index.end()) throw std::runtime_error("unknown species '" + name + "'");
+        return it->second;
+    };
+
+    const Value &rx = root.at("reactions");
+    if (rx.kind != Value::Array) throw std::runtime_error("'reactions' must be an array");
+    int n_runtime = 0;
+    for (auto &r : rx.arr) n_runtime += is_runtime(type_code(r.string("type")));
+    h.env_sec_base = 2 + n_runtime;
+    h.n_env = h.env_sec_base + 3 * h.n_sections;
+
+    int slot = 2;
+    for (auto &r : rx.arr) {
+        int t = type_code(r.string("type"));
+        if (is_sectioned(t)) {
+            for (int b = 0; b < h.n_sections; b++) {
+                std::string pre = "bin" + std::to_string(b) + ".";
+                Process p;
+                p.type = t;
+                p.slot = b;
+                if (t == CAMP_P_HENRY) {
+                    p.react.emplace_back(idx(r.string("gas")), 1);
+                    p.prod.emplace_back(idx(pre + r.string("aqueous")), 1.0);
+                    p.par[0] = r.number("H298");
+                    p.par[1] = r.number_or("C_H", 0.0);
+                    p.par[2] = r.number("alpha");
+                    p.par[3] = r.number("Dg");
+                    p.par[4] = r.number("MW");
+                } else {
+                    for (auto &kv : r.at("reactants").obj)
+                        add_coef(p.react, idx(pre + kv.first), as_multiplicity(kv.second.num, "stoichiometry"));
+                    for (auto &kv : r.at("products").obj)
+                        add_coef(p.prod, idx(pre + kv.first), (double)as_multiplicity(kv.second.num, "stoichiometry"));
+                    p.par[0] = r.number("A");
+                    p.par[1] = r.number_or("C", 0.0);
+                    p.par[2] = r.number("kr");
+                }
+                h.procs.push_back(p);
+            }
+            continue;
+        }
+        Process p;
+        p.type = t;
+        if (t == CAMP_P_EMISSION) {
+            p.prod.emplace_back(idx(r.string("species")), 1.0);
+        } else if (t == CAMP_P_LOSS) {
+            p.react.emplace_back(idx(r.string("species")), 1);
+        } else {
+            for (auto &kv : r.at("reactants").obj)
+                add_coef(p.react, idx(kv.first), as_multiplicity(kv.second.num, "stoichiometry"));
+            if (const Value *pr = r.find("products"))
+                for (auto &kv : pr->obj) add_coef(p.prod, idx(kv.first), kv.second.num);
+            if (t == CAMP_P_ARRHENIUS) {
+                p.par[0] = r.number("A");
+                p.par[1] = r.number_or("B", 0.0);
+                p.par[2] = r.find("C") ? r.number("C") : -r.number_or("Ea", 0.0) / kBoltzmann;
+                p.par[3] = r.number_or("D", 300.0);
+                p.par[4] = r.number_or("E", 0.0);
+            } else if (t == CAMP_P_TROE) {
+                p.par[0] = r.number("k0_A");
+                p.par[1] = r.number_or("k0_B", 0.0);
+                p.par[2] = r.number_or("k0_C", 0.0);
+                p.par[3] = r.number("kinf_A");
+                p.par[4] = r.number_or("kinf_B", 0.0);
+                p.par[5] = r.number_or("kinf_C", 0.0);
+                p.par[6] = r.number_or("Fc", 0.6);
+                p.par[7] = r.number_or("N", 1.0);
+            }
+        }
+        if (is_runtime(t)) p.slot = slot++;
+        h.procs.push_back(p);
+    }
+    for (auto &p : h.procs) {
+        int nr = 0, np = 0;
+        for (auto &e : p.react) nr += e.second;
+        if (nr > CAMP_MAXFAC) throw std::runtime_error("more than 3 reactant factors in one process");
+        if (p.reversible()) {
+            for (auto &e : p.prod) np += (int)e.second;
+            if (np > CAMP_MAXFAC) throw std::runtime_error("more than 3 product factors in a reversible process");
+        }
+    }
+}
+
+// ---- integer structure -----------------------------------------------------
+static std::vector<int> dependence(const Process &p) {  // species entering r_k
+    std::vector<int> d;
+    for (auto &e : p.react) if (std::find(d.begin(), d.end(), e.first) == d.end()) d.push_back(e.first);
+    if (p.reversible())
+        for (auto &e : p.prod) if (std::find(d.begin(), d.end(), e.first) == d.end()) d.push_back(e.first);
+    return d;
+}
+static std::vector<int> touched(const Process &p) {   // rows of f it changes
+    std::vector<int> d;
+    for (auto &e : p.react) if (std::find(d.begin(), d.end(), e.first) == d.end()) d.push_back(e.first);
+    for (auto &e : p.prod) if (std::find(d.begin(), d.end(), e.first) == d.end()) d.push_back(e.first);
+    return d;
+}
+static double net_coef(const Process &p, int s) {
+    double v = 0.0;
+    for (auto &e : p.react) if (e.first == s) v -= e.second;
+    for (auto &e : p.prod) if (e.first == s) v += e.second;
+    return v;
+}
+
+static void build_structure(HostMech &h) {
+    const int n = h.n;
+    std::vector<char> pat((size_t)n * n, 0);
+    for (int i = 0; i < n; i++) pat[(size_t)i * n + i] = 1;
+    for (auto &p : h.procs)
+        for (int j : dependence(p))
+            for (int i : touched(p)) pat[(size_t)i * n + j] = 1;
+    h.rowptr.assign(1, 0);
+    h.colidx.clear();
+    for (int i = 0; i < n; i++) {
+        for (int j = 0; j < n; j++) if (pat[(size_t)i * n + j]) h.colidx.push_back(j);
+        h.rowptr.push_back((int)h.colidx.size());
+    }
+    auto csr_pos = [&](int i, int j) {
+        auto b = h.colidx.begin() + h.rowptr[i], e = h.colidx.begin() + h.rowptr[i + 1];
+        auto it = std::lower_bound(b, e, j);
+        return (int)(it - h.colidx.begin());
+    };
+    h.rxn_map.clear();
+    for (auto &p : h.procs)
+        for (int j : dependence(p))
+            for (int i : touched(p)) h.rxn_map.push_back(csr_pos(i, j));
+
+    // exact minimum degree on pattern | pattern^T without the diagonal
+    std::vector<char> adj((size_t)n * n, 0);
+    std::vector<int> deg(n, 0);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++)
+            if (i != j && (pat[(size_t)i * n + j] || pat[(size_t)j * n + i])) adj[(size_t)i * n + j] = 1;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) deg[i] += adj[(size_t)i * n + j];
+    std::vector<char> alive(n, 1);
+    h.perm.clear();
+    std::vector<int> nb;
+    for (int step = 0; step < n; step++) {
+        int v = -1;
+        for (int a = 0; a < n; a++)
+            if (alive[a] && (v < 0 || deg[a] < deg[v])) v = a;
+        h.perm.push_back(v);
+        nb.clear();
+        for (int a = 0; a < n; a++) if (alive[a] && adj[(size_t)v * n + a]) nb.push_back(a);
+        for (int a : nb)
+            for (int b : nb)
+                if (a != b && !adj[(size_t)a * n + b]) { adj[(size_t)a * n + b] = 1; deg[a]++; }
+        for (int a : nb) { adj[(size_t)a * n + v] = 0; deg[a]--; }
+        alive[v] = 0;
+    }
+    h.iperm.assign(n, 0);
+    for (int k = 0; k < n; k++) h.iperm[h.perm[k]] = k;
+
+    // symbolic LU of the permuted pattern, no pivoting
+    std::vector<char> S((size_t)n * n, 0);
+    for (int i = 0; i < n; i++)
+        for (int q = h.rowptr[i]; q < h.rowptr[i + 1]; q++)
+            S[(size_t)h.iperm[i] * n + h.iperm[h.colidx[q]]] = 1;
+    for (int k = 0; k < n; k++)
+        for (int i = k + 1; i < n; i++) {
+            if (!S[(size_t)i * n + k]) continue;
+            for (int j = k + 1; j < n; j++)
+                if (S[(size_t)k * n + j]) S[(size_t)i * n + j] = 1;
+        }
+    h.lu_rowptr.assign(1, 0);
+    h.lu_colidx.clear();
+    for (int i = 0; i < n; i++) {
+        for (int j = 0; j < n; j++) if (S[(size_t)i * n + j]) h.lu_colidx.push_back(j);
+        h.lu_rowptr.push_back((int)h.lu_colidx.size());
+    }
+    h.level_fwd.assign(n, 0);
+    for (int i = 0; i < n; i++) {
+        int lv = -1;
+        for (int q = h.lu_rowptr[i]; q < h.lu_rowptr[i + 1]; q++) {
+            int k = h.lu_colidx[q];
+            if (k < i) lv = std::max(lv, h.level_fwd[k]);
+        }
+        h.level_fwd[i] = lv + 1;
+    }
+    h.level_bwd.assign(n, 0);
+    for (int i = n - 1; i >= 0; i--) {
+        int lv = -1;
+        for (int q = h.lu_rowptr[i]; q < h.lu_rowptr[i + 1]; q++) {
+            int j = h.lu_colidx[q];
+            if (j > i) lv = std::max(lv, h.level_bwd[j]);
+        }
+        h.level_bwd[i] = lv + 1;
+    }
+}
+
+// ---- device tables -----------------------------------------------------------
+static void build_tables(HostMech &h) {
+    const int n = h.n, R = (int)h.procs.size();
+    const auto &ip = h.iperm;
+
+    // rate constants and rate terms
+    h.rtype.resize(R); h.rslot.resize(R); h.rnr.resize(R); h.rnp.resize(R);
+    h.rpar.assign((size_t)R * 8, 0.0);
+    h.rfac.assign((size_t)R * 6, -1);
+    for (int k = 0; k < R; k++) {
+        const Process &p = h.procs[k];
+        h.rtype[k] = p.type;
+        h.rslot[k] = p.slot;
+        for (int i = 0; i < 8; i++) h.rpar[(size_t)k * 8 + i] = p.par[i];
+        int c = 0, nr = 0, np = 0;
+        for (auto &e : p.react)
+            for (int m = 0; m < e.second; m++) { h.rfac[(size_t)k * 6 + c++] = ip[e.first]; nr++; }
+        if (p.reversible()) {
+            c = 3;
+            for (auto &e : p.prod)
+                for (int m = 0; m < (int)e.second; m++) { h.rfac[(size_t)k * 6 + c++] = ip[e.first]; np++; }
+        }
+        h.rnr[k] = nr;
+        h.rnp[k] = np;
+    }
+
+    // forcing gather by position
+    std::vector<std::vector<std::pair<int, double>>> fl(n);
+    for (int k = 0; k < R; k++)
+        for (int s : touched(h.procs[k])) {
+            double nu = net_coef(h.procs[k], s);
+            if (nu != 0.0) fl[ip[s]].emplace_back(k, nu);
+        }
+    h.fptr.assign(1, 0);
+    h.fk.clear(); h.fc.clear();
+    for (int p = 0; p < n; p++) {
+        for (auto &e : fl[p]) { h.fk.push_back(e.first); h.fc.push_back(e.second); }
+        h.fptr.push_back((int)h.fk.size());
+    }
+
+    // dense trailing block: smallest d with D = n - d >= 8 and fill density >= 0.75
+    h.d = n;
+    for (int d = 0; d + 8 <= n; d++) {
+        long long cnt = 0;
+        for (int i = d; i < n; i++)
+            for (int q = h.lu_rowptr[i]; q < h.lu_rowptr[i + 1]; q++) cnt += (h.lu_colidx[q] >= d);
+        if ((double)cnt >= 0.75 * (double)(n - d) * (double)(n - d)) { h.d = d; break; }
+    }
+    h.D = n - h.d;
+    h.LD = h.D % 2 ? h.D : h.D + 1;
+
+    // storage offsets: sparse rows < d, the L21 part of rows >= d, then the block
+    std::vector<int> lu_off(h.lu_colidx.size(), -1);
+    int nsp = 0;
+    for (int i = 0; i < n; i++)
+        for (int q = h.lu_rowptr[i]; q < h.lu_rowptr[i + 1]; q++)
+            if (i < h.d || h.lu_colidx[q] < h.d) lu_off[q] = nsp++;
+    h.dbase = (nsp + 3) & ~3;
+    for (int i = h.d; i < n; i++)
+        for (int q = h.lu_rowptr[i]; q < h.lu_rowptr[i + 1]; q++)
+            if (h.lu_colidx[q] >= h.d) lu_off[q] = h.dbase + (i - h.d) * h.LD + (h.lu_colidx[q] - h.d);
+    h.nlu = h.dbase + h.D * h.LD;
+    if (h.nlu > 32767) throw std::runtime_error("LU storage exceeds 32767 entries");
+    auto off = [&](int i, int j) {
+        auto b = h.lu_colidx.begin() + h.lu_rowptr[i], e = h.lu_colidx.begin() + h.lu_rowptr[i + 1];
+        auto it = std::lower_bound(b, e, j);
+        if (it == e || *it != j) throw std::logic_error("entry outside the LU pattern");
+        return lu_off[it - h.lu_colidx.begin()];
+    };
+
+    // Jacobian gather by species-CSR non-zero
+    const int nnzJ = (int)h.colidx.size();
+    std::vector<std::vector<int>> jent(nnzJ);  // indices into entry arrays
+    std::vector<int> ek, eo;
+    std::vector<double> ec;
+    auto csr_pos = [&](int i, int j) {
+        auto b = h.colidx.begin() + h.rowptr[i], e = h.colidx.begin() + h.rowptr[i + 1];
+        return (int)(std::lower_bound(b, e, j) - h.colidx.begin());
+    };
+    for (int k = 0; k < R; k++) {
+        const Process &p = h.procs[k];
+        for (int j : dependence(p)) {
+            for (int i : touched(p)) {
+                double nu = net_coef(p, i);
+                if (nu == 0.0) continue;
+                int t = csr_pos(i, j);
+                // forward term: kf * prod(reactant factors)
+                for (int side = 0; side < 2; side++) {
+                    if (side == 1 && !p.reversible()) break;
+                    const int *fac = &h.rfac[(size_t)k * 6 + 3 * side];
+                    int mult = 0;
+                    for (int m = 0; m < 3; m++) mult += (fac[m] == ip[j]);
+                    if (!mult) continue;
+                    int others[2] = {-1, -1}, no = 0;
+                    bool skipped = false;
+                    for (int m = 0; m < 3; m++) {
+                        if (fac[m] < 0) continue;
+                        if (fac[m] == ip[j] && !skipped) { skipped = true; continue; }
+                        others[no++] = fac[m];
+                    }
+                    jent[t].push_back((int)ek.size());
+                    ek.push_back(side == 0 ? k : -(k + 1));
+                    eo.push_back(others[0]);
+                    eo.push_back(others[1]);
+                    ec.push_back(side == 0 ? nu * mult : -nu * mult);
+                }
+            }
+        }
+    }
+    h.jptr.assign(1, 0);
+    h.jdst.resize(nnzJ); h.jdiag.resize(nnzJ);
+    h.jk.clear(); h.jo.clear(); h.jc.clear();
+    for (int i = 0; i < n; i++)
+        for (int q = h.rowptr[i]; q < h.rowptr[i + 1]; q++) {
+            int j = h.colidx[q];
+            h.jdst[q] = off(ip[i], ip[j]);
+            h.jdiag[q] = (i == j);
+            for (int e : jent[q]) {
+                h.jk.push_back(ek[e]);
+                h.jo.push_back(eo[2 * e]);
+                h.jo.push_back(eo[2 * e + 1]);
+                h.jc.push_back(ec[e]);
+            }
+            h.jptr.push_back((int)h.jk.size());
+        }
+
+    // sparse factorisation ops, row by row; levels: sparse rows by level, then
+    // every block row in one final level (they only need sparse pivots)
+    h.fops_ptr.assign(1, 0);
+    h.fops.clear();
+    h.factor_updates = 0;
+    for (int i = 0; i < n; i++) {
+        for (int q = h.lu_rowptr[i]; q < h.lu_rowptr[i + 1]; q++) {
+            int k = h.lu_colidx[q];
+            if (k >= i || k >= h.d) continue;
+            h.fops.push_back(CAMP_OP_DIV | ((uint32_t)off(k, k) << 16) | (uint32_t)off(i, k));
+            for (int r = h.lu_rowptr[k]; r < h.lu_rowptr[k + 1]; r++) {
+                int j = h.lu_colidx[r];
+                if (j <= k) continue;
+                h.fops.push_back(((uint32_t)off(k, j) << 16) | (uint32_t)off(i, j));
+                h.factor_updates++;
+            }
+        }
+        h.fops_ptr.push_back((int)h.fops.size());
+    }
+    for (long long k = 0; k < h.D; k++) h.factor_updates += (h.D - 1 - k) * (h.D - 1 - k);
+    // algorithmic flop counts (structure only, independent of the storage)
+    h.flops_forcing = 2LL * (long long)h.fk.size();
+    for (int k = 0; k < R; k++) {
+        int nf = 0, nb = 0;
+        for (int m2 = 0; m2 < 3; m2++) nf += h.rfac[(size_t)k * 6 + m2] >= 0;
+        for (int m2 = 3; m2 < 6; m2++) nb += h.rfac[(size_t)k * 6 + m2] >= 0;
+        h.flops_forcing += nf + (h.procs[k].reversible() ? nb + 1 : 0);
+    }
+    h.flops_jacobian = 2LL * (long long)h.colidx.size();
+    for (size_t e = 0; e < h.jk.size(); e++)
+        h.flops_jacobian += 2 + (h.jo[2 * e] >= 0) + (h.jo[2 * e + 1] >= 0);
+    h.flops_factor = 0;
+    {
+        std::vector<int> lower(n, 0), upper(n, 0);
+        for (int i = 0; i < n; i++)
+            for (int q = h.lu_rowptr[i]; q < h.lu_rowptr[i + 1]; q++) {
+                int j = h.lu_colidx[q];
+                if (j < i) lower[j]++;   // column j of L
+                if (j > i) upper[i]++;   // row i of U
+            }
+        for (int k = 0; k < n; k++) h.flops_factor += 2LL * lower[k] * upper[k] + lower[k];
+    }
+    h.flops_solve = 2LL * ((long long)h.lu_colidx.size() - n) + n;
+    int maxl = -1;
+    for (int i = 0; i < h.d; i++) maxl = std::max(maxl, h.level_fwd[i]);
+    h.flev_ptr.assign(1, 0);
+    h.frow.clear();
+    for (int l = 0; l <= maxl; l++) {
+        for (int i = 0; i < h.d; i++) if (h.level_fwd[i] == l) h.frow.push_back(i);
+        h.flev_ptr.push_back((int)h.frow.size());
+    }
+    if (h.D > 0) {
+        for (int i = h.d; i < n; i++) h.frow.push_back(i);
+        h.flev_ptr.push_back((int)h.frow.size());
+    }
+
+    // substitution lists
+    h.sl_ptr.assign(1, 0);
+    h.sl_off.clear(); h.sl_col.clear();
+    h.su_ptr.assign(1, 0);
+    h.su_off.clear(); h.su_col.clear();
+    h.udiag.assign(n, -1);
+    for (int i = 0; i < n; i++) {
+        for (int q = h.lu_rowptr[i]; q < h.lu_rowptr[i + 1]; q++) {
+            int j = h.lu_colidx[q];
+            if (j < i && j < h.d) { h.sl_off.push_back(off(i, j)); h.sl_col.push_back(j); }
+            if (i < h.d && j > i) { h.su_off.push_back(off(i, j)); h.su_col.push_back(j); }
+            if (i < h.d && j == i) h.udiag[i] = off(i, i);
+        }
+        h.sl_ptr.push_back((int)h.sl_off.size());
+        h.su_ptr.push_back((int)h.su_off.size());
+    }
+    std::vector<int> bl(n, 0);
+    int maxb = -1;
+    for (int i = h.d - 1; i >= 0; i--) {
+        int lv = -1;
+        for (int q = h.lu_rowptr[i]; q < h.lu_rowptr[i + 1]; q++) {
+            int j = h.lu_colidx[q];
+            if (j > i && j < h.d) lv = std::max(lv, bl[j]);
+        }
+        bl[i] = lv + 1;
+        maxb = std::max(maxb, bl[i]);
+    }
+    h.blev_ptr.assign(1, 0);
+    h.brow.clear();
+    for (int l = 0; l <= maxb; l++) {
+        for (int i = 0; i < h.d; i++) if (bl[i] == l) h.brow.push_back(i);
+        h.blev_ptr.push_back((int)h.brow.size());
+    }
+}
+
+HostMech compile_mechanism(const char *json, size_t len) {
+    Value root = campjson::parse(json, len);
+    HostMech h;
+    read_processes(root, h);
+    if (h.n < 1) throw std::runtime_error("mechanism has no species");
+    build_structure(h);
+    build_tables(h);
+    return h;
+}
+
+void bdf_coefficients(DevMech &dm) {
+    for (int q = 0; q <= CAMP_QMAX + 1; q++) {
+        double c[CAMP_QMAX + 2] = {1.0, 0, 0, 0, 0, 0, 0};
+        for (int i = 1; i <= q; i++)  // c(x) *= (1 + x / i)
+            for (int j = i; j >= 1; j--) c[j] += c[j - 1] / (double)i;
+        for (int j = 0; j <= CAMP_QMAX + 1; j++) dm.lcoef[q][j] = c[j];
+        dm.ecoef[q] = q > 0 ? 1.0 / ((double)(q + 1) * c[1]) : 0.0;
+    }
+    dm.fact[0] = 1.0;
+    for (int i = 1; i <= CAMP_QMAX + 1; i++) dm.fact[i] = dm.fact[i - 1] * i;
+}
+
+// ---- packing ---------------------------------------------------------------
+namespace {
+struct Packer {
+    std::vector<unsigned char> img;
+    const unsigned char *base;
+    template <class T>
+    const T *put(const std::vector<T> &v) {
+        size_t off = (img.size() + 15) & ~(size_t)15;
+        img.resize(off + std::max<size_t>(v.size() * sizeof(T), 16), 0);
+        if (!v.empty()) std::copy((const unsigned char *)v.data(),
+                                  (const unsigned char *)v.data() + v.size() * sizeof(T), img.data() + off);
+        return reinterpret_cast<const T *>(reinterpret_cast<uintptr_t>(base) + off);
+    }
+};
+}  // namespace
+
+std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const unsigned char *base) {
+    Packer pk{{}, base};
+    dm.n = h.n;
+    dm.R = (int)h.procs.size();
+    dm.n_env = h.n_env;
+    dm.env_sec_base = h.env_sec_base;
+    dm.npl32 = (h.n + 31) / 32;
+    dm.rtype = pk.put(h.rtype);
+    dm.rpar = pk.put(h.rpar);
+    dm.rslot = pk.put(h.rslot);
+    dm.rnr = pk.put(h.rnr);
+    dm.rnp = pk.put(h.rnp);
+    dm.rfac = pk.put(h.rfac);
+    dm.fptr = pk.put(h.fptr);
+    dm.fk = pk.put(h.fk);
+    dm.fc = pk.put(h.fc);
+    dm.nnzJ = (int)h.colidx.size();
+    dm.jptr = pk.put(h.jptr);
+    dm.jdst = pk.put(h.jdst);
+    dm.jdiag = pk.put(h.jdiag);
+    dm.jk = pk.put(h.jk);
+    dm.jo = pk.put(h.jo);
+    dm.jc = pk.put(h.jc);
+    dm.nlu = h.nlu;
+    dm.d = h.d;
+    dm.D = h.D;
+    dm.LD = h.LD;
+    dm.dbase = h.dbase;
+    dm.n_flev = (int)h.flev_ptr.size() - 1;
+    dm.flev_ptr = pk.put(h.flev_ptr);
+    dm.frow = pk.put(h.frow);
+    dm.fops_ptr = pk.put(h.fops_ptr);
+    dm.fops = pk.put(h.fops);
+    dm.sl_ptr = pk.put(h.sl_ptr);
+    dm.sl_off = pk.put(h.sl_off);
+    dm.sl_col = pk.put(h.sl_col);
+    dm.n_blev = (int)h.blev_ptr.size() - 1;
+    dm.blev_ptr = pk.put(h.blev_ptr);
+    dm.brow = pk.put(h.brow);
+    dm.su_ptr = pk.put(h.su_ptr);
+    dm.su_off = pk.put(h.su_off);
+    dm.su_col = pk.put(h.su_col);
+    dm.udiag = pk.put(h.udiag);
+    dm.perm = pk.put(h.perm);
+    bdf_coefficients(dm);
+    return pk.img;
+}
+
+}  // namespace camp

@@ -1,0 +1,64 @@
+// Mechanism compiler: JSON text -> processes -> sparsity, ordering, symbolic
+// LU and the flat device tables (CAMP paper Table 1: get_used_jacobian_elements
+// and update_ids happen here, once per mechanism, on the host).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "devmech.h"
+
+namespace camp {
+
+struct Process {
+    int type = 0;
+    std::vector<std::pair<int, int>> react;    // (species, multiplicity), distinct
+    std::vector<std::pair<int, double>> prod;  // (species, yield), distinct
+    double par[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int slot = -1;                             // env slot or section
+    bool reversible() const { return type == CAMP_P_HENRY || type == CAMP_P_AQREV; }
+};
+
+// Host image of one compiled mechanism.  Integer structure follows the rules
+// in include/camp.h (camp_mech_structure); the device tables mirror DevMech.
+struct HostMech {
+    std::vector<std::string> species;
+    int n = 0, n_gas = 0, n_env = 0, n_sections = 0, env_sec_base = 0;
+    std::vector<Process> procs;
+
+    // integer structure (species numbering except the LU, which is permuted)
+    std::vector<int> rowptr, colidx, rxn_map, perm, iperm;
+    std::vector<int> lu_rowptr, lu_colidx, level_fwd, level_bwd;
+
+    // device tables
+    std::vector<int> rtype, rslot, rnr, rnp, rfac;
+    std::vector<double> rpar;
+    std::vector<int> fptr, fk;
+    std::vector<double> fc;
+    std::vector<int> jptr, jdst, jdiag, jk, jo;
+    std::vector<double> jc;
+    int nlu = 0, d = 0, D = 0, LD = 0, dbase = 0;
+    std::vector<int> flev_ptr, frow, fops_ptr;
+    std::vector<uint32_t> fops;
+    std::vector<int> sl_ptr, sl_off, sl_col;
+    std::vector<int> blev_ptr, brow, su_ptr, su_off, su_col, udiag;
+    long long factor_updates = 0;  // multiply-adds one device factorisation executes
+    // algorithmic work of the method, from the symbolic structure
+    long long flops_forcing = 0;   // one f(y): rate products + stoichiometric sums
+    long long flops_jacobian = 0;  // one J assembly into I - gamma J
+    long long flops_factor = 0;    // one sparse LU factorisation (2 per update + divisions)
+    long long flops_solve = 0;     // one pair of triangular solves
+};
+
+// Throws std::runtime_error with a message on malformed input.
+HostMech compile_mechanism(const char *json, size_t len);
+
+// Fill the coefficient arrays of a DevMech (host-side arithmetic).
+void bdf_coefficients(DevMech &dm);
+
+// Pack all device tables into one byte image; `dm` receives offsets
+// relative to `base` (pointers are rebased once the image is on the device).
+std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const unsigned char *base);
+
+}  // namespace camp

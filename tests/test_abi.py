@@ -1,0 +1,60 @@
+"""The C ABI library builds, loads and exports every declared entry point
+(no GPU: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2111_07436_gb300 import build, camp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    text = open(os.path.join(ROOT, "include", "camp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(camp_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared()
+    assert "camp_solve" in names and "camp_mech_load" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    assert set(declared()) <= set(camp.EXPORTS)
+
+
+def test_host_only_handle_refuses_to_solve():
+    from paper_2111_07436_gb300 import workloads as w
+    m = camp.Mechanism(w.workload(1).json(), device=False)
+    assert m.info.n_species == 8 and m.info.n_env == 7
+    assert m.species_index("B") == 1 and m.species_index("nope") == -1
+    L = camp.lib()
+    o = camp.SolveOpts()
+    L.camp_solve_opts_default(ctypes.byref(o), camp.VARIANT_MIXED)
+    fake = ctypes.c_void_p(16)  # never dereferenced: the handle is rejected first
+    rc = L.camp_solve(m._h, 4, fake, fake, 10.0, 1e-4, fake, 1, fake, ctypes.byref(o), None)
+    assert rc == -1 and b"without device tables" in L.camp_last_error()
+    rc = L.camp_solve(m._h, 4, fake, fake, -1.0, 1e-4, fake, 1, fake, ctypes.byref(o), None)
+    assert rc == -1 and b"dt" in L.camp_last_error()
+    rc = L.camp_solve(m._h, 4, fake, fake, 1.0, 1e-4, fake, 3, fake, ctypes.byref(o), None)
+    assert rc == -1 and b"atol_len" in L.camp_last_error()
+    assert L.camp_solve(m._h, 0, None, None, 1.0, 1e-4, None, 1, None, None, None) == 0
+
+
+def test_info_reports_the_dense_block():
+    from paper_2111_07436_gb300 import workloads as w
+    inf = camp.Mechanism(w.workload(2).json(), device=False).info
+    assert inf.n_species == 72 and inf.n_rxn == 186 and inf.n_env == 48
+    assert 0 < inf.dense_block <= 72 and inf.nnz_lu >= inf.nnz_jac
+    assert inf.smem_per_cell_fp64 > inf.smem_per_cell_mixed

@@ -1,0 +1,164 @@
+"""Whole solves on the GPU against the oracle, through the C ABI, for both
+forms (plain FP64; mixed FP32 J/LU with FP64 state and error test), static
+and persistent mappings, at small sizes in full and at the benchmark sizes on
+sampled cells; plus the edge cases of the method.  Parity rule and arbiter:
+tests/parity.py."""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_07436_gb300 import camp, workloads as w
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+FORMS = [(camp.VARIANT_FP64, False), (camp.VARIANT_MIXED, False), (camp.VARIANT_MIXED, True)]
+FORM_IDS = ["fp64-static", "mixed-static", "mixed-persistent"]
+
+
+def _gpu_solve(gm, y, env, dt, rtol, atol, variant, persistent, **kw):
+    import torch
+    ty = torch.tensor(y, device="cuda")
+    te = torch.tensor(env, device="cuda")
+    st = gm.solve(ty, te, dt, rtol, atol, variant=variant, persistent=persistent, **kw)
+    torch.cuda.synchronize()
+    return ty.cpu().numpy(), st.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def mechs(cuda):
+    out = {}
+    for k in (1, 2, 3):
+        wl = w.workload(k)
+        out[k] = (wl, camp.Mechanism(wl.json()), oracle.Mechanism(wl.json()))
+    return out
+
+
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+def test_small_mechanism_one_hour(mechs, form):
+    """One cell, 60 outer steps of 60 s; compared after every outer step."""
+    wl, gm, om = mechs[1]
+    y0, env = wl.inputs()
+    yg, yo = y0.copy(), y0.copy()
+    for step in range(wl.n_outer):
+        yg_new, st = _gpu_solve(gm, yg, env, wl.dt, wl.rtol, wl.atol, *form)
+        assert (st == 0).all()
+        yo_new, sto, _ = om.solve(yo, env, wl.dt, wl.rtol, wl.atol)
+        assert (sto == 0).all()
+        parity.check(om, yo, env, wl.dt, wl.rtol, wl.atol, yg_new, yo_new)
+        yg, yo = yg_new, yo_new
+
+
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+@pytest.mark.parametrize("k,C", [(2, 301), (3, 67)])
+def test_full_parity_small_batches(mechs, form, k, C):
+    wl, gm, om = mechs[k]
+    y0, env = wl.inputs(C)
+    yg, st = _gpu_solve(gm, y0, env, wl.dt, wl.rtol, wl.atol, *form)
+    yo, sto, _ = om.solve(y0, env, wl.dt, wl.rtol, wl.atol)
+    assert (st == 0).all() and (sto == 0).all()
+    parity.check(om, y0, env, wl.dt, wl.rtol, wl.atol, yg, yo)
+
+
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+@pytest.mark.parametrize("k,sample", [(2, 96), (3, 24)])
+def test_benchmark_size_sampled(mechs, form, k, sample):
+    """The full workload in one launch; a seeded sample of cells re-solved by
+    the oracle one by one."""
+    wl, gm, om = mechs[k]
+    y0, env = wl.inputs()
+    yg, st = _gpu_solve(gm, y0, env, wl.dt, wl.rtol, wl.atol, *form)
+    assert (st == 0).all()
+    idx = np.sort(np.random.default_rng(k).choice(wl.n_cells, sample, replace=False))
+    yo, sto, _ = om.solve(y0[idx], env[idx], wl.dt, wl.rtol, wl.atol)
+    assert (sto == 0).all()
+    parity.check(om, y0[idx], env[idx], wl.dt, wl.rtol, wl.atol, yg[idx], yo)
+
+
+def test_results_do_not_depend_on_batch_or_mapping(mechs):
+    """A cell's result is bit-identical alone, in a batch, under either
+    mapping and any cells-per-block."""
+    wl, gm, om = mechs[2]
+    y0, env = wl.inputs(200)
+    ref, _ = _gpu_solve(gm, y0, env, wl.dt, wl.rtol, wl.atol, camp.VARIANT_MIXED, True)
+    for persistent, cpb in ((False, 1), (False, 3), (True, 2)):
+        yg, _ = _gpu_solve(gm, y0, env, wl.dt, wl.rtol, wl.atol, camp.VARIANT_MIXED, persistent,
+                           cells_per_block=cpb)
+        assert np.array_equal(yg, ref)
+    alone, _ = _gpu_solve(gm, y0[17:18], env[17:18], wl.dt, wl.rtol, wl.atol, camp.VARIANT_MIXED, True)
+    assert np.array_equal(alone[0], ref[17])
+    shuffled = np.random.default_rng(1).permutation(200)
+    ys, _ = _gpu_solve(gm, y0[shuffled], env[shuffled], wl.dt, wl.rtol, wl.atol, camp.VARIANT_MIXED, True)
+    assert np.array_equal(ys, ref[shuffled])
+
+
+@pytest.mark.parametrize("variant", [camp.VARIANT_FP64, camp.VARIANT_MIXED])
+def test_edge_cases(mechs, variant):
+    import torch
+    wl, gm, om = mechs[2]
+    y0, env = wl.inputs(9)
+    # non-finite inputs: status 5, state untouched
+    y0[2, 5] = np.nan
+    env[4, 0] = np.inf
+    yg, st = _gpu_solve(gm, y0, env, wl.dt, wl.rtol, wl.atol, variant, False)
+    assert st[2] == 5 and st[4] == 5
+    assert np.isnan(yg[2, 5]) and np.array_equal(yg[4], y0[4])
+    assert (st[[0, 1, 3, 5, 6, 7, 8]] == 0).all()
+    # too few steps allowed: status 1, state untouched
+    y1, env1 = wl.inputs(5)
+    yg, st = _gpu_solve(gm, y1, env1, wl.dt, wl.rtol, wl.atol, variant, False, max_steps=3)
+    assert (st == 1).all() and np.array_equal(yg, y1)
+    # zero cells
+    e = torch.empty((0, gm.n), dtype=torch.float64, device="cuda")
+    gm.solve(e, torch.empty((0, gm.n_env), dtype=torch.float64, device="cuda"), wl.dt, wl.rtol, wl.atol,
+             variant=variant)
+    # per-species atol and a dark cell
+    y2, env2 = wl.inputs(4)
+    lay = w.layout(wl.mech)
+    for k2, kind in enumerate(lay.runtime_kind):
+        if kind == "PHOTOLYSIS":
+            env2[0, 2 + k2] = 0.0
+    atol = np.full(gm.n, wl.atol)
+    atol[::3] = 1e-7
+    yg, st = _gpu_solve(gm, y2, env2, wl.dt, wl.rtol, atol, variant, False)
+    yo, sto, _ = om.solve(y2, env2, wl.dt, wl.rtol, atol)
+    assert (st == 0).all()
+    parity.check(om, y2, env2, wl.dt, wl.rtol, atol, yg, yo)
+
+
+def test_dry_sections_freeze_aqueous_species(mechs):
+    wl, gm, om = mechs[3]
+    y0, env = wl.inputs(6)
+    lay = w.layout(wl.mech)
+    base = 2 + len(lay.runtime_defaults)
+    env[:, base + 2::3] = 0.0  # no water anywhere
+    y0[:, 72:] = 0.5
+    yg, st = _gpu_solve(gm, y0, env, wl.dt, wl.rtol, wl.atol, camp.VARIANT_MIXED, True)
+    assert (st == 0).all()
+    assert np.array_equal(yg[:, 72:], y0[:, 72:])
+
+
+def test_host_entry_point_matches_device_entry_point(mechs):
+    wl, gm, om = mechs[2]
+    y0, env = wl.inputs(50)
+    yd, std = _gpu_solve(gm, y0, env, wl.dt, wl.rtol, wl.atol, camp.VARIANT_MIXED, True)
+    yh = y0.copy()
+    sth = gm.solve_host(yh, env, wl.dt, wl.rtol, wl.atol, variant=camp.VARIANT_MIXED, persistent=True)
+    assert np.array_equal(yh, yd) and np.array_equal(sth, std)
+
+
+def test_stats_are_close_to_the_oracle(mechs):
+    import torch
+    wl, gm, om = mechs[2]
+    y0, env = wl.inputs(64)
+    ty = torch.tensor(y0, device="cuda")
+    stats = torch.zeros((64, camp.NSTATS), dtype=torch.int32, device="cuda")
+    gm.solve(ty, torch.tensor(env, device="cuda"), wl.dt, wl.rtol, wl.atol, variant=camp.VARIANT_FP64,
+             persistent=False, stats=stats)
+    sg = stats.cpu().numpy()
+    _, _, so = om.solve(y0, env, wl.dt, wl.rtol, wl.atol)
+    # same controller: the FP64 form takes the oracle's step sequence on most cells
+    assert np.mean(sg[:, 0] == so[:, 0]) > 0.5
+    assert abs(sg[:, 0].mean() / so[:, 0].mean() - 1) < 0.1
