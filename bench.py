@@ -25,7 +25,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOADS = {"small": 1, "gas72": 2, "multiphase232": 3}
+WORKLOADS = {"small": 1, "gas72": 2, "multiphase232": 3, "uneven": 4, "serving": 5}
 FP64_PEAK_NOMINAL_GFLOPS = 1250.0  # GB300 dense FP64, nominal
 
 
@@ -42,6 +42,8 @@ def args():
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--requests", type=int, default=2000, help="serving: number of chunk requests")
+    p.add_argument("--load", type=float, default=0.8, help="serving: offered load / measured capacity")
     return p.parse_args()
 
 
@@ -115,6 +117,10 @@ def oracle_rate(wl, seconds, rank_seed=0):
 # ----------------------------------------------------------------- main
 def main():
     a = args()
+    if a.workload == "uneven" and a.impl == "camp":
+        return bench_uneven(a)
+    if a.workload == "serving" and a.impl == "camp":
+        return bench_serving(a)
     from paper_2111_07436_gb300 import workloads as w
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -164,7 +170,8 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     gm = camp.Mechanism(wl.json())
     config["species"] = gm.n
-    wl.cell_seed += 1000 * rank  # each replica solves its own cells (weak scaling)
+    from paper_2111_07436_gb300 import replicas
+    wl.cell_seed = replicas.cell_seed(wl.cell_seed, rank)  # each replica solves its own cells
     y0, env = wl.inputs()
     C = wl.n_cells
     y0_d = torch.tensor(y0, device=dev)
@@ -215,11 +222,8 @@ def main():
         times = run(variant, persistent, a.steps, a.warmup)
     if dist:
         dist.barrier()
-    total = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(total, op=dist.ReduceOp.MAX)
-    ms = total.item() / a.steps
-    value = world * C * wl.n_outer / (ms / 1e3)
+    _, t_max, value = replicas.aggregate(C * wl.n_outer * a.steps, sum(times) / 1e3, dist)
+    ms = 1e3 * t_max / a.steps
 
     # plain FP64 form, one launch per outer step, for the mixed-vs-plain ratio
     plain = None
@@ -241,10 +245,8 @@ def main():
                              cells_per_block=a.cpb)
         if i >= a.warmup:
             e2e_t.append(time.perf_counter() - t)
-    e2e_s = torch.tensor([sum(e2e_t)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * C * wl.n_outer * a.steps / e2e_s.item(), "unit": "cell-steps/s",
+    _, _, e2e_value = replicas.aggregate(C * wl.n_outer * a.steps, sum(e2e_t), dist)
+    e2e = {"value": e2e_value, "unit": "cell-steps/s",
            "h2d_bytes_per_step": int(y_h.numel() * 8 + e_h.numel() * 8 + 8),
            "d2h_bytes_per_step": int(y_h.numel() * 8 + C * 4),
            "ok_cells": int((st_h == 0).sum())}
@@ -273,6 +275,196 @@ def main():
            "plain_fp64": plain, "mixed_over_plain": (value / world / plain["value"]) if plain else None,
            "roofline": roof, "hbm_io_gbs": hbm, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary()}
     print(json.dumps(out))
+
+
+def _groups_on_device(groups, dev):
+    import torch
+    from paper_2111_07436_gb300 import camp
+    out = []
+    for mj, y, env in groups:
+        gm = camp.Mechanism(json.dumps(mj))
+        out.append({"mech": gm, "y0": torch.tensor(y, device=dev), "env": torch.tensor(env, device=dev),
+                    "state": torch.empty(y.shape, dtype=torch.float64, device=dev),
+                    "status": torch.empty(len(y), dtype=torch.int32, device=dev),
+                    "atol": torch.full((1,), 1e-5, dtype=torch.float64, device=dev),
+                    "workspace": camp.workspace(dev)})
+    return out
+
+
+def bench_uneven(a):
+    """131072 cells of uneven stiffness (half dark, 10% cloud cells on the
+    multiphase mechanism): both mechanisms in one camp_solve_batch call, its
+    launches captured once in a CUDA graph and replayed per step, with the
+    autotuned cells-per-block; against the plain FP64 form, one static launch
+    per mechanism per step."""
+    import torch
+    from paper_2111_07436_gb300 import build, camp, workloads as w
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n_cells = a.cells or 131072
+    groups, cloud_idx = w.uneven_batch(n_cells)
+    G = _groups_on_device(groups, dev)
+    dt, rtol = 180.0, 1e-4
+    tuned = []
+    for g in G:  # autotune on a 4096-cell sample of each group
+        k = min(4096, g["y0"].shape[0])
+        tuned.append(g["mech"].autotune(g["y0"][:k].contiguous(), g["env"][:k].contiguous(), dt, rtol,
+                                        g["atol"]))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    side = torch.cuda.Stream()
+
+    def step(stream):
+        for g in G:
+            g["state"].copy_(g["y0"])
+        camp.solve_batch([{k: g[k] for k in ("mech", "state", "env", "atol", "status", "workspace")}
+                          for g in G], dt, rtol, stream=stream)
+
+    with torch.cuda.stream(side):  # first call creates the fork streams outside capture
+        step(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        step(side)
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(0) as clk:
+        for i in range(a.warmup + a.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            graph.replay()
+            e1.record()
+            times.append((e0, e1))
+        torch.cuda.synchronize()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in times[a.warmup:]) / a.steps
+    ok = sum(int((g["status"] == 0).sum().item()) for g in G)
+    # plain FP64: one static launch per mechanism per step
+    pt = []
+    for i in range(1 + max(1, a.steps // 2)):
+        flush.zero_()
+        for g in G:
+            g["state"].copy_(g["y0"])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for g in G:
+            g["mech"].solve(g["state"], g["env"], dt, rtol, g["atol"], status=g["status"],
+                            variant=camp.VARIANT_FP64, persistent=False)
+        e1.record()
+        pt.append((e0, e1))
+    torch.cuda.synchronize()
+    pms = sum(e0.elapsed_time(e1) for e0, e1 in pt[1:]) / (len(pt) - 1)
+    value = n_cells / (ms / 1e3)
+    print(json.dumps({
+        "metric": f"cell-steps/s at rtol {rtol:g}", "value": value, "unit": "cell-steps/s", "n_gpus": 1,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 state / f32 J+LU", "data": "synthetic",
+        "config": {"workload": f"uneven stiffness: {n_cells} cells, 50% dark, {len(cloud_idx)} cloud cells "
+                               f"on the 232-species mechanism, the rest on the 72-species one, dt 180 s",
+                   "groups": [int(g["y0"].shape[0]) for g in G],
+                   "autotuned_cpb_persistent_ms": tuned, "cuda_graph": True,
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "ok_cells": ok, "gpu_launches": 2 * a.steps,
+        "plain_fp64": {"value": n_cells / (pms / 1e3), "ms_per_step": pms,
+                       "form": "fp64, one static launch per mechanism"},
+        "mixed_over_plain": pms / ms, "clocks": clk.summary()}))
+
+
+def bench_serving(a):
+    """A Poisson stream of chunk requests (256..65536 cells, 70% gas-72 / 30%
+    multiphase-232, dt 60..600 s) through the continuous-batching server
+    under an 80 GB device budget.  Reports p50/p99 latency (arrival to
+    result on the host) and sustained cell-steps/s, mixed and plain FP64."""
+    import numpy as np
+    import torch
+    from paper_2111_07436_gb300 import build, camp, workloads as w
+    build.build()
+    torch.cuda.set_device(0)
+    reqs = w.serving_requests(a.requests)
+    mechs = {"gas72": w.large_gas_mechanism(), "multiphase232": w.multiphase_mechanism()}
+    gms = {k: camp.Mechanism(json.dumps(v)) for k, v in mechs.items()}
+    RING = 4 * 65536
+    pools = {}
+    for k, mj in mechs.items():  # pinned input pools; requests take disjoint ring regions
+        y, env = w.cells(mj, RING, seed=300 + len(k))
+        pools[k] = {"y0": y, "state": torch.from_numpy(y.copy()).pin_memory(),
+                    "env": torch.from_numpy(env).pin_memory(),
+                    "status": torch.zeros(RING, dtype=torch.int32).pin_memory(), "head": 0, "busy": []}
+
+    def region(k, n):
+        p = pools[k]
+        start = p["head"] if p["head"] + n <= RING else 0
+        for (s0, s1) in p["busy"]:
+            if start < s1 and s0 < start + n:
+                return None
+        p["head"] = start + n
+        p["busy"].append((start, start + n))
+        return start
+
+    def run(variant, rate_cells, n_req):
+        srv = camp.Server(hbm_budget_bytes=80 << 30, max_inflight=8)
+        rng = np.random.default_rng(205)
+        arrivals = np.cumsum(rng.exponential(1.0, n_req)) * (np.mean([r["cells"] for r in reqs[:n_req]]) / rate_cells) \
+            if rate_cells else np.zeros(n_req)
+        t0 = time.perf_counter()
+        live, lat, done_cells = [], [], 0
+        for p in pools.values():
+            p["busy"].clear()
+            p["head"] = 0
+
+        def reap(block):
+            nonlocal done_cells
+            for item in list(live):
+                rid, k, s0, n, t_arr = item
+                info = srv.wait(rid) if block else srv.poll(rid)
+                if info is None:
+                    continue
+                live.remove(item)
+                pools[k]["busy"].remove((s0, s0 + n))
+                lat.append(time.perf_counter() - t0 - t_arr)
+                done_cells += n
+                assert info["rc"] == 0, info
+                if block:
+                    return
+
+        for i, r in enumerate(reqs[:n_req]):
+            while time.perf_counter() - t0 < arrivals[i]:
+                reap(False)
+                time.sleep(5e-5)
+            k, n = r["mech"], r["cells"]
+            s0 = region(k, n)
+            while s0 is None:
+                reap(True)
+                s0 = region(k, n)
+            p = pools[k]
+            rid = srv.submit(gms[k], p["state"][s0:s0 + n], p["env"][s0:s0 + n], r["dt"], 1e-4, 1e-5,
+                             p["status"][s0:s0 + n], variant=variant)
+            live.append((rid, k, s0, n, arrivals[i]))
+        while live:
+            reap(True)
+        wall = time.perf_counter() - t0
+        srv.close()
+        lat = np.array(lat)
+        return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "cell_steps_per_s": done_cells / wall, "wall_s": wall, "requests": n_req}
+
+    # capacity: everything arrives at once (saturation)
+    n_cap = min(200, a.requests)
+    sat = run(camp.VARIANT_MIXED, 0, n_cap)
+    rate = a.load * sat["cell_steps_per_s"]
+    mixed = run(camp.VARIANT_MIXED, rate, a.requests)
+    n_plain = min(a.requests, 300)
+    sat_p = run(camp.VARIANT_FP64, 0, min(100, n_plain))
+    plain = run(camp.VARIANT_FP64, a.load * sat_p["cell_steps_per_s"], n_plain)
+    print(json.dumps({
+        "metric": "cell-steps/s at rtol 1e-4; p50/p99 chunk latency", "value": mixed["cell_steps_per_s"],
+        "unit": "cell-steps/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 state / f32 J+LU", "data": "synthetic",
+        "config": {"workload": f"serving: Poisson stream of {a.requests} chunks, 256..65536 cells "
+                               "(log-uniform), 70% gas-72 / 30% multiphase-232, dt 60..600 s, 80 GB budget, "
+                               f"offered load {a.load:g} x measured capacity", "max_inflight": 8},
+        "p50_ms": mixed["p50_ms"], "p99_ms": mixed["p99_ms"], "mixed": mixed, "saturation_mixed": sat,
+        "plain_fp64": plain, "saturation_plain_fp64": sat_p}))
 
 
 if __name__ == "__main__":

@@ -145,9 +145,9 @@ typedef struct {
     int32_t variant;         /* CAMP_VARIANT_* (default MIXED) */
     int32_t persistent;      /* 1: one resident grid takes cells from a work
                                 counter; 0: one group of lanes per cell, static
-                                grid (default 1 for MIXED, 0 for FP64) */
+                                grid; -1: the autotuned choice (default) */
     int32_t max_steps;       /* internal steps per cell (default 10000) */
-    int32_t cells_per_block; /* 0: library default */
+    int32_t cells_per_block; /* 0: autotuned choice, else the library default */
     double hmin_frac;        /* minimum step = hmin_frac * dt (default 1e-10) */
     int32_t *stats;          /* optional device [n_cells][CAMP_NSTATS]: steps,
                                 Newton iterations, Jacobian/LU setups,
@@ -193,6 +193,41 @@ int camp_solve_host(const camp_mech *m, int64_t n_cells, double *state, const do
                     double dt, double rtol, const double *atol, int32_t atol_len, int32_t *status,
                     const camp_solve_opts *opts, void *stream);
 
+/* ---- several mechanisms in one call --------------------------------------- */
+/* One group of cells per mechanism (e.g. gas-only cells and cells carrying
+ * aqueous phases).  Each group runs as its own persistent grid on a stream
+ * forked from `stream` (joined back before the call's work completes), the
+ * group with the most estimated work first, so that as one grid drains its
+ * counter the next one's blocks take the freed SMs.  Capturable in a CUDA
+ * graph (the fork/join uses events).  Arrays are device arrays as for
+ * camp_solve; groups must not alias.  At most CAMP_MAX_GROUPS groups. */
+#define CAMP_MAX_GROUPS 8
+typedef struct {
+    const camp_mech *mech;
+    int64_t n_cells;
+    double *state;
+    const double *env;
+    const double *atol;
+    int32_t atol_len;
+    int32_t *status;
+    int32_t *stats;      /* optional, as camp_solve_opts.stats */
+    void *workspace;     /* optional, as camp_solve_opts.workspace */
+} camp_group;
+
+int camp_solve_batch(const camp_group *groups, int32_t n_groups, double dt, double rtol,
+                     const camp_solve_opts *opts, void *stream);
+
+/* ---- launch autotuning ------------------------------------------------------ */
+/* Time camp_solve on the given cells (device arrays, left unchanged) for
+ * cells-per-block 1, 2 and 4 and both grid mappings, and make the fastest the
+ * mechanism's default for `variant` (used when opts.cells_per_block is 0 and
+ * opts.persistent is -1).  Synchronous; allocates scratch for one copy of
+ * the state.  *best_cpb / *best_persistent (may be NULL) receive the choice;
+ * *ms_best the time of one solve with it. */
+int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const double *env, double dt,
+                  double rtol, const double *atol, int32_t atol_len, int32_t variant,
+                  int32_t *best_cpb, int32_t *best_persistent, double *ms_best, void *stream);
+
 /* ---- single steps of the method, for testing ----------------------------- */
 /* Rate constants (paper Table 2) in ppb units: device env [n_cells][n_env]
  * -> kf, kr device [n_cells][n_rxn] (process order).  The rate of process k
@@ -217,6 +252,55 @@ int camp_jacobian(const camp_mech *m, int64_t n_cells, const double *state, cons
 int camp_lu_solve(const camp_mech *m, int64_t n_cells, const double *state, const double *env,
                   double gamma, const double *b, double *x, int32_t *status, int32_t variant,
                   void *stream);
+
+/* ---- continuous-batching request loop ----------------------------------- */
+/* The host model of the paper hands the solver one air mass (or chunk of
+ * grid cells) at a time, every time step (Sect. 2.4.2).  A camp_server takes
+ * such chunks -- any size, any loaded mechanism -- while earlier ones are
+ * still on the GPU: a worker thread admits them in arrival order as soon as
+ * a stream slot and enough of the device-memory budget are free, runs each
+ * on its own stream (copy in, camp_solve, copy out), and retires them as they
+ * complete; admitted chunks overlap on the device.  Results are the same as
+ * a lone camp_solve of the chunk (each cell is an independent cold start). */
+typedef struct camp_server camp_server;
+
+typedef struct {
+    size_t hbm_budget_bytes; /* device bytes in-flight chunks may hold (> 0) */
+    int32_t max_inflight;    /* concurrent chunks (streams); 0 = 8 */
+} camp_server_opts;
+
+typedef struct {
+    double t_submit, t_admit, t_done; /* seconds on the server's monotonic clock */
+    int64_t n_cells;
+    int32_t rc;                       /* CAMP_OK, CAMP_E_BUDGET (chunk larger than
+                                         the whole budget), or another error */
+} camp_request_info;
+
+/* Create a server on the current device. */
+int camp_server_create(const camp_server_opts *opts, camp_server **out);
+
+/* Queue a chunk.  state (in/out), env and status are HOST arrays laid out as
+ * for camp_solve; they must stay valid and untouched until the request is
+ * finished (poll/wait).  Pinned host memory lets the copies overlap.  atol is
+ * a scalar.  opts may be NULL (mixed form, persistent grid).  *req_id
+ * receives the request's id. */
+int camp_server_submit(camp_server *s, const camp_mech *m, int64_t n_cells, double *state,
+                       const double *env, double dt, double rtol, double atol, int32_t *status,
+                       const camp_solve_opts *opts, uint64_t *req_id);
+
+/* Non-blocking: *done = 1 once the request finished (then *info is filled
+ * and the id is released). */
+int camp_server_poll(camp_server *s, uint64_t req_id, int32_t *done, camp_request_info *info);
+
+/* Block until the request finishes or timeout_ms passes (CAMP_E_TIMEOUT;
+ * the request stays queued and can be waited for again). */
+int camp_server_wait(camp_server *s, uint64_t req_id, int32_t timeout_ms, camp_request_info *info);
+
+/* Queue depth, chunks on the device and budget bytes in use. */
+int camp_server_stats(camp_server *s, int32_t *pending, int32_t *inflight, size_t *bytes_in_use);
+
+/* Finish every queued and in-flight chunk, then release the server. */
+int camp_server_destroy(camp_server *s);
 
 /* Message for the last error on the calling thread ("" if none). */
 const char *camp_last_error(void);

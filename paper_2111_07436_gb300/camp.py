@@ -48,10 +48,33 @@ class SolveOpts(ctypes.Structure):
                 ("workspace", ctypes.c_void_p)]
 
 
+class Group(ctypes.Structure):
+    _fields_ = [("mech", ctypes.c_void_p), ("n_cells", ctypes.c_int64), ("state", ctypes.c_void_p),
+                ("env", ctypes.c_void_p), ("atol", ctypes.c_void_p), ("atol_len", ctypes.c_int32),
+                ("status", ctypes.c_void_p), ("stats", ctypes.c_void_p), ("workspace", ctypes.c_void_p)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("n_cells", ctypes.c_int64), ("rc", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+E_TIMEOUT = -7
+E_BUDGET = -6
+
 EXPORTS = ["camp_mech_load", "camp_mech_compile", "camp_mech_free", "camp_mech_info_get", "camp_mech_species_index",
            "camp_mech_structure", "camp_solve_opts_default", "camp_workspace_bytes", "camp_solve",
            "camp_solve_host", "camp_rate_constants", "camp_forcing", "camp_jacobian",
-           "camp_lu_solve", "camp_last_error"]
+           "camp_lu_solve", "camp_last_error", "camp_server_create", "camp_server_submit",
+           "camp_server_poll", "camp_server_wait", "camp_server_stats", "camp_server_destroy",
+           "camp_solve_batch", "camp_autotune"]
 
 
 def lib():
@@ -83,6 +106,16 @@ def lib():
     L.camp_jacobian.argtypes = [vp, i64, vp, vp, vp, i32, vp]
     L.camp_lu_solve.argtypes = [vp, i64, vp, vp, dbl, vp, vp, vp, i32, vp]
     L.camp_last_error.restype = ctypes.c_char_p
+    L.camp_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+    L.camp_server_submit.argtypes = [vp, vp, i64, vp, vp, dbl, dbl, dbl, vp, ctypes.POINTER(SolveOpts),
+                                     ctypes.POINTER(ctypes.c_uint64)]
+    L.camp_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32), ctypes.POINTER(RequestInfo)]
+    L.camp_server_wait.argtypes = [vp, ctypes.c_uint64, i32, ctypes.POINTER(RequestInfo)]
+    L.camp_server_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_size_t)]
+    L.camp_server_destroy.argtypes = [vp]
+    L.camp_solve_batch.argtypes = [ctypes.POINTER(Group), i32, dbl, dbl, ctypes.POINTER(SolveOpts), vp]
+    L.camp_autotune.argtypes = [vp, i64, vp, vp, dbl, dbl, vp, i32, i32, ctypes.POINTER(i32),
+                                ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
     _lib = L
     return L
 
@@ -176,6 +209,18 @@ class Mechanism:
                                 a.numel(), _ptr(status), ctypes.byref(o), _stream(stream)))
         return status
 
+    def autotune(self, state, env, dt, rtol, atol, variant=VARIANT_MIXED, stream=None):
+        """Pick cells-per-block and grid mapping by timing them on these cells
+        (device tensors, left unchanged); returns (cpb, persistent, ms)."""
+        C = state.shape[0]
+        a = atol if hasattr(atol, "data_ptr") else self._atol(atol, state.device)
+        cpb, pers, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(lib().camp_autotune(self._h, C, _ptr(_dev_f64(state, (C, self.n), "state")),
+                                   _ptr(_dev_f64(env, (C, self.n_env), "env")), float(dt), float(rtol),
+                                   _ptr(a), a.numel(), variant, ctypes.byref(cpb), ctypes.byref(pers),
+                                   ctypes.byref(ms), _stream(stream)))
+        return cpb.value, pers.value, ms.value
+
     def opts(self, variant=VARIANT_MIXED, persistent=None, max_steps=10000, cells_per_block=0,
              stats=None, workspace=None):
         o = SolveOpts()
@@ -251,3 +296,92 @@ class Mechanism:
                                    _ptr(_dev_f64(b, (C, self.n), "b")), _ptr(x), _ptr(st), variant,
                                    _stream(stream)))
         return x, st
+
+
+class Server:
+    """Continuous-batching request loop (camp_server_*): chunks of cells on
+    host buffers, admitted under a device-memory budget, overlapped on the
+    GPU.  Buffers passed to submit() must stay alive until the request
+    finishes; pinned memory lets copies overlap."""
+
+    def __init__(self, hbm_budget_bytes, max_inflight=8):
+        o = ServerOpts(int(hbm_budget_bytes), int(max_inflight))
+        h = ctypes.c_void_p()
+        _check(lib().camp_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, mech, state, env, dt, rtol, atol, status, variant=VARIANT_MIXED, persistent=None):
+        """state/env: C-contiguous float64 host arrays (numpy or pinned torch);
+        status: int32 host array.  Returns the request id."""
+        st = state if isinstance(state, np.ndarray) else state.numpy()
+        ev = env if isinstance(env, np.ndarray) else env.numpy()
+        ss = status if isinstance(status, np.ndarray) else status.numpy()
+        if st.shape[1] != mech.n or ev.shape != (st.shape[0], mech.n_env) or ss.shape != (st.shape[0],):
+            raise CampError("shape mismatch")
+        o = mech.opts(variant, persistent)
+        rid = ctypes.c_uint64()
+        _check(lib().camp_server_submit(self._h, mech._h, st.shape[0], ctypes.c_void_p(st.ctypes.data),
+                                        ctypes.c_void_p(ev.ctypes.data), float(dt), float(rtol),
+                                        float(atol), ctypes.c_void_p(ss.ctypes.data), ctypes.byref(o),
+                                        ctypes.byref(rid)))
+        self._keep[rid.value] = (state, env, status, mech)
+        return rid.value
+
+    def wait(self, rid, timeout_ms=600000):
+        """Request info dict, or None on timeout (the request stays queued)."""
+        info = RequestInfo()
+        rc = lib().camp_server_wait(self._h, rid, int(timeout_ms), ctypes.byref(info))
+        if rc == E_TIMEOUT:
+            return None
+        _check(rc)
+        self._keep.pop(rid, None)
+        return info.as_dict()
+
+    def poll(self, rid):
+        info = RequestInfo()
+        done = ctypes.c_int32()
+        _check(lib().camp_server_poll(self._h, rid, ctypes.byref(done), ctypes.byref(info)))
+        if not done.value:
+            return None
+        self._keep.pop(rid, None)
+        return info.as_dict()
+
+    def stats(self):
+        p, i, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+        _check(lib().camp_server_stats(self._h, ctypes.byref(p), ctypes.byref(i), ctypes.byref(b)))
+        return {"pending": p.value, "inflight": i.value, "bytes_in_use": b.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().camp_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        if _lib is not None:
+            self.close()
+
+
+def workspace(device):
+    """Device scratch for one concurrent solve (the work counter)."""
+    import torch
+    return torch.zeros(int(lib().camp_workspace_bytes()), dtype=torch.uint8, device=device)
+
+
+def solve_batch(groups, dt, rtol, variant=VARIANT_MIXED, stream=None):
+    """groups: list of dicts {mech, state, env, atol (tensor), status, stats?,
+    workspace?} of device tensors; one call, one persistent grid per group."""
+    arr = (Group * len(groups))()
+    for i, g in enumerate(groups):
+        m = g["mech"]
+        C = g["state"].shape[0]
+        _dev_f64(g["state"], (C, m.n), "state")
+        _dev_f64(g["env"], (C, m.n_env), "env")
+        arr[i] = Group(m._h.value, C, g["state"].data_ptr(), g["env"].data_ptr(), g["atol"].data_ptr(),
+                       g["atol"].numel(), g["status"].data_ptr(),
+                       g["stats"].data_ptr() if g.get("stats") is not None else None,
+                       g["workspace"].data_ptr() if g.get("workspace") is not None else None)
+    o = SolveOpts()
+    lib().camp_solve_opts_default(ctypes.byref(o), variant)
+    _check(lib().camp_solve_batch(arr, len(groups), float(dt), float(rtol), ctypes.byref(o), _stream(stream)))

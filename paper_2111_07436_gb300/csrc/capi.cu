@@ -24,6 +24,9 @@ struct camp_mech {
     void *stage = nullptr;
     size_t stage_bytes = 0;
     bool on_device = false;
+    int occ[2][9] = {};                 // blocks per SM by variant and cells per block (0 = unknown)
+    int tuned_cpb[2] = {0, 0};          // per variant, 0 = untuned
+    int tuned_persistent[2] = {-1, -1}; // per variant, -1 = untuned
 };
 
 namespace {
@@ -230,7 +233,7 @@ int camp_mech_structure(const camp_mech *m, int32_t *rowptr, int32_t *colidx, in
 void camp_solve_opts_default(camp_solve_opts *o, int variant) {
     if (!o) return;
     o->variant = variant;
-    o->persistent = variant == CAMP_VARIANT_MIXED ? 1 : 0;
+    o->persistent = -1;
     o->max_steps = 10000;
     o->cells_per_block = 0;
     o->hmin_frac = 1e-10;
@@ -262,8 +265,13 @@ int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double
 
     const bool f32 = o.variant == CAMP_VARIANT_MIXED;
     const int smem_cell = camp_cell_smem_bytes(m->dm, f32 ? 4 : 8);
-    int cpb = o.cells_per_block > 0 ? o.cells_per_block : (smem_cell > 8192 ? 1 : 2);
-    cpb = std::min(cpb, 8);
+    if (o.persistent < 0)
+        o.persistent = m->tuned_persistent[o.variant] >= 0 ? m->tuned_persistent[o.variant]
+                                                           : (o.variant == CAMP_VARIANT_MIXED ? 1 : 0);
+    int cpb = o.cells_per_block > 0 ? o.cells_per_block
+              : m->tuned_cpb[o.variant] > 0 ? m->tuned_cpb[o.variant]
+                                            : (smem_cell > 8192 ? 1 : 2);
+    cpb = std::min(cpb, 4);
     while (cpb > 1 && cpb * smem_cell > kMaxSmem) cpb--;
 
     SolveArgs a;
@@ -290,8 +298,11 @@ int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double
             if (!m->own_ws) CUDA_TRY(cudaMalloc(&m->own_ws, camp_workspace_bytes()));
             q = m->own_ws;
         }
-        int per_sm = 0;
-        CUDA_TRY(f32 ? camp_occupancy_f32(m->dm, cpb, &per_sm) : camp_occupancy_f64(m->dm, cpb, &per_sm));
+        int per_sm = m->occ[o.variant][cpb];
+        if (per_sm == 0) {
+            CUDA_TRY(f32 ? camp_occupancy_f32(m->dm, cpb, &per_sm) : camp_occupancy_f64(m->dm, cpb, &per_sm));
+            m->occ[o.variant][cpb] = per_sm;
+        }
         if (per_sm < 1) return fail(CAMP_E_UNSUPPORTED, "kernel does not fit on an SM");
         grid = std::min<long long>((long long)per_sm * m->sm_count, (n_cells + cpb - 1) / cpb);
         CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(unsigned long long), s));
@@ -349,6 +360,107 @@ int camp_solve_host(const camp_mech *mc, int64_t n_cells, double *state, const d
     if (host_stats)
         CUDA_TRY(cudaMemcpyAsync(host_stats, d_stats, b_stats, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    return CAMP_OK;
+}
+
+int camp_solve_batch(const camp_group *groups, int32_t n_groups, double dt, double rtol,
+                     const camp_solve_opts *opts, void *stream) {
+    if (!groups || n_groups < 0 || n_groups > CAMP_MAX_GROUPS) return fail(CAMP_E_INVAL, "bad group count");
+    if (n_groups == 0) return CAMP_OK;
+    // estimated work: cells x (per-cell f flops + LU solve flops), heaviest first
+    int order[CAMP_MAX_GROUPS];
+    double work[CAMP_MAX_GROUPS];
+    for (int g = 0; g < n_groups; g++) {
+        if (!groups[g].mech) return fail(CAMP_E_INVAL, "NULL mechanism in group");
+        const camp::HostMech &h = groups[g].mech->h;
+        work[g] = (double)groups[g].n_cells * (double)(h.flops_forcing + h.flops_solve + 20 * h.n);
+        order[g] = g;
+    }
+    std::sort(order, order + n_groups, [&](int a, int b) { return work[a] > work[b]; });
+    cudaStream_t parent = (cudaStream_t)stream;
+    thread_local cudaStream_t forks[CAMP_MAX_GROUPS] = {};
+    thread_local cudaEvent_t ev_fork = nullptr, ev_join[CAMP_MAX_GROUPS] = {};
+    thread_local int fork_dev = -1;
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (fork_dev != dev) {
+        for (int g = 0; g < CAMP_MAX_GROUPS; g++) {
+            CUDA_TRY(cudaStreamCreateWithFlags(&forks[g], cudaStreamNonBlocking));
+            CUDA_TRY(cudaEventCreateWithFlags(&ev_join[g], cudaEventDisableTiming));
+        }
+        CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        fork_dev = dev;
+    }
+    CUDA_TRY(cudaEventRecord(ev_fork, parent));
+    int rc = CAMP_OK;
+    for (int i = 0; i < n_groups; i++) {
+        const camp_group &gr = groups[order[i]];
+        CUDA_TRY(cudaStreamWaitEvent(forks[i], ev_fork, 0));
+        camp_solve_opts o;
+        camp_solve_opts_default(&o, opts ? opts->variant : CAMP_VARIANT_MIXED);
+        if (opts) o = *opts;
+        o.stats = gr.stats;
+        o.workspace = gr.workspace;
+        if (o.persistent < 0) o.persistent = 1;
+        if (!o.workspace && n_groups > 1 && o.persistent)
+            return fail(CAMP_E_INVAL, "each group of a multi-group persistent solve needs its own workspace");
+        rc = camp_solve(gr.mech, gr.n_cells, gr.state, gr.env, dt, rtol, gr.atol, gr.atol_len, gr.status,
+                        &o, forks[i]);
+        CUDA_TRY(cudaEventRecord(ev_join[i], forks[i]));
+        CUDA_TRY(cudaStreamWaitEvent(parent, ev_join[i], 0));
+        if (rc != CAMP_OK) return rc;
+    }
+    return CAMP_OK;
+}
+
+int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const double *env, double dt,
+                  double rtol, const double *atol, int32_t atol_len, int32_t variant, int32_t *best_cpb,
+                  int32_t *best_persistent, double *ms_best, void *stream) {
+    if (!m || n_cells <= 0 || !state || !env || !atol) return fail(CAMP_E_INVAL, "bad argument");
+    if (variant != CAMP_VARIANT_MIXED && variant != CAMP_VARIANT_FP64) return fail(CAMP_E_INVAL, "unknown variant");
+    if (int rc = check_device(m)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)n_cells * m->h.n * 8;
+    double *work = nullptr;
+    int32_t *status = nullptr;
+    CUDA_TRY(cudaMallocAsync((void **)&work, bytes, s));
+    CUDA_TRY(cudaMallocAsync((void **)&status, (size_t)n_cells * 4, s));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const int cpbs[3] = {1, 2, 4};
+    float best = 1e30f;
+    int bc = 1, bp = 1, rc = CAMP_OK;
+    for (int pers = 0; pers <= 1 && rc == CAMP_OK; pers++)
+        for (int ci = 0; ci < 3 && rc == CAMP_OK; ci++) {
+            const int smem_cell = camp_cell_smem_bytes(m->dm, variant == CAMP_VARIANT_MIXED ? 4 : 8);
+            if (cpbs[ci] * smem_cell > kMaxSmem) continue;
+            camp_solve_opts o;
+            camp_solve_opts_default(&o, variant);
+            o.persistent = pers;
+            o.cells_per_block = cpbs[ci];
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && rc == CAMP_OK; rep++) {  // first run warms up
+                if (cudaMemcpyAsync(work, state, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) rc = CAMP_E_CUDA;
+                cudaEventRecord(e0, s);
+                if (rc == CAMP_OK) rc = camp_solve(m, n_cells, work, env, dt, rtol, atol, atol_len, status, &o, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = CAMP_E_CUDA;
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (rc == CAMP_OK && ms < best) { best = ms; bc = cpbs[ci]; bp = pers; }
+        }
+    cudaFreeAsync(work, s);
+    cudaFreeAsync(status, s);
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != CAMP_OK) return rc;
+    m->tuned_cpb[variant] = bc;
+    m->tuned_persistent[variant] = bp;
+    if (best_cpb) *best_cpb = bc;
+    if (best_persistent) *best_persistent = bp;
+    if (ms_best) *ms_best = best;
     return CAMP_OK;
 }
 

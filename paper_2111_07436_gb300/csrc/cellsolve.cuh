@@ -233,6 +233,13 @@ template <> __device__ __forceinline__ float tiny_pivot<float>() { return 1e-30f
 template <> __device__ __forceinline__ double tiny_pivot<double>() { return 1e-300; }
 
 // ---- LU factorisation in place; returns true if every pivot is usable -------
+// Pivots are checked, then replaced by their reciprocals: the substitutions
+// and later rows multiply instead of dividing.
+template <typename LT>
+__device__ __forceinline__ bool bad_pivot(LT u) {
+    return !(fabs((double)u) > (double)tiny_pivot<LT>()) || !isfinite((double)u);
+}
+
 template <int G, typename LT>
 __device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigned gm) {
     LT *lu = c.lu;
@@ -248,15 +255,17 @@ __device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigne
                 uint32_t op = __ldg(m.fops + q);
                 int t = CAMP_OP_TGT(op), s = CAMP_OP_SRC(op);
                 if (op & CAMP_OP_DIV) {
-                    l = lu[t] / lu[s];
+                    l = lu[t] * lu[s];  // lu[s] holds 1 / U(k,k)
                     lu[t] = l;
                 } else {
                     lu[t] -= l * lu[s];
                 }
             }
             if (i < m.d) {
-                LT u = lu[__ldg(m.udiag + i)];
-                bad |= !(fabs((double)u) > (double)tiny_pivot<LT>()) || !isfinite((double)u);
+                const int di = __ldg(m.udiag + i);
+                LT u = lu[di];
+                bad |= bad_pivot(u);
+                lu[di] = (LT)1 / u;
             }
         }
         __syncwarp(gm);
@@ -266,9 +275,11 @@ __device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigne
     LT *A = lu + m.dbase;
     for (int k = 0; k < D; k++) {
         LT piv = A[k * LD + k];
-        if (lane == 0) bad |= !(fabs((double)piv) > (double)tiny_pivot<LT>()) || !isfinite((double)piv);
-        for (int i = k + 1 + lane; i < D; i += G) A[i * LD + k] = A[i * LD + k] / piv;
+        bad |= bad_pivot(piv);
+        LT rp = (LT)1 / piv;
+        for (int i = k + 1 + lane; i < D; i += G) A[i * LD + k] *= rp;
         __syncwarp(gm);
+        if (lane == 0) A[k * LD + k] = rp;
         for (int j = k + 1 + lane; j < D; j += G) {
             LT ukj = A[k * LD + j];
             for (int i = k + 1; i < D; i++) A[i * LD + j] -= A[i * LD + k] * ukj;
@@ -279,6 +290,11 @@ __device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigne
 }
 
 // ---- substitution: solves (LU) x = x in place (c.x holds the right side) -----
+// Sparse rows go level by level through shared memory; the dense block's
+// right side lives in registers (lane l holds rows l, l+32, ...) and each
+// pivot's value is broadcast with a shuffle, so the block needs no barrier.
+constexpr int DMAX_SLOTS = 4;  // dense blocks up to 128 rows
+
 template <int G, typename LT>
 __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, unsigned gm) {
     LT *x = c.x;
@@ -296,20 +312,49 @@ __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, uns
         }
         __syncwarp(gm);
     }
-    // dense block forward (unit lower) and backward
     const int D = m.D, LD = m.LD, d = m.d;
-    const LT *A = lu + m.dbase;
-    LT *xb = x + d;
-    for (int k = 0; k < D; k++) {
-        LT xk = xb[k];
-        for (int i = k + 1 + lane; i < D; i += G) xb[i] -= A[i * LD + k] * xk;
-        __syncwarp(gm);
-    }
-    for (int k = D - 1; k >= 0; k--) {
-        LT xk = xb[k] / A[k * LD + k];
-        __syncwarp(gm);
-        if (lane == 0) xb[k] = xk;
-        for (int i = lane; i < k; i += G) xb[i] -= A[i * LD + k] * xk;
+    if (D > 0) {
+        const LT *A = lu + m.dbase;
+        LT xr[DMAX_SLOTS];
+#pragma unroll
+        for (int t = 0; t < DMAX_SLOTS; t++) {
+            int i = lane + G * t;
+            xr[t] = (i < D) ? x[d + i] : (LT)0;
+        }
+        // forward, unit lower
+        for (int k = 0; k < D; k++) {
+            const int ks = k / G;
+            LT own = xr[0];
+#pragma unroll
+            for (int t = 1; t < DMAX_SLOTS; t++)
+                if (ks == t) own = xr[t];
+            const LT xk = __shfl_sync(gm, own, k % G, G);
+#pragma unroll
+            for (int t = 0; t < DMAX_SLOTS; t++) {
+                int i = lane + G * t;
+                if (i > k && i < D) xr[t] -= A[i * LD + k] * xk;
+            }
+        }
+        // backward, upper with reciprocal diagonal
+        for (int k = D - 1; k >= 0; k--) {
+            const int ks = k / G;
+            LT own = xr[0];
+#pragma unroll
+            for (int t = 1; t < DMAX_SLOTS; t++)
+                if (ks == t) own = xr[t];
+            const LT xk = __shfl_sync(gm, own, k % G, G) * A[k * LD + k];
+#pragma unroll
+            for (int t = 0; t < DMAX_SLOTS; t++) {
+                int i = lane + G * t;
+                if (i == k) xr[t] = xk;
+                else if (i < k) xr[t] -= A[i * LD + k] * xk;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < DMAX_SLOTS; t++) {
+            int i = lane + G * t;
+            if (i < D) x[d + i] = xr[t];
+        }
         __syncwarp(gm);
     }
     // backward, sparse rows by level
@@ -320,7 +365,7 @@ __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, uns
             LT s = x[i];
             int qb = __ldg(m.su_ptr + i), qe = __ldg(m.su_ptr + i + 1);
             for (int q = qb; q < qe; q++) s -= lu[__ldg(m.su_off + q)] * x[__ldg(m.su_col + q)];
-            x[i] = s / lu[__ldg(m.udiag + i)];
+            x[i] = s * lu[__ldg(m.udiag + i)];
         }
         __syncwarp(gm);
     }

@@ -18,7 +18,7 @@ __device__ __forceinline__ unsigned group_mask() {
 // `queue` null the mapping is static (cell = block * cpb + group); otherwise
 // the groups take cells from the counter until it passes n_cells.
 template <int G, int NPL, typename LT>
-__global__ void __launch_bounds__(256) k_solve(DevMech m, SolveArgs a) {
+__global__ void __maxnreg__(NPL >= 6 ? 232 : 184) k_solve(DevMech m, SolveArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int group = threadIdx.x / G, lane = threadIdx.x % G;
     const unsigned gm = group_mask<G>();

@@ -10,11 +10,24 @@ namespace {
 using LT = CAMP_LT;
 constexpr int G = 32;
 
+// Raise a kernel's dynamic shared-memory limit once to the maximum, so that
+// launches (possibly inside stream capture) make no further attribute calls.
+template <class K>
+cudaError_t allow_smem(K kern) {
+    static int done_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || done_dev == dev) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e == cudaSuccess) done_dev = dev;
+    return e;
+}
+
 template <int NPL>
 cudaError_t launch_solve_npl(const DevMech &m, const SolveArgs &a, int grid, cudaStream_t s) {
     auto kern = campdev::k_solve<G, NPL, LT>;
     int smem = camp_cell_smem_bytes(m, (int)sizeof(LT)) * a.cpb;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_smem(kern);
     if (e != cudaSuccess) return e;
     kern<<<grid, G * a.cpb, smem, s>>>(m, a);
     return cudaGetLastError();
@@ -24,7 +37,7 @@ template <int NPL>
 cudaError_t occupancy_npl(const DevMech &m, int cpb, int *blocks) {
     auto kern = campdev::k_solve<G, NPL, LT>;
     int smem = camp_cell_smem_bytes(m, (int)sizeof(LT)) * cpb;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_smem(kern);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, G * cpb, smem);
 }

@@ -312,6 +312,7 @@ static void build_tables(HostMech &h) {
             for (int q = h.lu_rowptr[i]; q < h.lu_rowptr[i + 1]; q++) cnt += (h.lu_colidx[q] >= d);
         if ((double)cnt >= 0.75 * (double)(n - d) * (double)(n - d)) { h.d = d; break; }
     }
+    if (n - h.d > 128) h.d = n - 128;  // the substitution keeps at most 4 block rows per lane
     h.D = n - h.d;
     h.LD = h.D % 2 ? h.D : h.D + 1;
 

@@ -365,6 +365,37 @@ class Workload:
                      self.cell_seed, **self.cell_kwargs)
 
 
+def uneven_batch(n_cells=131072, seed=204, cloud_fraction=0.1, night_fraction=0.5):
+    """Cells of uneven stiffness: half dark (J = 0), and a `cloud_fraction`
+    share carrying the aqueous sections with cloud water (liquid water
+    content uniform 0.1..1 g/m^3 spread over the sections in proportion to
+    N r^3); the rest are gas-only cells of the 72-species mechanism.
+    Returns [(mechanism, y0, env), ...] for the gas and cloud groups and the
+    seeded random cell order they were drawn in."""
+    rng = np.random.default_rng(seed)
+    cloudy = rng.random(n_cells) < cloud_fraction
+    n_cloud = int(cloudy.sum())
+    gas, mp = large_gas_mechanism(), multiphase_mechanism()
+    yg, eg = cells(gas, n_cells - n_cloud, seed + 1, night_fraction=night_fraction)
+    ym, em = cells(mp, n_cloud, seed + 2, night_fraction=night_fraction, cloud_fraction=1.0)
+    return [(gas, yg, eg), (mp, ym, em)], np.flatnonzero(cloudy)
+
+
+def serving_requests(n_requests=2000, seed=205, gas_share=0.7, cells_lo=256, cells_hi=65536,
+                     dt_lo=60.0, dt_hi=600.0):
+    """A stream of chunk requests: size log-uniform in [cells_lo, cells_hi],
+    mechanism gas-72 with probability gas_share else multiphase-232, step
+    uniform in [dt_lo, dt_hi] s, inputs seeded per request.  Arrival times
+    are drawn by the caller (Poisson at a chosen rate)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_requests):
+        out.append({"cells": int(np.exp(rng.uniform(math.log(cells_lo), math.log(cells_hi)))),
+                    "mech": "gas72" if rng.random() < gas_share else "multiphase232",
+                    "dt": float(rng.uniform(dt_lo, dt_hi)), "seed": 10_000 + i})
+    return out
+
+
 def workload(k: int) -> Workload:
     """k = 1..3: the single-mechanism workloads (sizes in the docstrings)."""
     if k == 1:

@@ -1,0 +1,110 @@
+"""Several mechanisms in one call (camp_solve_batch), the launch autotuner,
+and CUDA-graph replay of the batched solve -- all give the results of plain
+single-mechanism solves, bit for bit, and match the oracle."""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_07436_gb300 import camp, workloads as w
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def groups(cuda):
+    import torch
+    gs, cloud = w.uneven_batch(3000, seed=44)
+    out = []
+    for mj, y, env in gs:
+        out.append({"mj": mj, "mech": camp.Mechanism(json.dumps(mj)), "y0": y, "env_np": env,
+                    "env": torch.tensor(env, device=cuda),
+                    "atol": torch.full((1,), 1e-5, dtype=torch.float64, device=cuda),
+                    "workspace": camp.workspace(cuda)})
+    return out
+
+
+def _reset(groups):
+    import torch
+    for g in groups:
+        g["state"] = torch.tensor(g["y0"], device="cuda")
+        g["status"] = torch.empty(len(g["y0"]), dtype=torch.int32, device="cuda")
+
+
+def _args(groups):
+    return [{k: g[k] for k in ("mech", "state", "env", "atol", "status", "workspace")} for g in groups]
+
+
+def test_batch_equals_separate_solves_and_the_oracle(groups):
+    import torch
+    _reset(groups)
+    camp.solve_batch(_args(groups), 180.0, 1e-4)
+    torch.cuda.synchronize()
+    got = [g["state"].cpu().numpy() for g in groups]
+    for g, yb in zip(groups, got):
+        ty = torch.tensor(g["y0"], device="cuda")
+        st = g["mech"].solve(ty, g["env"], 180.0, 1e-4, 1e-5, persistent=True)
+        torch.cuda.synchronize()
+        assert np.array_equal(ty.cpu().numpy(), yb)
+        assert (st.cpu().numpy() == 0).all() and (g["status"].cpu().numpy() == 0).all()
+        om = oracle.Mechanism(json.dumps(g["mj"]))
+        idx = np.sort(np.random.default_rng(2).choice(len(g["y0"]), 24, replace=False))
+        yo, so, _ = om.solve(g["y0"][idx], g["env_np"][idx], 180.0, 1e-4, 1e-5)
+        assert (so == 0).all()
+        parity.check(om, g["y0"][idx], g["env_np"][idx], 180.0, 1e-4, 1e-5, yb[idx], yo)
+
+
+def test_cloud_cells_take_more_steps(groups):
+    import torch
+    _reset(groups)
+    stats = [torch.zeros((len(g["y0"]), camp.NSTATS), dtype=torch.int32, device="cuda") for g in groups]
+    args = _args(groups)
+    for a_, s in zip(args, stats):
+        a_["stats"] = s
+    camp.solve_batch(args, 180.0, 1e-4)
+    torch.cuda.synchronize()
+    gas_steps = stats[0][:, 0].float().mean().item()
+    cloud_steps = stats[1][:, 0].float().mean().item()
+    assert cloud_steps > gas_steps
+    steps = torch.cat([s[:, 0] for s in stats]).float()
+    assert steps.max().item() / max(steps.min().item(), 1) > 3  # uneven stiffness
+
+
+def test_graph_replay_equals_direct_call(groups):
+    import torch
+    _reset(groups)
+    camp.solve_batch(_args(groups), 180.0, 1e-4)
+    torch.cuda.synchronize()
+    ref = [g["state"].cpu().numpy() for g in groups]
+    y0s = [torch.tensor(g["y0"], device="cuda") for g in groups]
+    _reset(groups)
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        for g, y0 in zip(groups, y0s):
+            g["state"].copy_(y0)
+        camp.solve_batch(_args(groups), 180.0, 1e-4, stream=side)
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        for g, r in zip(groups, ref):
+            assert np.array_equal(g["state"].cpu().numpy(), r)
+
+
+def test_autotune_picks_a_valid_launch(groups):
+    import torch
+    g = groups[0]
+    y = torch.tensor(g["y0"][:512], device="cuda")
+    e = g["env"][:512].contiguous()
+    before = y.clone()
+    cpb, pers, ms = g["mech"].autotune(y, e, 180.0, 1e-4, g["atol"])
+    assert cpb in (1, 2, 4) and pers in (0, 1) and ms > 0
+    assert torch.equal(y, before)  # inputs untouched
+    ta = y.clone()
+    g["mech"].solve(ta, e, 180.0, 1e-4, 1e-5)  # uses the tuned defaults
+    tb = y.clone()
+    g["mech"].solve(tb, e, 180.0, 1e-4, 1e-5, persistent=True, cells_per_block=1)
+    torch.cuda.synchronize()
+    assert torch.equal(ta, tb)
