@@ -302,6 +302,14 @@ int camp_server_stats(camp_server *s, int32_t *pending, int32_t *inflight, size_
 /* Finish every queued and in-flight chunk, then release the server. */
 int camp_server_destroy(camp_server *s);
 
+/* ---- measurement --------------------------------------------------------- */
+/* Sustained fused multiply-add throughput of the current device in GFLOP/s
+ * (2 flops per FMA), FP64 (fp64 = 1) or FP32: 8 independent chains per
+ * thread, 8 blocks of 256 threads per SM.  Synchronous on `stream`.  The
+ * denominator of the solve's arithmetic roofline (the paper has no
+ * counterpart: it is a property of the machine). */
+int camp_probe_fma_rate(int32_t fp64, double *gflops, void *stream);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char *camp_last_error(void);
 

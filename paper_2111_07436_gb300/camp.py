@@ -74,7 +74,7 @@ EXPORTS = ["camp_mech_load", "camp_mech_compile", "camp_mech_free", "camp_mech_i
            "camp_solve_host", "camp_rate_constants", "camp_forcing", "camp_jacobian",
            "camp_lu_solve", "camp_last_error", "camp_server_create", "camp_server_submit",
            "camp_server_poll", "camp_server_wait", "camp_server_stats", "camp_server_destroy",
-           "camp_solve_batch", "camp_autotune"]
+           "camp_solve_batch", "camp_autotune", "camp_probe_fma_rate"]
 
 
 def lib():
@@ -116,6 +116,7 @@ def lib():
     L.camp_solve_batch.argtypes = [ctypes.POINTER(Group), i32, dbl, dbl, ctypes.POINTER(SolveOpts), vp]
     L.camp_autotune.argtypes = [vp, i64, vp, vp, dbl, dbl, vp, i32, i32, ctypes.POINTER(i32),
                                 ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
+    L.camp_probe_fma_rate.argtypes = [i32, ctypes.POINTER(dbl), vp]
     _lib = L
     return L
 
@@ -385,3 +386,10 @@ def solve_batch(groups, dt, rtol, variant=VARIANT_MIXED, stream=None):
     o = SolveOpts()
     lib().camp_solve_opts_default(ctypes.byref(o), variant)
     _check(lib().camp_solve_batch(arr, len(groups), float(dt), float(rtol), ctypes.byref(o), _stream(stream)))
+
+
+def probe_fma_rate(fp64=True, stream=None):
+    """Measured FMA throughput of the current GPU, GFLOP/s."""
+    g = ctypes.c_double()
+    _check(lib().camp_probe_fma_rate(int(fp64), ctypes.byref(g), _stream(stream)))
+    return g.value

@@ -74,11 +74,15 @@ struct CellPtr {
 };
 
 // ---- group primitives --------------------------------------------------------
-template <int G>
-__device__ __forceinline__ double gsum(double v, unsigned gm) {
+template <int G, typename T>
+__device__ __forceinline__ T gsum_t(T v, unsigned gm) {
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gm, v, o, G);
     return __shfl_sync(gm, v, 0, G);
+}
+template <int G>
+__device__ __forceinline__ double gsum(double v, unsigned gm) {
+    return gsum_t<G, double>(v, gm);
 }
 
 // ---- rate constants (Table 2), per process, from the cell's env ------------
@@ -427,6 +431,20 @@ __device__ __forceinline__ void nord_rescale(double (&z)[QMAX + 1][NPL], int q, 
     }
 }
 
+// x^p for the step-size and order heuristics.  Only the accept/reject tests
+// need FP64; a step-size factor needs a few digits, so this takes FP32
+// log2/exp2 (x = 0 gives 0 for p > 0 and +inf for p < 0).
+__device__ __forceinline__ double ctl_pow(double x, double p) {
+    return (double)exp2f((float)p * __log2f((float)x));
+}
+
+// 1/d for d > 0 to ~1e-14 relative: an FP32 estimate refined by one
+// Newton-Raphson step w <- w (2 - d w) in FP64.
+__device__ __forceinline__ double recip_refined(double d) {
+    double w = (double)__frcp_rn((float)d);
+    return w * fma(-d, w, 2.0);
+}
+
 struct CellStats {
     int steps, newton, jac, errfail, ordsum;
 };
@@ -477,7 +495,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
 #pragma unroll
         for (int s = 0; s < NPL; s++) {
             int p = lane + G * s;
-            w[s] = (p < n) ? 1.0 / (rtol * fabs(z[0][s]) + atl[s]) : 0.0;
+            w[s] = (p < n) ? recip_refined(fma(rtol, fabs(z[0][s]), atl[s])) : 0.0;
         }
     };
     auto any_nonfinite = [&](const double(&v)[NPL]) {
@@ -576,19 +594,20 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                         if (p < n) c.x[p] = (LT)(-(e[s] - gamma * f[s] + z[1][s] / l1));
                     }
                     substitute<G, LT>(m, c, lane, gm);
-                    double dsq = 0.0;
+                    // the update's norm in the LU precision (it only steers the iteration)
+                    LT dsq = (LT)0;
                     bool nf = false;
 #pragma unroll
                     for (int s = 0; s < NPL; s++) {
                         int p = lane + G * s;
-                        double dl = (p < n) ? (double)c.x[p] : 0.0;
-                        if (scale != 1.0) dl *= scale;
-                        e[s] += dl;
-                        double a = dl * w[s];
+                        LT xl = (p < n) ? c.x[p] : (LT)0;
+                        if (scale != 1.0) xl *= (LT)scale;
+                        e[s] += (double)xl;
+                        LT a = xl * (LT)w[s];
                         dsq += a * a;
-                        nf |= !isfinite(dl);
+                        nf |= !isfinite((double)xl);
                     }
-                    double dn = sqrt(gsum<G>(dsq, gm) / (double)n);
+                    double dn = sqrt((double)gsum_t<G, LT>(dsq, gm) / (double)n);
                     if (__any_sync(gm, nf) || !isfinite(dn)) break;
                     double test = dn;
                     if (it > 0) {
@@ -624,7 +643,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
 #pragma unroll
                     for (int s = 0; s < NPL; s++) z[1][s] = h * f[s];
                 } else {
-                    double eta = 0.9 * pow(err, -1.0 / (q + 1));
+                    double eta = 0.9 * ctl_pow(err, -1.0 / (q + 1));
                     if (eta < 0.2) eta = 0.2;
                     h *= eta;
                     if (h < hmin) { status = ST_ERRTEST; break; }
@@ -652,7 +671,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
         if (any_nonfinite(z[0])) { status = ST_NONFINITE; break; }
 
         if (--qwait <= 0 && t < T) {
-            double eta_q = 1.0 / (pow(1.2 * err, 1.0 / (q + 1)) + 1e-6);
+            double eta_q = 1.0 / (ctl_pow(1.2 * err, 1.0 / (q + 1)) + 1e-6);
             double eta_m = 0.0, eta_p = 0.0;
             if (q > 1) {
                 double zs = 0.0;
@@ -664,13 +683,13 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                     }
                 }
                 double em = m.ecoef[q - 1] * m.fact[q] * sqrt(gsum<G>(zs, gm) / (double)n);
-                eta_m = 1.0 / (pow(1.3 * em, 1.0 / q) + 1e-6);
+                eta_m = 1.0 / (ctl_pow(1.3 * em, 1.0 / q) + 1e-6);
             }
             if (q < QMAX && ep_valid) {
 #pragma unroll
                 for (int s = 0; s < NPL; s++) t1[s] = e[s] - ep[s];
                 double epl = m.ecoef[q + 1] * wrms<G, NPL>(m, t1, w, gm);
-                eta_p = 1.0 / (pow(1.4 * epl, 1.0 / (q + 2)) + 1e-6);
+                eta_p = 1.0 / (ctl_pow(1.4 * epl, 1.0 / (q + 2)) + 1e-6);
             }
             double eta = eta_q;
             int qn = q;
