@@ -20,7 +20,8 @@ struct camp_mech {
     int device = 0;
     int sm_count = 0;
     unsigned long long *own_ws = nullptr;
-    std::mutex mu;           // guards own_ws creation and the staging buffers
+    std::mutex mu;           // guards own_ws creation
+    std::mutex stage_mu;     // serialises camp_solve_host's staging buffers
     void *stage = nullptr;
     size_t stage_bytes = 0;
     bool on_device = false;
@@ -330,7 +331,7 @@ int camp_solve_host(const camp_mech *mc, int64_t n_cells, double *state, const d
     const size_t b_stats = (size_t)n_cells * 4 * CAMP_NSTATS;
     int32_t *host_stats = opts ? opts->stats : nullptr;
     const size_t need = b_state + b_env + b_stat + b_atol + (host_stats ? b_stats : 0);
-    std::lock_guard<std::mutex> lk(m->mu);
+    std::lock_guard<std::mutex> lk(m->stage_mu);
     if (m->stage_bytes < need) {
         if (m->stage) cudaFree(m->stage);
         m->stage = nullptr;
