@@ -77,7 +77,7 @@ int camp_pick_npl(int n) {
 }
 
 int camp_cell_smem_bytes(const DevMech &m, int lu_elem) {
-    return campdev::cell_smem(m.n, m.R, m.nlu, lu_elem).bytes;
+    return campdev::cell_smem(m.n, m.R, m.n_rev, m.nlu, lu_elem).bytes;
 }
 
 cudaError_t camp_launch_rates(const DevMech &m, long long n_cells, const double *env, double *kf,

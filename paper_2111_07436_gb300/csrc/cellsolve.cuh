@@ -45,13 +45,13 @@ struct CellSmem {
     int ys, rs, kf, kr, x, lu, bytes;
 };
 __host__ __device__ inline int align16(int b) { return (b + 15) & ~15; }
-__host__ __device__ inline CellSmem cell_smem(int n, int R, int nlu, int lu_elem) {
+__host__ __device__ inline CellSmem cell_smem(int n, int R, int n_rev, int nlu, int lu_elem) {
     CellSmem c;
     int o = 0;
     c.ys = o; o = align16(o + 8 * n);
     c.rs = o; o = align16(o + 8 * R);
     c.kf = o; o = align16(o + 8 * R);
-    c.kr = o; o = align16(o + 8 * R);
+    c.kr = o; o = align16(o + 8 * n_rev);
     c.x = o;  o = align16(o + lu_elem * n);
     c.lu = o; o = align16(o + lu_elem * nlu);
     c.bytes = o;
@@ -63,7 +63,7 @@ struct CellPtr {
     double *ys, *rs, *kf, *kr;
     LT *x, *lu;
     __device__ CellPtr(char *base, const DevMech &m) {
-        CellSmem c = cell_smem(m.n, m.R, m.nlu, (int)sizeof(LT));
+        CellSmem c = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT));
         ys = (double *)(base + c.ys);
         rs = (double *)(base + c.rs);
         kf = (double *)(base + c.kf);
@@ -179,7 +179,9 @@ __device__ __forceinline__ double rate_term(const DevMech &m, int k, const doubl
     return a;
 }
 
-// y (own positions, registers) -> f (own positions).  Leaves ys = y.
+// y (own positions, registers) -> f (own positions).  The per-position sums
+// are spread over the lanes by the compiler's balanced assignment (32-lane
+// groups) and handed back through shared memory (reusing ys).
 template <int G, int NPL, typename LT>
 __device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, const double (&y)[NPL],
                                        double (&f)[NPL], int lane, unsigned gm) {
@@ -189,17 +191,39 @@ __device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, c
         if (p < m.n) c.ys[p] = y[s];
     }
     __syncwarp(gm);
-    for (int k = lane; k < m.R; k += G) c.rs[k] = rate_term(m, k, c.ys, c.kf[k], c.kr[k]);
+    for (int k = lane; k < m.R; k += G) {
+        const int rv = __ldg(m.rrev + k);
+        c.rs[k] = rate_term(m, k, c.ys, c.kf[k], rv >= 0 ? c.kr[rv] : 0.0);
+    }
     __syncwarp(gm);
-#pragma unroll
-    for (int s = 0; s < NPL; s++) {
-        int p = lane + G * s;
-        double acc = 0.0;
-        if (p < m.n) {
-            int b = __ldg(m.fptr + p), e = __ldg(m.fptr + p + 1);
+    if (G == 32) {
+        double *fs = c.ys;  // y is no longer needed
+        const int b0 = __ldg(m.flane_ptr + lane), b1 = __ldg(m.flane_ptr + lane + 1);
+        for (int i = b0; i < b1; i++) {
+            const int p = __ldg(m.flane_pos + i);
+            const int b = __ldg(m.fptr + p), e = __ldg(m.fptr + p + 1);
+            double acc = 0.0;
             for (int q = b; q < e; q++) acc += __ldg(m.fc + q) * c.rs[__ldg(m.fk + q)];
+            fs[p] = acc;
         }
-        f[s] = acc;
+        __syncwarp(gm);
+#pragma unroll
+        for (int s = 0; s < NPL; s++) {
+            int p = lane + G * s;
+            f[s] = (p < m.n) ? fs[p] : 0.0;
+        }
+        __syncwarp(gm);
+    } else {
+#pragma unroll
+        for (int s = 0; s < NPL; s++) {
+            int p = lane + G * s;
+            double acc = 0.0;
+            if (p < m.n) {
+                int b = __ldg(m.fptr + p), e = __ldg(m.fptr + p + 1);
+                for (int q = b; q < e; q++) acc += __ldg(m.fc + q) * c.rs[__ldg(m.fk + q)];
+            }
+            f[s] = acc;
+        }
     }
 }
 
@@ -244,6 +268,56 @@ __device__ __forceinline__ bool bad_pivot(LT u) {
     return !(fabs((double)u) > (double)tiny_pivot<LT>()) || !isfinite((double)u);
 }
 
+// Dense trailing block, right-looking.  Lane l owns block rows and columns
+// l + 32 t (t < NS): it scales its rows' multipliers, then updates its
+// columns over all trailing rows (one broadcast load of the multiplier per
+// row serves both of its columns).  Two barriers per pivot.
+template <int NS, typename LT>
+__device__ __forceinline__ bool dense_factor(LT *A, int D, int LD, int lane, unsigned gm) {
+    bool bad = false;
+    for (int k = 0; k < D; k++) {
+        const LT piv = A[k * LD + k];
+        bad |= bad_pivot(piv);
+        const LT rp = (LT)1 / piv;
+#pragma unroll
+        for (int t = 0; t < NS; t++) {
+            const int i = lane + 32 * t;
+            if (i > k && i < D) A[i * LD + k] *= rp;
+        }
+        __syncwarp(gm);
+        if (lane == 0) A[k * LD + k] = rp;
+        LT u[NS];
+        bool act[NS];
+#pragma unroll
+        for (int t = 0; t < NS; t++) {
+            const int j = lane + 32 * t;
+            act[t] = j > k && j < D;
+            u[t] = act[t] ? A[k * LD + j] : (LT)0;
+        }
+        int i = k + 1;
+        for (; i + 1 < D; i += 2) {
+            const LT l0 = A[i * LD + k], l1 = A[(i + 1) * LD + k];
+#pragma unroll
+            for (int t = 0; t < NS; t++) {
+                if (act[t]) {
+                    LT *p0 = A + i * LD + lane + 32 * t;
+                    const LT a0 = p0[0], a1 = p0[LD];
+                    p0[0] = a0 - l0 * u[t];
+                    p0[LD] = a1 - l1 * u[t];
+                }
+            }
+        }
+        if (i < D) {
+            const LT l0 = A[i * LD + k];
+#pragma unroll
+            for (int t = 0; t < NS; t++)
+                if (act[t]) A[i * LD + lane + 32 * t] -= l0 * u[t];
+        }
+        __syncwarp(gm);
+    }
+    return bad;
+}
+
 template <int G, typename LT>
 __device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigned gm) {
     LT *lu = c.lu;
@@ -274,30 +348,66 @@ __device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigne
         }
         __syncwarp(gm);
     }
-    // dense trailing block, right-looking: multipliers by row, updates by column
-    const int D = m.D, LD = m.LD;
     LT *A = lu + m.dbase;
-    for (int k = 0; k < D; k++) {
-        LT piv = A[k * LD + k];
-        bad |= bad_pivot(piv);
-        LT rp = (LT)1 / piv;
-        for (int i = k + 1 + lane; i < D; i += G) A[i * LD + k] *= rp;
-        __syncwarp(gm);
-        if (lane == 0) A[k * LD + k] = rp;
-        for (int j = k + 1 + lane; j < D; j += G) {
-            LT ukj = A[k * LD + j];
-            for (int i = k + 1; i < D; i++) A[i * LD + j] -= A[i * LD + k] * ukj;
-        }
-        __syncwarp(gm);
+    switch ((m.D + 31) >> 5) {
+    case 0: break;
+    case 1: bad |= dense_factor<1, LT>(A, m.D, m.LD, lane, gm); break;
+    case 2: bad |= dense_factor<2, LT>(A, m.D, m.LD, lane, gm); break;
+    case 3: bad |= dense_factor<3, LT>(A, m.D, m.LD, lane, gm); break;
+    default: bad |= dense_factor<4, LT>(A, m.D, m.LD, lane, gm); break;
     }
     return !__any_sync(gm, bad);
 }
 
 // ---- substitution: solves (LU) x = x in place (c.x holds the right side) -----
-// Sparse rows go level by level through shared memory; the dense block's
-// right side lives in registers (lane l holds rows l, l+32, ...) and each
-// pivot's value is broadcast with a shuffle, so the block needs no barrier.
-constexpr int DMAX_SLOTS = 4;  // dense blocks up to 128 rows
+// Sparse rows go level by level through shared memory.  The dense block's
+// right side lives in registers (lane l holds rows l + 32 t); each pivot's
+// value is broadcast with a shuffle, and the loops run one 32-row diagonal
+// block at a time so that only that block's rows need a comparison.  Rows
+// past the block end read the last row (a valid address) and are discarded.
+template <int NS, typename LT>
+__device__ __forceinline__ void dense_subst(const LT *A, int D, int LD, LT *xb, int lane, unsigned gm) {
+    LT xr[NS];
+    int rowc[NS];
+#pragma unroll
+    for (int t = 0; t < NS; t++) {
+        const int i = lane + 32 * t;
+        rowc[t] = (i < D ? i : D - 1) * LD;
+        xr[t] = i < D ? xb[i] : (LT)0;
+    }
+#pragma unroll
+    for (int kb = 0; kb < NS; kb++) {  // forward, unit lower
+        const int k0 = 32 * kb, k1 = min(D, k0 + 32);
+#pragma unroll 4
+        for (int k = k0; k < k1; k++) {
+            const LT xk = __shfl_sync(gm, xr[kb], k - k0);
+#pragma unroll
+            for (int t = kb; t < NS; t++) {
+                const LT a = A[rowc[t] + k];
+                if (t > kb || lane > k - k0) xr[t] -= a * xk;
+            }
+        }
+    }
+#pragma unroll
+    for (int kb = NS - 1; kb >= 0; kb--) {  // backward, upper with reciprocal diagonal
+        const int k0 = 32 * kb, k1 = min(D, k0 + 32);
+#pragma unroll 4
+        for (int k = k1 - 1; k >= k0; k--) {
+            const LT xk = __shfl_sync(gm, xr[kb], k - k0) * A[k * LD + k];
+            if (lane == k - k0) xr[kb] = xk;
+#pragma unroll
+            for (int t = 0; t <= kb; t++) {
+                const LT a = A[rowc[t] + k];
+                if (t < kb || lane < k - k0) xr[t] -= a * xk;
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NS; t++) {
+        const int i = lane + 32 * t;
+        if (i < D) xb[i] = xr[t];
+    }
+}
 
 template <int G, typename LT>
 __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, unsigned gm) {
@@ -316,51 +426,15 @@ __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, uns
         }
         __syncwarp(gm);
     }
-    const int D = m.D, LD = m.LD, d = m.d;
-    if (D > 0) {
-        const LT *A = lu + m.dbase;
-        LT xr[DMAX_SLOTS];
-#pragma unroll
-        for (int t = 0; t < DMAX_SLOTS; t++) {
-            int i = lane + G * t;
-            xr[t] = (i < D) ? x[d + i] : (LT)0;
-        }
-        // forward, unit lower
-        for (int k = 0; k < D; k++) {
-            const int ks = k / G;
-            LT own = xr[0];
-#pragma unroll
-            for (int t = 1; t < DMAX_SLOTS; t++)
-                if (ks == t) own = xr[t];
-            const LT xk = __shfl_sync(gm, own, k % G, G);
-#pragma unroll
-            for (int t = 0; t < DMAX_SLOTS; t++) {
-                int i = lane + G * t;
-                if (i > k && i < D) xr[t] -= A[i * LD + k] * xk;
-            }
-        }
-        // backward, upper with reciprocal diagonal
-        for (int k = D - 1; k >= 0; k--) {
-            const int ks = k / G;
-            LT own = xr[0];
-#pragma unroll
-            for (int t = 1; t < DMAX_SLOTS; t++)
-                if (ks == t) own = xr[t];
-            const LT xk = __shfl_sync(gm, own, k % G, G) * A[k * LD + k];
-#pragma unroll
-            for (int t = 0; t < DMAX_SLOTS; t++) {
-                int i = lane + G * t;
-                if (i == k) xr[t] = xk;
-                else if (i < k) xr[t] -= A[i * LD + k] * xk;
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < DMAX_SLOTS; t++) {
-            int i = lane + G * t;
-            if (i < D) x[d + i] = xr[t];
-        }
-        __syncwarp(gm);
+    const LT *A = lu + m.dbase;
+    switch ((m.D + 31) >> 5) {
+    case 0: break;
+    case 1: dense_subst<1, LT>(A, m.D, m.LD, x + m.d, lane, gm); break;
+    case 2: dense_subst<2, LT>(A, m.D, m.LD, x + m.d, lane, gm); break;
+    case 3: dense_subst<3, LT>(A, m.D, m.LD, x + m.d, lane, gm); break;
+    default: dense_subst<4, LT>(A, m.D, m.LD, x + m.d, lane, gm); break;
     }
+    __syncwarp(gm);
     // backward, sparse rows by level
     for (int L = 0; L < m.n_blev; L++) {
         int b = __ldg(m.blev_ptr + L), e = __ldg(m.blev_ptr + L + 1);
@@ -487,7 +561,8 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
         double a, b;
         rate_constant(m, k, env_cell, a, b);
         c.kf[k] = a;
-        c.kr[k] = b;
+        const int rv = __ldg(m.rrev + k);
+        if (rv >= 0) c.kr[rv] = b;
     }
     __syncwarp(gm);
 

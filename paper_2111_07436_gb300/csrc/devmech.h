@@ -42,18 +42,23 @@ struct DevMech {
 
     // --- rate terms r_k = kf prod(fwd) - kr prod(rev), positions, -1 = none ---
     const int *rfac;      // [R][6]: 3 forward then 3 reverse
+    int n_rev;            // reversible processes (the only ones with a kr)
+    const int *rrev;      // [R] index into the cell's kr array, -1 if irreversible
 
     // --- forcing gather, by position ---
     const int *fptr;      // [n+1]
     const int *fk;        // [nf] process index
     const double *fc;     // [nf] net stoichiometric coefficient
+    // positions each of the 32 lanes sums, balanced by gather length
+    const int *flane_ptr; // [33]
+    const int *flane_pos; // [n]
 
     // --- Jacobian gather, by Jacobian non-zero ---
     int nnzJ;
     const int *jptr;      // [nnzJ+1]
     const int *jdst;      // [nnzJ] LU storage offset; the diagonal is flagged by jdiag
     const int *jdiag;     // [nnzJ] 1 on the diagonal
-    const int *jk;        // [nj] process k (forward constant) or -(k+1) (reverse constant)
+    const int *jk;        // [nj] process k (forward constant) or -(r+1), r = rrev[k] (reverse)
     const int *jo;        // [nj][2] other factor positions, -1 = none
     const double *jc;     // [nj] coefficient (net stoich x multiplicity, signed)
 

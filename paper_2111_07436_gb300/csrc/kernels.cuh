@@ -9,20 +9,23 @@ namespace campdev {
 
 template <int G>
 __device__ __forceinline__ unsigned group_mask() {
-    if (G == 32) return 0xffffffffu;
-    const int sub = (threadIdx.x & 31) / G;
-    return ((1u << G) - 1u) << (sub * G);
+    if constexpr (G == 32) {
+        return 0xffffffffu;
+    } else {
+        const int sub = (threadIdx.x & 31) / G;
+        return ((1u << G) - 1u) << (sub * G);
+    }
 }
 
 // The whole solve: each group of G lanes integrates one cell at a time.  With
 // `queue` null the mapping is static (cell = block * cpb + group); otherwise
 // the groups take cells from the counter until it passes n_cells.
 template <int G, int NPL, typename LT>
-__global__ void __maxnreg__(NPL >= 6 ? 232 : 184) k_solve(DevMech m, SolveArgs a) {
+__global__ void __maxnreg__(NPL >= 6 ? 232 : 168) k_solve(DevMech m, SolveArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int group = threadIdx.x / G, lane = threadIdx.x % G;
     const unsigned gm = group_mask<G>();
-    const CellSmem L = cell_smem(m.n, m.R, m.nlu, (int)sizeof(LT));
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT));
     CellPtr<LT> c(smem + group * L.bytes, m);
     long long cell = a.queue ? 0 : (long long)blockIdx.x * a.cpb + group;
     for (;;) {
@@ -73,7 +76,8 @@ __device__ __forceinline__ void load_cell(const DevMech &m, const CellPtr<LT> &c
         double a, b;
         rate_constant(m, k, env, a, b);
         c.kf[k] = a;
-        c.kr[k] = b;
+        const int rv = __ldg(m.rrev + k);
+        if (rv >= 0) c.kr[rv] = b;
     }
 #pragma unroll
     for (int s = 0; s < NPL; s++) {
@@ -93,7 +97,7 @@ __global__ void k_forcing(DevMech m, long long n_cells, const double *state, con
     const unsigned gm = group_mask<G>();
     const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
     if (cell >= n_cells) return;
-    const CellSmem L = cell_smem(m.n, m.R, m.nlu, (int)sizeof(LT));
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT));
     CellPtr<LT> c(smem + group * L.bytes, m);
     double y[NPL], f[NPL];
     load_cell<G, NPL, LT>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
@@ -115,7 +119,7 @@ __global__ void k_jacobian(DevMech m, long long n_cells, const double *state, co
     const unsigned gm = group_mask<G>();
     const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
     if (cell >= n_cells) return;
-    const CellSmem L = cell_smem(m.n, m.R, m.nlu, (int)sizeof(LT));
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT));
     CellPtr<LT> c(smem + group * L.bytes, m);
     double y[NPL];
     load_cell<G, NPL, LT>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
@@ -133,7 +137,7 @@ __global__ void k_lu_solve(DevMech m, long long n_cells, const double *state, co
     const unsigned gm = group_mask<G>();
     const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
     if (cell >= n_cells) return;
-    const CellSmem L = cell_smem(m.n, m.R, m.nlu, (int)sizeof(LT));
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT));
     CellPtr<LT> c(smem + group * L.bytes, m);
     double y[NPL];
     load_cell<G, NPL, LT>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);

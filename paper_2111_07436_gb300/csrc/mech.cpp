@@ -273,6 +273,10 @@ static void build_tables(HostMech &h) {
     h.rtype.resize(R); h.rslot.resize(R); h.rnr.resize(R); h.rnp.resize(R);
     h.rpar.assign((size_t)R * 8, 0.0);
     h.rfac.assign((size_t)R * 6, -1);
+    h.rrev.assign(R, -1);
+    h.n_rev = 0;
+    for (int k = 0; k < R; k++)
+        if (h.procs[k].reversible()) h.rrev[k] = h.n_rev++;
     for (int k = 0; k < R; k++) {
         const Process &p = h.procs[k];
         h.rtype[k] = p.type;
@@ -302,6 +306,29 @@ static void build_tables(HostMech &h) {
     for (int p = 0; p < n; p++) {
         for (auto &e : fl[p]) { h.fk.push_back(e.first); h.fc.push_back(e.second); }
         h.fptr.push_back((int)h.fk.size());
+    }
+    // longest-processing-time assignment of the per-position sums to 32 lanes
+    {
+        std::vector<int> order(n);
+        for (int p = 0; p < n; p++) order[p] = p;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return h.fptr[a + 1] - h.fptr[a] > h.fptr[b + 1] - h.fptr[b];
+        });
+        std::vector<std::vector<int>> lanes(32);
+        std::vector<int> load(32, 0);
+        for (int p : order) {
+            int best = 0;
+            for (int l = 1; l < 32; l++)
+                if (load[l] < load[best]) best = l;
+            lanes[best].push_back(p);
+            load[best] += std::max(1, h.fptr[p + 1] - h.fptr[p]);
+        }
+        h.flane_ptr.assign(1, 0);
+        h.flane_pos.clear();
+        for (auto &v : lanes) {
+            for (int p : v) h.flane_pos.push_back(p);
+            h.flane_ptr.push_back((int)h.flane_pos.size());
+        }
     }
 
     // dense trailing block: smallest d with D = n - d >= 8 and fill density >= 0.75
@@ -366,7 +393,7 @@ static void build_tables(HostMech &h) {
                         others[no++] = fac[m];
                     }
                     jent[t].push_back((int)ek.size());
-                    ek.push_back(side == 0 ? k : -(k + 1));
+                    ek.push_back(side == 0 ? k : -(h.rrev[k] + 1));
                     eo.push_back(others[0]);
                     eo.push_back(others[1]);
                     ec.push_back(side == 0 ? nu * mult : -nu * mult);
@@ -533,9 +560,13 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.rnr = pk.put(h.rnr);
     dm.rnp = pk.put(h.rnp);
     dm.rfac = pk.put(h.rfac);
+    dm.n_rev = h.n_rev;
+    dm.rrev = pk.put(h.rrev);
     dm.fptr = pk.put(h.fptr);
     dm.fk = pk.put(h.fk);
     dm.fc = pk.put(h.fc);
+    dm.flane_ptr = pk.put(h.flane_ptr);
+    dm.flane_pos = pk.put(h.flane_pos);
     dm.nnzJ = (int)h.colidx.size();
     dm.jptr = pk.put(h.jptr);
     dm.jdst = pk.put(h.jdst);

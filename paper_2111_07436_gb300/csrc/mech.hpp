@@ -32,10 +32,12 @@ struct HostMech {
     std::vector<int> lu_rowptr, lu_colidx, level_fwd, level_bwd;
 
     // device tables
-    std::vector<int> rtype, rslot, rnr, rnp, rfac;
+    std::vector<int> rtype, rslot, rnr, rnp, rfac, rrev;
+    int n_rev = 0;
     std::vector<double> rpar;
     std::vector<int> fptr, fk;
     std::vector<double> fc;
+    std::vector<int> flane_ptr, flane_pos;
     std::vector<int> jptr, jdst, jdiag, jk, jo;
     std::vector<double> jc;
     int nlu = 0, d = 0, D = 0, LD = 0, dbase = 0;

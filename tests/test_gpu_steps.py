@@ -81,8 +81,14 @@ def test_lu_solve(case, variant, tol, gamma):
     x, st = x.cpu().numpy(), st.cpu().numpy()
     for c in range(len(case["y"])):
         kf, kr = om.rate_constants(case["env"][c])
-        Mo = np.eye(gm.n) - gamma * om.jacobian(kf, kr, case["y"][c])
+        Jo = om.jacobian(kf, kr, case["y"][c])
+        Mo = np.eye(gm.n) - gamma * Jo
         xo = oracle.dense_lu_solve(Mo, b[c])
+        if variant == camp.VARIANT_MIXED and st[c] != 0:
+            # FP32 elimination loses the unit diagonal once gamma |J| passes
+            # 1/eps32; the kernel must then report the breakdown (status 4)
+            assert st[c] == 4 and gamma * np.abs(Jo).max() > 1 / np.finfo(np.float32).eps
+            continue
         assert st[c] == 0
         r = np.linalg.norm(Mo @ x[c] - b[c]) / (np.linalg.norm(Mo, np.inf) * np.linalg.norm(x[c], np.inf))
         assert r <= tol
