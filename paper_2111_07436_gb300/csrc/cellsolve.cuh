@@ -159,18 +159,26 @@ __device__ inline void rate_constant(const DevMech &m, int k, const double *__re
     }
 }
 
+// finite test on the exponent bits (integer pipe, not the FP64 pipe)
+__device__ __forceinline__ bool finite_bits(double x) {
+    return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+
 // ---- forcing f(y): rates of all processes, then a per-position gather --------
+// r_k = kf prod(forward factors) - kr prod(reverse factors); rv < 0 marks an
+// irreversible process.
 __device__ __forceinline__ double rate_term(const DevMech &m, int k, const double *ys, double kf,
-                                            double kr) {
+                                            const double *kr, int rv) {
     const int *fac = m.rfac + 6 * k;
     int a0 = __ldg(fac), a1 = __ldg(fac + 1), a2 = __ldg(fac + 2);
     double a = kf;
     if (a0 >= 0) a *= ys[a0];
     if (a1 >= 0) a *= ys[a1];
     if (a2 >= 0) a *= ys[a2];
-    if (kr != 0.0) {
+    if (rv >= 0) {
+        const double kr_k = kr[rv];
         int b0 = __ldg(fac + 3), b1 = __ldg(fac + 4), b2 = __ldg(fac + 5);
-        double b = kr;
+        double b = kr_k;
         if (b0 >= 0) b *= ys[b0];
         if (b1 >= 0) b *= ys[b1];
         if (b2 >= 0) b *= ys[b2];
@@ -192,8 +200,7 @@ __device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, c
     }
     __syncwarp(gm);
     for (int k = lane; k < m.R; k += G) {
-        const int rv = __ldg(m.rrev + k);
-        c.rs[k] = rate_term(m, k, c.ys, c.kf[k], rv >= 0 ? c.kr[rv] : 0.0);
+        c.rs[k] = rate_term(m, k, c.ys, c.kf[k], c.kr, __ldg(m.rrev + k));
     }
     __syncwarp(gm);
     if (G == 32) {
@@ -265,7 +272,7 @@ template <> __device__ __forceinline__ double tiny_pivot<double>() { return 1e-3
 // and later rows multiply instead of dividing.
 template <typename LT>
 __device__ __forceinline__ bool bad_pivot(LT u) {
-    return !(fabs((double)u) > (double)tiny_pivot<LT>()) || !isfinite((double)u);
+    return !(fabs(u) > tiny_pivot<LT>()) || !isfinite(u);
 }
 
 // Dense trailing block, right-looking.  Lane l owns block rows and columns
@@ -536,7 +543,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
 
     // inputs must be finite
     bool bad = false;
-    for (int i = lane; i < m.n_env; i += G) bad |= !isfinite(env_cell[i]);
+    for (int i = lane; i < m.n_env; i += G) bad |= !finite_bits(env_cell[i]);
     double z[QMAX + 1][NPL], e[NPL], ep[NPL], w[NPL], f[NPL], t1[NPL];
     double atl[NPL];
 #pragma unroll
@@ -548,7 +555,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
             v = y_cell[sp];
             a = atol[atol_len == 1 ? 0 : sp];
         }
-        bad |= !isfinite(v);
+        bad |= !finite_bits(v);
 #pragma unroll
         for (int j = 0; j <= QMAX; j++) z[j][s] = 0.0;
         z[0][s] = v;
@@ -576,7 +583,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
     auto any_nonfinite = [&](const double(&v)[NPL]) {
         bool b2 = false;
 #pragma unroll
-        for (int s = 0; s < NPL; s++) b2 |= !isfinite(v[s]);
+        for (int s = 0; s < NPL; s++) b2 |= !finite_bits(v[s]);
         return __any_sync(gm, b2) != 0;
     };
 
@@ -680,7 +687,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                         e[s] += (double)xl;
                         LT a = xl * (LT)w[s];
                         dsq += a * a;
-                        nf |= !isfinite((double)xl);
+                        nf |= !isfinite(xl);
                     }
                     double dn = sqrt((double)gsum_t<G, LT>(dsq, gm) / (double)n);
                     if (__any_sync(gm, nf) || !isfinite(dn)) break;

@@ -12,7 +12,8 @@ constexpr int G = 32;
 
 // Raise a kernel's dynamic shared-memory limit once to the maximum, so that
 // launches (possibly inside stream capture) make no further attribute calls.
-template <class K>
+// One flag per kernel instantiation (the tag), not per function type.
+template <int Tag, class K>
 cudaError_t allow_smem(K kern) {
     static int done_dev = -1;
     int dev = 0;
@@ -27,7 +28,7 @@ template <int NPL>
 cudaError_t launch_solve_npl(const DevMech &m, const SolveArgs &a, int grid, cudaStream_t s) {
     auto kern = campdev::k_solve<G, NPL, LT>;
     int smem = camp_cell_smem_bytes(m, (int)sizeof(LT)) * a.cpb;
-    cudaError_t e = allow_smem(kern);
+    cudaError_t e = allow_smem<NPL>(kern);
     if (e != cudaSuccess) return e;
     kern<<<grid, G * a.cpb, smem, s>>>(m, a);
     return cudaGetLastError();
@@ -37,7 +38,7 @@ template <int NPL>
 cudaError_t occupancy_npl(const DevMech &m, int cpb, int *blocks) {
     auto kern = campdev::k_solve<G, NPL, LT>;
     int smem = camp_cell_smem_bytes(m, (int)sizeof(LT)) * cpb;
-    cudaError_t e = allow_smem(kern);
+    cudaError_t e = allow_smem<NPL>(kern);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, G * cpb, smem);
 }
