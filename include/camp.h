@@ -193,6 +193,36 @@ int camp_solve_host(const camp_mech *m, int64_t n_cells, double *state, const do
                     double dt, double rtol, const double *atol, int32_t atol_len, int32_t *status,
                     const camp_solve_opts *opts, void *stream);
 
+/* ---- solving without allocating device memory ---------------------------- */
+/* camp_solve_host stages the chunk through device buffers it obtains with
+ * cudaMalloc (and, for the persistent grid, a work counter).  Some callers
+ * cannot let a library allocate: host models that hand all device memory to
+ * their own pool allocator, or run under a hard device-memory cap, where a
+ * hidden cudaMalloc fails or eats into the pool; time-stepping loops that
+ * must not stall on the device-wide synchronisation that cudaMalloc and
+ * cudaFree can cause while other streams are busy; and codes that must never
+ * see an out-of-memory error in the middle of a run.  This variant allocates
+ * nothing: it stages through one array of CAMP_STATIC_SCRATCH_BYTES that is
+ * part of the library's device image (every GPU that loads the library
+ * holds it until the process exits).
+ *   Same arguments and results as camp_solve_host (host arrays in and out,
+ *   synchronous on `stream`; opts->stats, if set, is a host array).
+ *   The chunk must fit: n_cells * (8 n_species + 8 n_env + 4 [+ 20 with
+ *   stats]) plus alignment must not exceed the array; larger calls return
+ *   CAMP_E_INVAL and touch nothing -- split the chunk.
+ *   The first call on a device looks up the array's device address (with
+ *   that device current) and caches it; make that first call before any
+ *   stream capture.
+ *   All calls share the array and leave their data in it; the work counter
+ *   is reset by every call.  Calls hold a process-wide lock and synchronise
+ *   their stream before returning; calls that still overlap on the GPU (for
+ *   example replays of a captured call on two streams) race on the array.
+ * The paper has no counterpart to this entry point. */
+#define CAMP_STATIC_SCRATCH_BYTES (16u << 20)
+int camp_solve_host_static(const camp_mech *m, int64_t n_cells, double *state, const double *env,
+                           double dt, double rtol, const double *atol, int32_t atol_len,
+                           int32_t *status, const camp_solve_opts *opts, void *stream);
+
 /* ---- several mechanisms in one call --------------------------------------- */
 /* One group of cells per mechanism (e.g. gas-only cells and cells carrying
  * aqueous phases).  Each group runs as its own persistent grid on a stream

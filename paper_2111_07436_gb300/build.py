@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcamp.so")
-SOURCES = ["capi.cu", "solve_f32.cu", "solve_f64.cu", "mech.cpp", "server.cpp", "probe.cu"]
+SOURCES = ["capi.cu", "solve_f32.cu", "solve_f64.cu", "mech.cpp", "server.cpp", "probe.cu", "static_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -74,7 +74,7 @@ EXPORTS = ["camp_mech_load", "camp_mech_compile", "camp_mech_free", "camp_mech_i
            "camp_solve_host", "camp_rate_constants", "camp_forcing", "camp_jacobian",
            "camp_lu_solve", "camp_last_error", "camp_server_create", "camp_server_submit",
            "camp_server_poll", "camp_server_wait", "camp_server_stats", "camp_server_destroy",
-           "camp_solve_batch", "camp_autotune", "camp_probe_fma_rate"]
+           "camp_solve_batch", "camp_autotune", "camp_probe_fma_rate", "camp_solve_host_static"]
 
 
 def lib():
@@ -117,6 +117,7 @@ def lib():
     L.camp_autotune.argtypes = [vp, i64, vp, vp, dbl, dbl, vp, i32, i32, ctypes.POINTER(i32),
                                 ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
     L.camp_probe_fma_rate.argtypes = [i32, ctypes.POINTER(dbl), vp]
+    L.camp_solve_host_static.argtypes = L.camp_solve.argtypes
     _lib = L
     return L
 

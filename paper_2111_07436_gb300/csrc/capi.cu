@@ -68,6 +68,8 @@ cudaError_t forcing_npl(const DevMech &m, long long n_cells, const double *state
 }
 }  // namespace
 
+int camp_record_error(int code, const char *msg) { return fail(code, msg); }
+
 int camp_pick_npl(int n) {
     const int need = (n + 31) / 32;
     const int avail[] = {1, 2, 3, 4, 6, 8};

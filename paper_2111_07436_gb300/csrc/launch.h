@@ -48,3 +48,6 @@ cudaError_t camp_launch_lu_solve_f32(const DevMech &m, long long n_cells, const 
 cudaError_t camp_launch_lu_solve_f64(const DevMech &m, long long n_cells, const double *state,
                                      const double *env, double gamma, const double *b, double *x,
                                      int *status, cudaStream_t s);
+
+// Record an error message for camp_last_error() and return `code`.
+int camp_record_error(int code, const char *msg);
