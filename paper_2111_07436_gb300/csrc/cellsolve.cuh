@@ -237,26 +237,52 @@ __device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, c
 // ---- Jacobian gather: J (or M = I - gamma J) at ys into LU storage -----------
 // mode 0: write M = I - gamma J into c.lu (zeroing fill and block entries)
 // mode 1: write J values to out[nnzJ] (species-CSR order)
+// In FP32 the rate constants and y are converted once into scratch that is
+// free at this point (the rate array and the substitution vector), so the
+// per-entry gather does no FP64/FP32 conversion.
 template <int G, typename LT>
 __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c, double gamma,
                                          int lane, unsigned gm, int mode, double *out) {
-    if (mode == 0) {
-        for (int i = lane; i < m.nlu; i += G) c.lu[i] = (LT)0;
-        __syncwarp(gm);
+    const LT *kfv, *krv, *yv;
+    const LT *jcv;
+    if constexpr (sizeof(LT) == 4) {
+        LT *kf32 = (LT *)c.rs, *kr32 = kf32 + m.R, *y32 = c.x;
+        for (int k = lane; k < m.R; k += G) kf32[k] = (LT)c.kf[k];
+        for (int k = lane; k < m.n_rev; k += G) kr32[k] = (LT)c.kr[k];
+        for (int p = lane; p < m.n; p += G) y32[p] = (LT)c.ys[p];
+        kfv = kf32;
+        krv = kr32;
+        yv = y32;
+        jcv = (const LT *)m.jc32;
+    } else {
+        kfv = (const LT *)c.kf;
+        krv = (const LT *)c.kr;
+        yv = (const LT *)c.ys;
+        jcv = (const LT *)m.jc;
     }
+    if (mode == 0) {  // 16-byte stores: the LU array starts 16-byte aligned
+        constexpr int V = 16 / sizeof(LT);
+        float4 *z4 = (float4 *)c.lu;
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int nv = m.nlu / V;
+        for (int i = lane; i < nv; i += G) z4[i] = zero;
+        for (int i = nv * V + lane; i < m.nlu; i += G) c.lu[i] = (LT)0;
+    }
+    __syncwarp(gm);
+    const LT g = (LT)gamma;
     for (int t = lane; t < m.nnzJ; t += G) {
         LT acc = (LT)0;
         int b = __ldg(m.jptr + t), e = __ldg(m.jptr + t + 1);
         for (int q = b; q < e; q++) {
             int k = __ldg(m.jk + q);
-            LT v = (LT)__ldg(m.jc + q) * (LT)(k >= 0 ? c.kf[k] : c.kr[-k - 1]);
+            LT v = __ldg(jcv + q) * (k >= 0 ? kfv[k] : krv[-k - 1]);
             int o1 = __ldg(m.jo + 2 * q), o2 = __ldg(m.jo + 2 * q + 1);
-            if (o1 >= 0) v *= (LT)c.ys[o1];
-            if (o2 >= 0) v *= (LT)c.ys[o2];
+            if (o1 >= 0) v *= yv[o1];
+            if (o2 >= 0) v *= yv[o2];
             acc += v;
         }
         if (mode == 0)
-            c.lu[__ldg(m.jdst + t)] = (__ldg(m.jdiag + t) ? (LT)1 : (LT)0) - (LT)gamma * acc;
+            c.lu[__ldg(m.jdst + t)] = (__ldg(m.jdiag + t) ? (LT)1 : (LT)0) - g * acc;
         else
             out[t] = (double)acc;
     }
@@ -275,50 +301,75 @@ __device__ __forceinline__ bool bad_pivot(LT u) {
     return !(fabs(u) > tiny_pivot<LT>()) || !isfinite(u);
 }
 
-// Dense trailing block, right-looking.  Lane l owns block rows and columns
-// l + 32 t (t < NS): it scales its rows' multipliers, then updates its
-// columns over all trailing rows (one broadcast load of the multiplier per
-// row serves both of its columns).  Two barriers per pivot.
+// Dense trailing block, right-looking in panels of W = 4 pivots.  For each
+// panel: (1) factor its W columns over the rows below (lane l owns rows
+// l + 32 t); (2) forward-substitute the W pivot rows to the right of the
+// panel with the panel's unit lower triangle (lane l owns columns l + 32 t);
+// (3) one rank-W update of the trailing block, each entry loaded and stored
+// once per panel (the W multipliers of a row are broadcast loads).
+// Pivots are checked and replaced by their reciprocals.
 template <int NS, typename LT>
 __device__ __forceinline__ bool dense_factor(LT *A, int D, int LD, int lane, unsigned gm) {
+    constexpr int W = 4;
     bool bad = false;
-    for (int k = 0; k < D; k++) {
-        const LT piv = A[k * LD + k];
-        bad |= bad_pivot(piv);
-        const LT rp = (LT)1 / piv;
+    for (int kp = 0; kp < D; kp += W) {
+        const int w = min(W, D - kp);
+        // (1) panel columns kp .. kp+w-1
+        for (int c = 0; c < w; c++) {
+            const int k = kp + c;
+            const LT piv = A[k * LD + k];
+            bad |= bad_pivot(piv);
+            const LT rp = (LT)1 / piv;
 #pragma unroll
-        for (int t = 0; t < NS; t++) {
-            const int i = lane + 32 * t;
-            if (i > k && i < D) A[i * LD + k] *= rp;
+            for (int t = 0; t < NS; t++) {
+                const int i = lane + 32 * t;
+                if (i > k && i < D) {
+                    LT *row = A + i * LD;
+                    const LT l = row[k] * rp;
+                    row[k] = l;
+                    for (int j = k + 1; j < kp + w; j++) row[j] -= l * A[k * LD + j];
+                }
+            }
+            __syncwarp(gm);
+            if (lane == 0) A[k * LD + k] = rp;
         }
-        __syncwarp(gm);
-        if (lane == 0) A[k * LD + k] = rp;
-        LT u[NS];
+        const int j0 = kp + w;
+        if (j0 >= D) break;
+        // (2) pivot rows of the panel, columns right of it: unit lower solve
+        LT u[W][NS];
         bool act[NS];
 #pragma unroll
         for (int t = 0; t < NS; t++) {
-            const int j = lane + 32 * t;
-            act[t] = j > k && j < D;
-            u[t] = act[t] ? A[k * LD + j] : (LT)0;
+            const int j = j0 + lane + 32 * t;
+            act[t] = j < D;
+#pragma unroll
+            for (int r = 0; r < W; r++) {
+                LT v = (LT)0;
+                if (act[t] && r < w) {
+                    v = A[(kp + r) * LD + j];
+                    for (int p = 0; p < r; p++) v -= A[(kp + r) * LD + kp + p] * u[p][t];
+                    A[(kp + r) * LD + j] = v;
+                }
+                u[r][t] = v;
+            }
         }
-        int i = k + 1;
-        for (; i + 1 < D; i += 2) {
-            const LT l0 = A[i * LD + k], l1 = A[(i + 1) * LD + k];
+        __syncwarp(gm);
+        // (3) trailing block: rank-w update
+        for (int i = j0; i < D; i++) {
+            const LT *li = A + i * LD + kp;
+            LT l[W];
+#pragma unroll
+            for (int r = 0; r < W; r++) l[r] = r < w ? li[r] : (LT)0;
 #pragma unroll
             for (int t = 0; t < NS; t++) {
                 if (act[t]) {
-                    LT *p0 = A + i * LD + lane + 32 * t;
-                    const LT a0 = p0[0], a1 = p0[LD];
-                    p0[0] = a0 - l0 * u[t];
-                    p0[LD] = a1 - l1 * u[t];
+                    LT *a = A + i * LD + j0 + lane + 32 * t;
+                    LT v = *a;
+#pragma unroll
+                    for (int r = 0; r < W; r++) v -= l[r] * u[r][t];
+                    *a = v;
                 }
             }
-        }
-        if (i < D) {
-            const LT l0 = A[i * LD + k];
-#pragma unroll
-            for (int t = 0; t < NS; t++)
-                if (act[t]) A[i * LD + lane + 32 * t] -= l0 * u[t];
         }
         __syncwarp(gm);
     }
@@ -515,8 +566,8 @@ __device__ __forceinline__ void nord_rescale(double (&z)[QMAX + 1][NPL], int q, 
 // x^p for the step-size and order heuristics.  Only the accept/reject tests
 // need FP64; a step-size factor needs a few digits, so this takes FP32
 // log2/exp2 (x = 0 gives 0 for p > 0 and +inf for p < 0).
-__device__ __forceinline__ double ctl_pow(double x, double p) {
-    return (double)exp2f((float)p * __log2f((float)x));
+__device__ __forceinline__ float ctl_powf(float x, float p) {
+    return exp2f(p * __log2f(x));
 }
 
 // 1/d for d > 0 to ~1e-14 relative: an FP32 estimate refined by one
@@ -617,15 +668,21 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
 
     int q = 1, qwait = 2, nst = 0, nst_lu = 0;
     bool have_lu = false, need_setup = true, ep_valid = false;
-    double t = 0.0, gamma_lu = 0.0;
+    double t = 0.0, gamma_lu = 0.0, rgamma_lu = 0.0;
     int status = ST_OK;
+    // Squared-norm forms of the controller's tests (same decisions as
+    // comparing the norms themselves): Newton converged when
+    // dn^2 min(1, rho^2) <= tol^2, diverged when rho^2 > RHO_DIV^2; the step
+    // is accepted when ecoef^2 mean((e w)^2) <= 1.
+    constexpr double NEWTON_TOL2 = NEWTON_TOL * NEWTON_TOL;
+    constexpr double RHO_DIV2 = RHO_DIV * RHO_DIV;
 
     while (t < T) {
         if (nst >= max_steps) { status = ST_MAXSTEPS; break; }
         set_weights();
         int nef = 0, ncf = 0;
         bool last = false;
-        double err = 0.0;
+        double err2 = 0.0;
         bool accepted = false;
         while (!accepted) {
             last = false;
@@ -638,10 +695,10 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                 last = true;
             }
             nord_predict<NPL>(z, q);
-            const double l1 = m.lcoef[q][1];
-            const double gamma = h / l1;
+            const double rl1 = m.inv_l1[q];
+            const double gamma = h * rl1;
             bool jcur = false, lu_fail = false;
-            if (!have_lu || need_setup || nst >= nst_lu + MSBJ || fabs(gamma / gamma_lu - 1.0) > DGMAX) {
+            if (!have_lu || need_setup || nst >= nst_lu + MSBJ || fabs(gamma * rgamma_lu - 1.0) > DGMAX) {
 #pragma unroll
                 for (int s = 0; s < NPL; s++) {
                     int p = lane + G * s;
@@ -652,6 +709,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                 lu_fail = !factor<G, LT>(m, c, lane, gm);
                 st.jac++;
                 gamma_lu = gamma;
+                rgamma_lu = 1.0 / gamma;
                 nst_lu = nst;
                 have_lu = !lu_fail;
                 need_setup = false;
@@ -660,10 +718,10 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
             // modified Newton on G(e) = e - gamma f(z0 + e) + z1 / l1
             bool conv = false;
             if (!lu_fail) {
-                double dprev = 0.0;
+                LT dprev2 = (LT)0;
 #pragma unroll
                 for (int s = 0; s < NPL; s++) e[s] = 0.0;
-                const double scale = (gamma != gamma_lu) ? 2.0 / (1.0 + gamma / gamma_lu) : 1.0;
+                const LT scale = (gamma != gamma_lu) ? (LT)2 / ((LT)1 + (LT)(gamma * rgamma_lu)) : (LT)1;
                 for (int it = 0; it < NEWTON_MAXIT; it++) {
 #pragma unroll
                     for (int s = 0; s < NPL; s++) t1[s] = z[0][s] + e[s];
@@ -673,7 +731,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
 #pragma unroll
                     for (int s = 0; s < NPL; s++) {
                         int p = lane + G * s;
-                        if (p < n) c.x[p] = (LT)(-(e[s] - gamma * f[s] + z[1][s] / l1));
+                        if (p < n) c.x[p] = (LT)(-(e[s] - gamma * f[s] + z[1][s] * rl1));
                     }
                     substitute<G, LT>(m, c, lane, gm);
                     // the update's norm in the LU precision (it only steers the iteration)
@@ -683,22 +741,22 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                     for (int s = 0; s < NPL; s++) {
                         int p = lane + G * s;
                         LT xl = (p < n) ? c.x[p] : (LT)0;
-                        if (scale != 1.0) xl *= (LT)scale;
+                        xl *= scale;
                         e[s] += (double)xl;
                         LT a = xl * (LT)w[s];
                         dsq += a * a;
                         nf |= !isfinite(xl);
                     }
-                    double dn = sqrt((double)gsum_t<G, LT>(dsq, gm) / (double)n);
-                    if (__any_sync(gm, nf) || !isfinite(dn)) break;
-                    double test = dn;
+                    const LT dn2 = gsum_t<G, LT>(dsq, gm) * (LT)m.rn;
+                    if (__any_sync(gm, nf) || !isfinite(dn2)) break;
+                    LT test2 = dn2;
                     if (it > 0) {
-                        double rho = dn / dprev;
-                        if (rho > RHO_DIV) break;
-                        if (rho < 1.0) test = dn * rho;
+                        const LT rho2 = dn2 / dprev2;
+                        if (rho2 > (LT)RHO_DIV2) break;
+                        if (rho2 < (LT)1) test2 = dn2 * rho2;
                     }
-                    if (test <= NEWTON_TOL) { conv = true; break; }
-                    dprev = dn;
+                    if (test2 <= (LT)NEWTON_TOL2) { conv = true; break; }
+                    dprev2 = dn2;
                 }
             }
             if (!conv) {
@@ -712,8 +770,13 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                 qwait = q + 1;
                 continue;
             }
-            err = m.ecoef[q] * wrms<G, NPL>(m, e, w, gm);
-            if (err > 1.0) {
+            {
+                double es = 0.0;
+#pragma unroll
+                for (int s = 0; s < NPL; s++) { double a = e[s] * w[s]; es += a * a; }
+                err2 = m.ecoef2[q] * (gsum<G>(es, gm) * m.rn);
+            }
+            if (err2 > 1.0) {
                 nord_retract<NPL>(z, q);
                 st.errfail++;
                 if (++nef >= MAX_NEF) { status = ST_ERRTEST; break; }
@@ -725,11 +788,12 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
 #pragma unroll
                     for (int s = 0; s < NPL; s++) z[1][s] = h * f[s];
                 } else {
-                    double eta = 0.9 * ctl_pow(err, -1.0 / (q + 1));
-                    if (eta < 0.2) eta = 0.2;
-                    h *= eta;
+                    // 0.9 err^(-1/(q+1)) = 0.9 (err^2)^(-1/(2(q+1)))
+                    float eta = 0.9f * ctl_powf((float)err2, -0.5f / (float)(q + 1));
+                    if (eta < 0.2f) eta = 0.2f;
+                    h *= (double)eta;
                     if (h < hmin) { status = ST_ERRTEST; break; }
-                    nord_rescale<NPL>(z, q, eta);
+                    nord_rescale<NPL>(z, q, (double)eta);
                 }
                 qwait = q + 1;
                 continue;
@@ -753,8 +817,9 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
         if (any_nonfinite(z[0])) { status = ST_NONFINITE; break; }
 
         if (--qwait <= 0 && t < T) {
-            double eta_q = 1.0 / (ctl_pow(1.2 * err, 1.0 / (q + 1)) + 1e-6);
-            double eta_m = 0.0, eta_p = 0.0;
+            // eta = 1 / ((c err)^(1/(p+1)) + 1e-6), taken from squared norms
+            float eta_q = 1.0f / (ctl_powf(1.44f * (float)err2, 0.5f / (float)(q + 1)) + 1e-6f);
+            float eta_m = 0.0f, eta_p = 0.0f;
             if (q > 1) {
                 double zs = 0.0;
 #pragma unroll
@@ -764,23 +829,24 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                         for (int s = 0; s < NPL; s++) { double a = z[j][s] * w[s]; zs += a * a; }
                     }
                 }
-                double em = m.ecoef[q - 1] * m.fact[q] * sqrt(gsum<G>(zs, gm) / (double)n);
-                eta_m = 1.0 / (ctl_pow(1.3 * em, 1.0 / q) + 1e-6);
+                const double em2 = m.ecoef2[q - 1] * m.fact[q] * m.fact[q] * (gsum<G>(zs, gm) * m.rn);
+                eta_m = 1.0f / (ctl_powf(1.69f * (float)em2, 0.5f / (float)q) + 1e-6f);
             }
             if (q < QMAX && ep_valid) {
+                double ds = 0.0;
 #pragma unroll
-                for (int s = 0; s < NPL; s++) t1[s] = e[s] - ep[s];
-                double epl = m.ecoef[q + 1] * wrms<G, NPL>(m, t1, w, gm);
-                eta_p = 1.0 / (ctl_pow(1.4 * epl, 1.0 / (q + 2)) + 1e-6);
+                for (int s = 0; s < NPL; s++) { double a = (e[s] - ep[s]) * w[s]; ds += a * a; }
+                const double ep2 = m.ecoef2[q + 1] * (gsum<G>(ds, gm) * m.rn);
+                eta_p = 1.0f / (ctl_powf(1.96f * (float)ep2, 0.5f / (float)(q + 2)) + 1e-6f);
             }
-            double eta = eta_q;
+            float eta = eta_q;
             int qn = q;
             if (eta_m > eta) { eta = eta_m; qn = q - 1; }
             if (eta_p > eta) { eta = eta_p; qn = q + 1; }
-            if (eta < ETA_THRESH) {
+            if (eta < (float)ETA_THRESH) {
                 qwait = 2;
             } else {
-                if (eta > ETA_MAX) eta = ETA_MAX;
+                if (eta > (float)ETA_MAX) eta = (float)ETA_MAX;
                 if (qn == q + 1) {
                     const double c_up = m.lcoef[q][q] / (double)(q + 1);
 #pragma unroll
@@ -792,8 +858,8 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                     }
                 }
                 q = qn;
-                h *= eta;
-                nord_rescale<NPL>(z, q, eta);
+                h *= (double)eta;
+                nord_rescale<NPL>(z, q, (double)eta);
                 qwait = q + 1;
             }
         }

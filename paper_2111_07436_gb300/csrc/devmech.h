@@ -61,6 +61,7 @@ struct DevMech {
     const int *jk;        // [nj] process k (forward constant) or -(r+1), r = rrev[k] (reverse)
     const int *jo;        // [nj][2] other factor positions, -1 = none
     const double *jc;     // [nj] coefficient (net stoich x multiplicity, signed)
+    const float *jc32;    // [nj] the same coefficients in FP32 (mixed form)
 
     // --- LU storage: sparse rows [0, nsp) then a dense trailing block ---
     int nlu;              // storage entries
@@ -97,4 +98,9 @@ struct DevMech {
     double lcoef[CAMP_QMAX + 2][CAMP_QMAX + 2];
     double ecoef[CAMP_QMAX + 2];
     double fact[CAMP_QMAX + 2];
+    // the same, arranged so the step controller multiplies instead of
+    // dividing and compares squares instead of taking roots
+    double inv_l1[CAMP_QMAX + 2];   // 1 / l_1(q)
+    double ecoef2[CAMP_QMAX + 2];   // ecoef(q)^2
+    double rn;                      // 1 / n
 };

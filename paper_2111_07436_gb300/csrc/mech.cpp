@@ -417,6 +417,7 @@ static void build_tables(HostMech &h) {
             }
             h.jptr.push_back((int)h.jk.size());
         }
+    h.jc32.assign(h.jc.begin(), h.jc.end());
 
     // sparse factorisation ops, row by row; levels: sparse rows by level, then
     // every block row in one final level (they only need sparse pivots)
@@ -529,6 +530,11 @@ void bdf_coefficients(DevMech &dm) {
     }
     dm.fact[0] = 1.0;
     for (int i = 1; i <= CAMP_QMAX + 1; i++) dm.fact[i] = dm.fact[i - 1] * i;
+    for (int q = 0; q <= CAMP_QMAX + 1; q++) {
+        dm.inv_l1[q] = q > 0 ? 1.0 / dm.lcoef[q][1] : 0.0;
+        dm.ecoef2[q] = dm.ecoef[q] * dm.ecoef[q];
+    }
+    dm.rn = dm.n > 0 ? 1.0 / (double)dm.n : 0.0;
 }
 
 // ---- packing ---------------------------------------------------------------
@@ -574,6 +580,7 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.jk = pk.put(h.jk);
     dm.jo = pk.put(h.jo);
     dm.jc = pk.put(h.jc);
+    dm.jc32 = pk.put(h.jc32);
     dm.nlu = h.nlu;
     dm.d = h.d;
     dm.D = h.D;

@@ -40,6 +40,7 @@ struct HostMech {
     std::vector<int> flane_ptr, flane_pos;
     std::vector<int> jptr, jdst, jdiag, jk, jo;
     std::vector<double> jc;
+    std::vector<float> jc32;
     int nlu = 0, d = 0, D = 0, LD = 0, dbase = 0;
     std::vector<int> flev_ptr, frow, fops_ptr;
     std::vector<uint32_t> fops;
