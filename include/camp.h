@@ -147,7 +147,8 @@ typedef struct {
                                 counter; 0: one group of lanes per cell, static
                                 grid; -1: the autotuned choice (default) */
     int32_t max_steps;       /* internal steps per cell (default 10000) */
-    int32_t cells_per_block; /* 0: autotuned choice, else the library default */
+    int32_t cells_per_block; /* 0: the autotuned choice if any, else the
+                                count (1..4) with the most resident cells */
     double hmin_frac;        /* minimum step = hmin_frac * dt (default 1e-10) */
     int32_t *stats;          /* optional device [n_cells][CAMP_NSTATS]: steps,
                                 Newton iterations, Jacobian/LU setups,
@@ -249,7 +250,7 @@ int camp_solve_batch(const camp_group *groups, int32_t n_groups, double dt, doub
 
 /* ---- launch autotuning ------------------------------------------------------ */
 /* Time camp_solve on the given cells (device arrays, left unchanged) for
- * cells-per-block 1, 2 and 4 and both grid mappings, and make the fastest the
+ * cells-per-block 1 to 4 and both grid mappings, and make the fastest the
  * mechanism's default for `variant` (used when opts.cells_per_block is 0 and
  * opts.persistent is -1).  Synchronous; allocates scratch for one copy of
  * the state.  *best_cpb / *best_persistent (may be NULL) receive the choice;

@@ -271,9 +271,26 @@ int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double
     if (o.persistent < 0)
         o.persistent = m->tuned_persistent[o.variant] >= 0 ? m->tuned_persistent[o.variant]
                                                            : (o.variant == CAMP_VARIANT_MIXED ? 1 : 0);
-    int cpb = o.cells_per_block > 0 ? o.cells_per_block
-              : m->tuned_cpb[o.variant] > 0 ? m->tuned_cpb[o.variant]
-                                            : (smem_cell > 8192 ? 1 : 2);
+    auto occupancy = [&](int cpb_, int *per_sm) -> cudaError_t {
+        if (m->occ[o.variant][cpb_] == 0) {
+            cudaError_t e = f32 ? camp_occupancy_f32(m->dm, cpb_, per_sm) : camp_occupancy_f64(m->dm, cpb_, per_sm);
+            if (e != cudaSuccess) return e;
+            m->occ[o.variant][cpb_] = *per_sm > 0 ? *per_sm : -1;
+        }
+        *per_sm = m->occ[o.variant][cpb_] > 0 ? m->occ[o.variant][cpb_] : 0;
+        return cudaSuccess;
+    };
+    int cpb = o.cells_per_block > 0 ? o.cells_per_block : m->tuned_cpb[o.variant];
+    if (cpb <= 0) {  // most resident cells per SM, fewest cells per block on ties
+        int best = 0;
+        cpb = 1;
+        for (int c2 = 1; c2 <= 4; c2++) {
+            if (c2 * smem_cell > kMaxSmem) break;
+            int per_sm = 0;
+            CUDA_TRY(occupancy(c2, &per_sm));
+            if (per_sm * c2 > best) { best = per_sm * c2; cpb = c2; }
+        }
+    }
     cpb = std::min(cpb, 4);
     while (cpb > 1 && cpb * smem_cell > kMaxSmem) cpb--;
 
@@ -301,11 +318,8 @@ int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double
             if (!m->own_ws) CUDA_TRY(cudaMalloc(&m->own_ws, camp_workspace_bytes()));
             q = m->own_ws;
         }
-        int per_sm = m->occ[o.variant][cpb];
-        if (per_sm == 0) {
-            CUDA_TRY(f32 ? camp_occupancy_f32(m->dm, cpb, &per_sm) : camp_occupancy_f64(m->dm, cpb, &per_sm));
-            m->occ[o.variant][cpb] = per_sm;
-        }
+        int per_sm = 0;
+        CUDA_TRY(occupancy(cpb, &per_sm));
         if (per_sm < 1) return fail(CAMP_E_UNSUPPORTED, "kernel does not fit on an SM");
         grid = std::min<long long>((long long)per_sm * m->sm_count, (n_cells + cpb - 1) / cpb);
         CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(unsigned long long), s));
@@ -431,11 +445,11 @@ int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const doub
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
-    const int cpbs[3] = {1, 2, 4};
+    const int cpbs[4] = {1, 2, 3, 4};
     float best = 1e30f;
     int bc = 1, bp = 1, rc = CAMP_OK;
     for (int pers = 0; pers <= 1 && rc == CAMP_OK; pers++)
-        for (int ci = 0; ci < 3 && rc == CAMP_OK; ci++) {
+        for (int ci = 0; ci < 4 && rc == CAMP_OK; ci++) {
             const int smem_cell = camp_cell_smem_bytes(m->dm, variant == CAMP_VARIANT_MIXED ? 4 : 8);
             if (cpbs[ci] * smem_cell > kMaxSmem) continue;
             camp_solve_opts o;

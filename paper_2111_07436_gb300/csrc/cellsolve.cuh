@@ -165,26 +165,34 @@ __device__ __forceinline__ bool finite_bits(double x) {
 }
 
 // ---- forcing f(y): rates of all processes, then a per-position gather --------
-// r_k = kf prod(forward factors) - kr prod(reverse factors); rv < 0 marks an
-// irreversible process.
+// r_k = kf prod(forward factors) - kr prod(reverse factors), from the
+// process's packed record (16-bit fields, 0xffff = none).
+__device__ __forceinline__ int lo16(int v) { return v & 0xffff; }
+__device__ __forceinline__ int hi16(int v) { return (int)((unsigned)v >> 16); }
+constexpr int NONE16 = 0xffff;
+
 __device__ __forceinline__ double rate_term(const DevMech &m, int k, const double *ys, double kf,
-                                            const double *kr, int rv) {
-    const int *fac = m.rfac + 6 * k;
-    int a0 = __ldg(fac), a1 = __ldg(fac + 1), a2 = __ldg(fac + 2);
+                                            const double *kr) {
+    const int4 rp = __ldg(m.rpack + k);
+    const int a0 = lo16(rp.x), a1 = hi16(rp.x), a2 = lo16(rp.y), rv = hi16(rp.y);
     double a = kf;
-    if (a0 >= 0) a *= ys[a0];
-    if (a1 >= 0) a *= ys[a1];
-    if (a2 >= 0) a *= ys[a2];
-    if (rv >= 0) {
-        const double kr_k = kr[rv];
-        int b0 = __ldg(fac + 3), b1 = __ldg(fac + 4), b2 = __ldg(fac + 5);
-        double b = kr_k;
-        if (b0 >= 0) b *= ys[b0];
-        if (b1 >= 0) b *= ys[b1];
-        if (b2 >= 0) b *= ys[b2];
+    if (a0 != NONE16) a *= ys[a0];
+    if (a1 != NONE16) a *= ys[a1];
+    if (a2 != NONE16) a *= ys[a2];
+    if (rv != NONE16) {
+        const int b0 = lo16(rp.z), b1 = hi16(rp.z), b2 = lo16(rp.w);
+        double b = kr[rv];
+        if (b0 != NONE16) b *= ys[b0];
+        if (b1 != NONE16) b *= ys[b1];
+        if (b2 != NONE16) b *= ys[b2];
         a -= b;
     }
     return a;
+}
+
+__device__ __forceinline__ double gather_entry(const DevMech &m, int q, const double *rs) {
+    const int4 g = __ldg(m.fpack + q);
+    return __hiloint2double(g.y, g.x) * rs[g.z];
 }
 
 // y (own positions, registers) -> f (own positions).  The per-position sums
@@ -199,19 +207,16 @@ __device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, c
         if (p < m.n) c.ys[p] = y[s];
     }
     __syncwarp(gm);
-    for (int k = lane; k < m.R; k += G) {
-        c.rs[k] = rate_term(m, k, c.ys, c.kf[k], c.kr, __ldg(m.rrev + k));
-    }
+    for (int k = lane; k < m.R; k += G) c.rs[k] = rate_term(m, k, c.ys, c.kf[k], c.kr);
     __syncwarp(gm);
     if (G == 32) {
         double *fs = c.ys;  // y is no longer needed
         const int b0 = __ldg(m.flane_ptr + lane), b1 = __ldg(m.flane_ptr + lane + 1);
         for (int i = b0; i < b1; i++) {
-            const int p = __ldg(m.flane_pos + i);
-            const int b = __ldg(m.fptr + p), e = __ldg(m.fptr + p + 1);
+            const int4 job = __ldg(m.flane_job + i);
             double acc = 0.0;
-            for (int q = b; q < e; q++) acc += __ldg(m.fc + q) * c.rs[__ldg(m.fk + q)];
-            fs[p] = acc;
+            for (int q = job.y; q < job.z; q++) acc += gather_entry(m, q, c.rs);
+            fs[job.x] = acc;
         }
         __syncwarp(gm);
 #pragma unroll
@@ -227,7 +232,7 @@ __device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, c
             double acc = 0.0;
             if (p < m.n) {
                 int b = __ldg(m.fptr + p), e = __ldg(m.fptr + p + 1);
-                for (int q = b; q < e; q++) acc += __ldg(m.fc + q) * c.rs[__ldg(m.fk + q)];
+                for (int q = b; q < e; q++) acc += gather_entry(m, q, c.rs);
             }
             f[s] = acc;
         }
@@ -244,7 +249,6 @@ template <int G, typename LT>
 __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c, double gamma,
                                          int lane, unsigned gm, int mode, double *out) {
     const LT *kfv, *krv, *yv;
-    const LT *jcv;
     if constexpr (sizeof(LT) == 4) {
         LT *kf32 = (LT *)c.rs, *kr32 = kf32 + m.R, *y32 = c.x;
         for (int k = lane; k < m.R; k += G) kf32[k] = (LT)c.kf[k];
@@ -253,12 +257,10 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
         kfv = kf32;
         krv = kr32;
         yv = y32;
-        jcv = (const LT *)m.jc32;
     } else {
         kfv = (const LT *)c.kf;
         krv = (const LT *)c.kr;
         yv = (const LT *)c.ys;
-        jcv = (const LT *)m.jc;
     }
     if (mode == 0) {  // 16-byte stores: the LU array starts 16-byte aligned
         constexpr int V = 16 / sizeof(LT);
@@ -272,17 +274,28 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
     const LT g = (LT)gamma;
     for (int t = lane; t < m.nnzJ; t += G) {
         LT acc = (LT)0;
-        int b = __ldg(m.jptr + t), e = __ldg(m.jptr + t + 1);
-        for (int q = b; q < e; q++) {
-            int k = __ldg(m.jk + q);
-            LT v = __ldg(jcv + q) * (k >= 0 ? kfv[k] : krv[-k - 1]);
-            int o1 = __ldg(m.jo + 2 * q), o2 = __ldg(m.jo + 2 * q + 1);
-            if (o1 >= 0) v *= yv[o1];
-            if (o2 >= 0) v *= yv[o2];
+        const int4 nz = __ldg(m.jnz + t);
+        for (int q = nz.x; q < nz.y; q++) {
+            LT v;
+            int k, oo;
+            if constexpr (sizeof(LT) == 4) {
+                const int4 je = __ldg(m.jpack + q);
+                k = je.y;
+                oo = je.z;
+                v = __int_as_float(je.x);
+            } else {
+                k = __ldg(m.jk + q);
+                oo = lo16(__ldg(m.jo + 2 * q)) | (lo16(__ldg(m.jo + 2 * q + 1)) << 16);
+                v = (LT)__ldg(m.jc + q);
+            }
+            v *= (k >= 0 ? kfv[k] : krv[-k - 1]);
+            const int o1 = lo16(oo), o2 = hi16(oo);
+            if (o1 != NONE16) v *= yv[o1];
+            if (o2 != NONE16) v *= yv[o2];
             acc += v;
         }
         if (mode == 0)
-            c.lu[__ldg(m.jdst + t)] = (__ldg(m.jdiag + t) ? (LT)1 : (LT)0) - g * acc;
+            c.lu[nz.z] = (nz.w ? (LT)1 : (LT)0) - g * acc;
         else
             out[t] = (double)acc;
     }
@@ -479,7 +492,10 @@ __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, uns
             int i = __ldg(m.frow + r);
             LT s = x[i];
             int qb = __ldg(m.sl_ptr + i), qe = __ldg(m.sl_ptr + i + 1);
-            for (int q = qb; q < qe; q++) s -= lu[__ldg(m.sl_off + q)] * x[__ldg(m.sl_col + q)];
+            for (int q = qb; q < qe; q++) {
+                const int e2 = __ldg(m.sl_pack + q);
+                s -= lu[lo16(e2)] * x[hi16(e2)];
+            }
             x[i] = s;
         }
         __syncwarp(gm);
@@ -500,7 +516,10 @@ __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, uns
             int i = __ldg(m.brow + r);
             LT s = x[i];
             int qb = __ldg(m.su_ptr + i), qe = __ldg(m.su_ptr + i + 1);
-            for (int q = qb; q < qe; q++) s -= lu[__ldg(m.su_off + q)] * x[__ldg(m.su_col + q)];
+            for (int q = qb; q < qe; q++) {
+                const int e2 = __ldg(m.su_pack + q);
+                s -= lu[lo16(e2)] * x[hi16(e2)];
+            }
             x[i] = s * lu[__ldg(m.udiag + i)];
         }
         __syncwarp(gm);

@@ -7,6 +7,7 @@
 // loads and stores translate back to declaration order.
 #pragma once
 #include <stdint.h>
+#include <vector_types.h>
 
 #define CAMP_QMAX 5
 #define CAMP_MAXFAC 3  // at most 3 factors (with multiplicity) per rate term
@@ -52,6 +53,23 @@ struct DevMech {
     // positions each of the 32 lanes sums, balanced by gather length
     const int *flane_ptr; // [33]
     const int *flane_pos; // [n]
+
+    // --- the same tables packed so one 16-byte load serves one record ---
+    // rate term k: x = fwd0 | fwd1 << 16, y = fwd2 | rv << 16,
+    //              z = rev0 | rev1 << 16, w = rev2  (16-bit fields, 0xffff = none)
+    const int4 *rpack;    // [R]
+    // gather entry q: (x, y) = bits of the FP64 coefficient, z = process
+    const int4 *fpack;    // [nf]
+    // lane job i: x = position, y = first entry, z = end entry
+    const int4 *flane_job;// [n], lanes' jobs in flane_ptr ranges
+    // Jacobian non-zero t: x = first entry, y = end entry, z = LU offset, w = diagonal
+    const int4 *jnz;      // [nnzJ]
+    // Jacobian entry q: x = bits of the FP32 coefficient, y = constant index
+    // (k, or -(r+1) for a reverse constant), z = o1 | o2 << 16
+    const int4 *jpack;    // [nj]
+    // substitution entries: off | col << 16
+    const int *sl_pack;   // [len(sl_off)]
+    const int *su_pack;   // [len(su_off)]
 
     // --- Jacobian gather, by Jacobian non-zero ---
     int nnzJ;

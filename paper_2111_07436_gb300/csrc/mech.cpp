@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <stdexcept>
 #include <string>
 #include <unordered_map>
@@ -175,6 +176,60 @@ static double net_coef(const Process &p, int s) {
     for (auto &e : p.react) if (e.first == s) v -= e.second;
     for (auto &e : p.prod) if (e.first == s) v += e.second;
     return v;
+}
+
+static int field16(int v) {
+    if (v < -1 || v > 32766) throw std::runtime_error("index does not fit a 16-bit table field");
+    return v < 0 ? 0xffff : v;
+}
+
+static void pack_records(HostMech &h) {
+    const int R = (int)h.procs.size(), n = h.n;
+    h.rpack.assign((size_t)R * 4, 0);
+    for (int k = 0; k < R; k++) {
+        const int *f = &h.rfac[(size_t)k * 6];
+        int *o = &h.rpack[(size_t)k * 4];
+        o[0] = field16(f[0]) | (field16(f[1]) << 16);
+        o[1] = field16(f[2]) | (field16(h.rrev[k]) << 16);
+        o[2] = field16(f[3]) | (field16(f[4]) << 16);
+        o[3] = field16(f[5]);
+    }
+    h.fpack.assign(h.fk.size() * 4, 0);
+    for (size_t q = 0; q < h.fk.size(); q++) {
+        uint64_t bits;
+        std::memcpy(&bits, &h.fc[q], 8);
+        h.fpack[q * 4 + 0] = (int)(uint32_t)(bits & 0xffffffffu);
+        h.fpack[q * 4 + 1] = (int)(uint32_t)(bits >> 32);
+        h.fpack[q * 4 + 2] = h.fk[q];
+    }
+    h.flane_job.assign((size_t)n * 4, 0);
+    for (int i = 0; i < n; i++) {
+        int p = h.flane_pos[i];
+        h.flane_job[(size_t)i * 4 + 0] = p;
+        h.flane_job[(size_t)i * 4 + 1] = h.fptr[p];
+        h.flane_job[(size_t)i * 4 + 2] = h.fptr[p + 1];
+    }
+    const int nnzJ = (int)h.colidx.size();
+    h.jnz.assign((size_t)nnzJ * 4, 0);
+    for (int t = 0; t < nnzJ; t++) {
+        h.jnz[(size_t)t * 4 + 0] = h.jptr[t];
+        h.jnz[(size_t)t * 4 + 1] = h.jptr[t + 1];
+        h.jnz[(size_t)t * 4 + 2] = h.jdst[t];
+        h.jnz[(size_t)t * 4 + 3] = h.jdiag[t];
+    }
+    h.jpack.assign(h.jk.size() * 4, 0);
+    for (size_t q = 0; q < h.jk.size(); q++) {
+        float c = (float)h.jc[q];
+        int cb;
+        std::memcpy(&cb, &c, 4);
+        h.jpack[q * 4 + 0] = cb;
+        h.jpack[q * 4 + 1] = h.jk[q];
+        h.jpack[q * 4 + 2] = field16(h.jo[2 * q]) | (field16(h.jo[2 * q + 1]) << 16);
+    }
+    h.sl_pack.resize(h.sl_off.size());
+    for (size_t q = 0; q < h.sl_off.size(); q++) h.sl_pack[q] = field16(h.sl_off[q]) | (field16(h.sl_col[q]) << 16);
+    h.su_pack.resize(h.su_off.size());
+    for (size_t q = 0; q < h.su_off.size(); q++) h.su_pack[q] = field16(h.su_off[q]) | (field16(h.su_col[q]) << 16);
 }
 
 static void build_structure(HostMech &h) {
@@ -517,6 +572,7 @@ HostMech compile_mechanism(const char *json, size_t len) {
     if (h.n < 1) throw std::runtime_error("mechanism has no species");
     build_structure(h);
     build_tables(h);
+    pack_records(h);
     return h;
 }
 
@@ -602,6 +658,13 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.su_col = pk.put(h.su_col);
     dm.udiag = pk.put(h.udiag);
     dm.perm = pk.put(h.perm);
+    dm.rpack = reinterpret_cast<const int4 *>(pk.put(h.rpack));
+    dm.fpack = reinterpret_cast<const int4 *>(pk.put(h.fpack));
+    dm.flane_job = reinterpret_cast<const int4 *>(pk.put(h.flane_job));
+    dm.jnz = reinterpret_cast<const int4 *>(pk.put(h.jnz));
+    dm.jpack = reinterpret_cast<const int4 *>(pk.put(h.jpack));
+    dm.sl_pack = pk.put(h.sl_pack);
+    dm.su_pack = pk.put(h.su_pack);
     bdf_coefficients(dm);
     return pk.img;
 }
