@@ -272,6 +272,32 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
     }
     __syncwarp(gm);
     const LT g = (LT)gamma;
+    if constexpr (sizeof(LT) == 4) {
+        if (G == 32) {
+            // flat per-lane entry list: independent loads, one store per non-zero
+            const int b = __ldg(m.jl_ptr + lane), e = __ldg(m.jl_ptr + lane + 1);
+            LT acc = (LT)0;
+#pragma unroll 4
+            for (int i = b; i < e; i++) {
+                const int4 r = __ldg(m.jl_rec + i);
+                const int k = (int)(short)(r.y & 0xffff);
+                const int o1 = hi16(r.y), o2 = lo16(r.w);
+                LT v = __int_as_float(r.x) * (k >= 0 ? kfv[k] : krv[-k - 1]);
+                if (o1 != NONE16) v *= yv[o1];
+                if (o2 != NONE16) v *= yv[o2];
+                acc += v;
+                if (r.z & (1 << 17)) {
+                    if (mode == 0)
+                        c.lu[r.z & 0xffff] = ((r.z >> 16) & 1 ? (LT)1 : (LT)0) - g * acc;
+                    else
+                        out[hi16(r.w)] = (double)acc;
+                    acc = (LT)0;
+                }
+            }
+            __syncwarp(gm);
+            return;
+        }
+    }
     for (int t = lane; t < m.nnzJ; t += G) {
         LT acc = (LT)0;
         const int4 nz = __ldg(m.jnz + t);
@@ -367,19 +393,53 @@ __device__ __forceinline__ bool dense_factor(LT *A, int D, int LD, int lane, uns
             }
         }
         __syncwarp(gm);
-        // (3) trailing block: rank-w update
-        for (int i = j0; i < D; i++) {
-            const LT *li = A + i * LD + kp;
-            LT l[W];
+        // (3) trailing block: rank-w update, two rows at a time with every
+        // load issued before the stores (rows never alias; the compiler
+        // cannot know that)
+        int i = j0;
+        for (; i + 1 < D; i += 2) {
+            const LT *l0p = A + i * LD + kp, *l1p = l0p + LD;
+            LT l0[W], l1[W], a0[NS], a1[NS];
 #pragma unroll
-            for (int r = 0; r < W; r++) l[r] = r < w ? li[r] : (LT)0;
+            for (int r = 0; r < W; r++) {
+                l0[r] = r < w ? l0p[r] : (LT)0;
+                l1[r] = r < w ? l1p[r] : (LT)0;
+            }
+#pragma unroll
+            for (int t = 0; t < NS; t++) {
+                const int col = j0 + lane + 32 * t;
+                a0[t] = act[t] ? A[i * LD + col] : (LT)0;
+                a1[t] = act[t] ? A[(i + 1) * LD + col] : (LT)0;
+            }
+#pragma unroll
+            for (int t = 0; t < NS; t++) {
+#pragma unroll
+                for (int r = 0; r < W; r++) {
+                    a0[t] -= l0[r] * u[r][t];
+                    a1[t] -= l1[r] * u[r][t];
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < NS; t++) {
+                if (act[t]) {
+                    const int col = j0 + lane + 32 * t;
+                    A[i * LD + col] = a0[t];
+                    A[(i + 1) * LD + col] = a1[t];
+                }
+            }
+        }
+        if (i < D) {
+            const LT *l0p = A + i * LD + kp;
+            LT l0[W];
+#pragma unroll
+            for (int r = 0; r < W; r++) l0[r] = r < w ? l0p[r] : (LT)0;
 #pragma unroll
             for (int t = 0; t < NS; t++) {
                 if (act[t]) {
                     LT *a = A + i * LD + j0 + lane + 32 * t;
                     LT v = *a;
 #pragma unroll
-                    for (int r = 0; r < W; r++) v -= l[r] * u[r][t];
+                    for (int r = 0; r < W; r++) v -= l0[r] * u[r][t];
                     *a = v;
                 }
             }

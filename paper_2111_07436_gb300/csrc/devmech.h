@@ -67,6 +67,13 @@ struct DevMech {
     // Jacobian entry q: x = bits of the FP32 coefficient, y = constant index
     // (k, or -(r+1) for a reverse constant), z = o1 | o2 << 16
     const int4 *jpack;    // [nj]
+    // FP32 Jacobian assembly: per-lane flat entry lists (nonzeros spread
+    // over 32 lanes by entry count).  Record: x = bits of the FP32
+    // coefficient, y = k (signed 16 bits; -(r+1) for a reverse constant)
+    // | o1 << 16, z = LU offset | diag << 16 | last-entry-of-nonzero << 17,
+    // w = o2 | CSR index << 16
+    const int *jl_ptr;    // [33]
+    const int4 *jl_rec;   // [entries + empty non-zeros]
     // substitution entries: off | col << 16
     const int *sl_pack;   // [len(sl_off)]
     const int *su_pack;   // [len(su_off)]

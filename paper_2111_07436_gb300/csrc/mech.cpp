@@ -226,6 +226,44 @@ static void pack_records(HostMech &h) {
         h.jpack[q * 4 + 1] = h.jk[q];
         h.jpack[q * 4 + 2] = field16(h.jo[2 * q]) | (field16(h.jo[2 * q + 1]) << 16);
     }
+    // per-lane flat Jacobian entry lists, longest-processing-time over 32 lanes
+    {
+        std::vector<int> order(nnzJ);
+        for (int t = 0; t < nnzJ; t++) order[t] = t;
+        auto cnt = [&](int t) { return std::max(1, h.jptr[t + 1] - h.jptr[t]); };
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt(a) > cnt(b); });
+        std::vector<std::vector<int>> lanes(32);
+        std::vector<int> load(32, 0);
+        for (int t : order) {
+            int best = 0;
+            for (int l = 1; l < 32; l++)
+                if (load[l] < load[best]) best = l;
+            lanes[best].push_back(t);
+            load[best] += cnt(t);
+        }
+        if (nnzJ > 65535) throw std::runtime_error("too many Jacobian non-zeros for the packed records");
+        h.jl_ptr.assign(1, 0);
+        h.jl_rec.clear();
+        auto emit = [&](float c, int k, int o1, int o2, int t, bool last) {
+            int cb;
+            std::memcpy(&cb, &c, 4);
+            h.jl_rec.push_back(cb);
+            h.jl_rec.push_back((k & 0xffff) | (field16(o1) << 16));
+            h.jl_rec.push_back(h.jdst[t] | (h.jdiag[t] << 16) | ((last ? 1 : 0) << 17));
+            h.jl_rec.push_back(field16(o2) | (t << 16));
+        };
+        for (auto &v : lanes) {
+            for (int t : v) {
+                int b = h.jptr[t], e = h.jptr[t + 1];
+                if (b == e) emit(0.0f, 0, -1, -1, t, true);
+                for (int q = b; q < e; q++) {
+                    if (h.jk[q] < -32768 || h.jk[q] > 32767) throw std::runtime_error("process index too large");
+                    emit((float)h.jc[q], h.jk[q], h.jo[2 * q], h.jo[2 * q + 1], t, q == e - 1);
+                }
+            }
+            h.jl_ptr.push_back((int)h.jl_rec.size() / 4);
+        }
+    }
     h.sl_pack.resize(h.sl_off.size());
     for (size_t q = 0; q < h.sl_off.size(); q++) h.sl_pack[q] = field16(h.sl_off[q]) | (field16(h.sl_col[q]) << 16);
     h.su_pack.resize(h.su_off.size());
@@ -664,6 +702,8 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.jnz = reinterpret_cast<const int4 *>(pk.put(h.jnz));
     dm.jpack = reinterpret_cast<const int4 *>(pk.put(h.jpack));
     dm.sl_pack = pk.put(h.sl_pack);
+    dm.jl_ptr = pk.put(h.jl_ptr);
+    dm.jl_rec = reinterpret_cast<const int4 *>(pk.put(h.jl_rec));
     dm.su_pack = pk.put(h.su_pack);
     bdf_coefficients(dm);
     return pk.img;

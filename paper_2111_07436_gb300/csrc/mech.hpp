@@ -39,6 +39,7 @@ struct HostMech {
     std::vector<double> fc;
     std::vector<int> flane_ptr, flane_pos;
     std::vector<int> rpack, fpack, flane_job, jnz, jpack, sl_pack, su_pack;  // int4 records as 4 ints
+    std::vector<int> jl_ptr, jl_rec;
     std::vector<int> jptr, jdst, jdiag, jk, jo;
     std::vector<double> jc;
     std::vector<float> jc32;
