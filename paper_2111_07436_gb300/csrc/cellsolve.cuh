@@ -335,6 +335,10 @@ template <> __device__ __forceinline__ double tiny_pivot<double>() { return 1e-3
 // ---- LU factorisation in place; returns true if every pivot is usable -------
 // Pivots are checked, then replaced by their reciprocals: the substitutions
 // and later rows multiply instead of dividing.
+// 1 / u, correctly rounded, without the general division's range handling
+__device__ __forceinline__ float recip(float u) { return __frcp_rn(u); }
+__device__ __forceinline__ double recip(double u) { return 1.0 / u; }
+
 template <typename LT>
 __device__ __forceinline__ bool bad_pivot(LT u) {
     return !(fabs(u) > tiny_pivot<LT>()) || !isfinite(u);
@@ -358,7 +362,10 @@ __device__ __forceinline__ bool dense_factor(LT *A, int D, int LD, int lane, uns
             const int k = kp + c;
             const LT piv = A[k * LD + k];
             bad |= bad_pivot(piv);
-            const LT rp = (LT)1 / piv;
+            const LT rp = recip(piv);
+            LT uk[W];  // the pivot row inside the panel
+#pragma unroll
+            for (int j = 1; j < W; j++) uk[j] = (c + j < w) ? A[k * LD + k + j] : (LT)0;
 #pragma unroll
             for (int t = 0; t < NS; t++) {
                 const int i = lane + 32 * t;
@@ -366,7 +373,9 @@ __device__ __forceinline__ bool dense_factor(LT *A, int D, int LD, int lane, uns
                     LT *row = A + i * LD;
                     const LT l = row[k] * rp;
                     row[k] = l;
-                    for (int j = k + 1; j < kp + w; j++) row[j] -= l * A[k * LD + j];
+#pragma unroll
+                    for (int j = 1; j < W; j++)
+                        if (c + j < w) row[k + j] -= l * uk[j];
                 }
             }
             __syncwarp(gm);
@@ -474,7 +483,7 @@ __device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigne
                 const int di = __ldg(m.udiag + i);
                 LT u = lu[di];
                 bad |= bad_pivot(u);
-                lu[di] = (LT)1 / u;
+                lu[di] = recip(u);
             }
         }
         __syncwarp(gm);
