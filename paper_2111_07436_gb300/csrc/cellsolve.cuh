@@ -214,9 +214,14 @@ __device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, c
         const int b0 = __ldg(m.flane_ptr + lane), b1 = __ldg(m.flane_ptr + lane + 1);
         for (int i = b0; i < b1; i++) {
             const int4 job = __ldg(m.flane_job + i);
-            double acc = 0.0;
-            for (int q = job.y; q < job.z; q++) acc += gather_entry(m, q, c.rs);
-            fs[job.x] = acc;
+            double acc = 0.0, acc2 = 0.0;
+            int q = job.y;
+            for (; q + 1 < job.z; q += 2) {
+                acc += gather_entry(m, q, c.rs);
+                acc2 += gather_entry(m, q + 1, c.rs);
+            }
+            if (q < job.z) acc += gather_entry(m, q, c.rs);
+            fs[job.x] = acc + acc2;
         }
         __syncwarp(gm);
 #pragma unroll
@@ -515,30 +520,71 @@ __device__ __forceinline__ void dense_subst(const LT *A, int D, int LD, LT *xb, 
         rowc[t] = (i < D ? i : D - 1) * LD;
         xr[t] = i < D ? xb[i] : (LT)0;
     }
+    // forward, unit lower, two pivots per round: x_k and the not yet final
+    // x_{k+1} come by two independent shuffles, every lane finishes x_{k+1}
+    // with the broadcast L(k+1,k), then both columns update the rows below
 #pragma unroll
-    for (int kb = 0; kb < NS; kb++) {  // forward, unit lower
+    for (int kb = 0; kb < NS; kb++) {
         const int k0 = 32 * kb, k1 = min(D, k0 + 32);
-#pragma unroll 4
-        for (int k = k0; k < k1; k++) {
-            const LT xk = __shfl_sync(gm, xr[kb], k - k0);
+        int k = k0;
+        for (; k + 1 < k1; k += 2) {
+            const int o = k - k0;
+            const LT xk = __shfl_sync(gm, xr[kb], o);
+            const LT xn = __shfl_sync(gm, xr[kb], o + 1);
+            const LT l10 = A[(k + 1) * LD + k];
+            const LT xk1 = xn - l10 * xk;
+#pragma unroll
+            for (int t = kb; t < NS; t++) {
+                const LT a0 = A[rowc[t] + k], a1 = A[rowc[t] + k + 1];
+                if (t > kb || lane > o + 1) {
+                    xr[t] -= a0 * xk;
+                    xr[t] -= a1 * xk1;
+                } else if (lane == o + 1) {
+                    xr[t] = xk1;
+                }
+            }
+        }
+        if (k < k1) {  // odd block length: one pivot left
+            const int o = k - k0;
+            const LT xk = __shfl_sync(gm, xr[kb], o);
 #pragma unroll
             for (int t = kb; t < NS; t++) {
                 const LT a = A[rowc[t] + k];
-                if (t > kb || lane > k - k0) xr[t] -= a * xk;
+                if (t > kb || lane > o) xr[t] -= a * xk;
             }
         }
     }
+    // backward, upper with reciprocal diagonal, two pivots per round
 #pragma unroll
-    for (int kb = NS - 1; kb >= 0; kb--) {  // backward, upper with reciprocal diagonal
+    for (int kb = NS - 1; kb >= 0; kb--) {
         const int k0 = 32 * kb, k1 = min(D, k0 + 32);
-#pragma unroll 4
-        for (int k = k1 - 1; k >= k0; k--) {
-            const LT xk = __shfl_sync(gm, xr[kb], k - k0) * A[k * LD + k];
-            if (lane == k - k0) xr[kb] = xk;
+        int k = k1 - 1;
+        for (; k - 1 >= k0; k -= 2) {
+            const int o = k - k0;  // pivots k and k-1
+            const LT xk = __shfl_sync(gm, xr[kb], o) * A[k * LD + k];
+            const LT xp = __shfl_sync(gm, xr[kb], o - 1);
+            const LT xk1 = (xp - A[(k - 1) * LD + k] * xk) * A[(k - 1) * LD + k - 1];
+#pragma unroll
+            for (int t = 0; t <= kb; t++) {
+                const LT a0 = A[rowc[t] + k], a1 = A[rowc[t] + k - 1];
+                if (t < kb || lane < o - 1) {
+                    xr[t] -= a0 * xk;
+                    xr[t] -= a1 * xk1;
+                } else if (lane == o) {
+                    xr[t] = xk;
+                } else if (lane == o - 1) {
+                    xr[t] = xk1;
+                }
+            }
+        }
+        if (k >= k0) {  // one pivot left
+            const int o = k - k0;
+            const LT xk = __shfl_sync(gm, xr[kb], o) * A[k * LD + k];
 #pragma unroll
             for (int t = 0; t <= kb; t++) {
                 const LT a = A[rowc[t] + k];
-                if (t < kb || lane < k - k0) xr[t] -= a * xk;
+                if (t < kb || lane < o) xr[t] -= a * xk;
+                else if (lane == o) xr[t] = xk;
             }
         }
     }
@@ -559,13 +605,19 @@ __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, uns
         int b = __ldg(m.flev_ptr + L), e = __ldg(m.flev_ptr + L + 1);
         for (int r = b + lane; r < e; r += G) {
             int i = __ldg(m.frow + r);
-            LT s = x[i];
+            LT s = x[i], s2 = (LT)0;
             int qb = __ldg(m.sl_ptr + i), qe = __ldg(m.sl_ptr + i + 1);
-            for (int q = qb; q < qe; q++) {
+            int q = qb;
+            for (; q + 1 < qe; q += 2) {
+                const int e2 = __ldg(m.sl_pack + q), e3 = __ldg(m.sl_pack + q + 1);
+                s -= lu[lo16(e2)] * x[hi16(e2)];
+                s2 += lu[lo16(e3)] * x[hi16(e3)];
+            }
+            if (q < qe) {
                 const int e2 = __ldg(m.sl_pack + q);
                 s -= lu[lo16(e2)] * x[hi16(e2)];
             }
-            x[i] = s;
+            x[i] = s - s2;
         }
         __syncwarp(gm);
     }
@@ -583,13 +635,19 @@ __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, uns
         int b = __ldg(m.blev_ptr + L), e = __ldg(m.blev_ptr + L + 1);
         for (int r = b + lane; r < e; r += G) {
             int i = __ldg(m.brow + r);
-            LT s = x[i];
+            LT s = x[i], s2 = (LT)0;
             int qb = __ldg(m.su_ptr + i), qe = __ldg(m.su_ptr + i + 1);
-            for (int q = qb; q < qe; q++) {
+            int q = qb;
+            for (; q + 1 < qe; q += 2) {
+                const int e2 = __ldg(m.su_pack + q), e3 = __ldg(m.su_pack + q + 1);
+                s -= lu[lo16(e2)] * x[hi16(e2)];
+                s2 += lu[lo16(e3)] * x[hi16(e3)];
+            }
+            if (q < qe) {
                 const int e2 = __ldg(m.su_pack + q);
                 s -= lu[lo16(e2)] * x[hi16(e2)];
             }
-            x[i] = s * lu[__ldg(m.udiag + i)];
+            x[i] = (s - s2) * lu[__ldg(m.udiag + i)];
         }
         __syncwarp(gm);
     }
