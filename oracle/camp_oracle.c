@@ -33,7 +33,8 @@
 
 /* ---- mechanism arrays (filled from JSON by oracle/mech.py) -------------- */
 enum { OM_ARRHENIUS = 0, OM_TROE = 1, OM_PHOTOLYSIS = 2, OM_EMISSION = 3,
-       OM_LOSS = 4, OM_HENRY = 5, OM_AQREV = 6 };
+       OM_LOSS = 4, OM_HENRY = 5, OM_AQREV = 6, OM_CUSTOM_H2O2 = 7, OM_CUSTOM_OH_HNO3 = 8,
+       OM_COND_ARRHENIUS = 9, OM_SIMPOL = 10 };
 
 #define OM_MAXSP 4
 typedef struct {
@@ -96,6 +97,27 @@ static double ipow(double x, int n) {
     return r;
 }
 
+/* Arrhenius with D = 300 K and E = 0: A exp(C/T) (T/300)^B, the building
+ * block of the Troe and custom rate constants (Table 2) */
+static double arr300(double A, double B, double C, double T) {
+    return A * exp(C / T) * pow(T / 300.0, B);
+}
+
+/* Gas-to-particle mass transfer of one section, s^-1 (Table 2,
+ * HenrysLawPhaseTransfer; Zaveri et al. 2008): N particles of radius rad
+ * each collect 4 pi rad Dg f_fs(Kn, alpha) with the Fuchs-Sutugin factor
+ * f_fs = 0.75 alpha (1 + Kn) / (Kn^2 + Kn + 0.283 Kn alpha + 0.75 alpha),
+ * Kn = lambda / rad, mean free path lambda = 3 Dg / cbar and mean speed
+ * cbar = sqrt(8 R T / (pi MW)). */
+static double mass_transfer(double rad, double Np, double alpha, double Dg, double MW,
+                            double T) {
+    double cbar = sqrt(8.0 * RGAS * T / (PI * MW));
+    double lambda = 3.0 * Dg / cbar;
+    double Kn = lambda / rad;
+    double ffs = 0.75 * alpha * (1.0 + Kn) / (Kn * Kn + Kn + 0.283 * Kn * alpha + 0.75 * alpha);
+    return Np * 4.0 * PI * rad * Dg * ffs;
+}
+
 void om_rate_constants(const om_mech *m, const double *env, double *kf, double *kr) {
     const double T = env[0], P = env[1];
     const double Mair = P / (KB * T) * 1e-6;   /* air number density, molec cm^-3 */
@@ -133,22 +155,39 @@ void om_rate_constants(const om_mech *m, const double *env, double *kf, double *
             kf[k] = env[r->env_slot];
             break;
         case OM_HENRY: {
-            /* H(T) = H298 exp(C (1/T - 1/298)) [M Pa^-1]; k_c = 4 pi r Dg f_fs(Kn, alpha)
-             * per particle (Table 2, HenrysLawPhaseTransfer), times N particles. */
+            /* H(T) = H298 exp(C (1/T - 1/298)) [M Pa^-1]; condensation k_c of
+             * the section (Table 2, HenrysLawPhaseTransfer); evaporation
+             * k_c / (H_cc L) with the dimensionless H_cc = 1000 H R T, so
+             * that at equilibrium y_aq / y_gas = H_cc L. */
             int b = r->section;
             double rad = env[m->env_section_base + 3 * b];
             double Np = env[m->env_section_base + 3 * b + 1];
             double L = env[m->env_section_base + 3 * b + 2];
             if (!(L > 0.0 && Np > 0.0 && rad > 0.0)) break;
             double H = r->p[0] * exp(r->p[1] * (1.0 / T - 1.0 / 298.0));
-            double alpha = r->p[2], Dg = r->p[3], MW = r->p[4];
-            double Hcc = 1000.0 * H * RGAS * T;           /* aq M / gas M, dimensionless */
-            double cbar = sqrt(8.0 * RGAS * T / (PI * MW)); /* mean molecular speed */
-            double lambda = 3.0 * Dg / cbar;              /* mean free path */
-            double Kn = lambda / rad;
-            double ffs = 0.75 * alpha * (1.0 + Kn) /
-                         (Kn * Kn + Kn + 0.283 * Kn * alpha + 0.75 * alpha);
-            double kb = Np * 4.0 * PI * rad * Dg * ffs;  /* s^-1 */
+            double Hcc = 1000.0 * H * RGAS * T;
+            double kb = mass_transfer(rad, Np, r->p[2], r->p[3], r->p[4], T);
+            kf[k] = kb;
+            kr[k] = kb / (Hcc * L);
+            break;
+        }
+        case OM_SIMPOL: {
+            /* Condensation as for Henry's law; evaporation from the SIMPOL.1
+             * vapour pressure log10 p0 [atm] = B1/T + B2 + B3 T + B4 ln T
+             * (Table 2, SimpolPhaseTransfer).  Reading: the condensed phase
+             * is an ideal solution of fixed total molarity c_tot, so Raoult's
+             * law p = (c / c_tot) p0 acts as Henry's law with
+             * H = c_tot / p0 [M Pa^-1]. */
+            int b = r->section;
+            double rad = env[m->env_section_base + 3 * b];
+            double Np = env[m->env_section_base + 3 * b + 1];
+            double L = env[m->env_section_base + 3 * b + 2];
+            if (!(L > 0.0 && Np > 0.0 && rad > 0.0)) break;
+            double lg = r->p[0] / T + r->p[1] + r->p[2] * T + r->p[3] * log(T);
+            double p0 = 101325.0 * pow(10.0, lg);          /* Pa */
+            double H = r->p[7] / p0;
+            double Hcc = 1000.0 * H * RGAS * T;
+            double kb = mass_transfer(rad, Np, r->p[4], r->p[5], r->p[6], T);
             kf[k] = kb;
             kr[k] = kb / (Hcc * L);
             break;
@@ -166,6 +205,37 @@ void om_rate_constants(const om_mech *m, const double *env, double *kf, double *
             double phi = 1e-9 * P / (RGAS * T * 1000.0 * L);
             kf[k] = Keq * krev * ipow(phi, nr - 1);
             kr[k] = krev * ipow(phi, np - 1);
+            break;
+        }
+        case OM_CUSTOM_H2O2: {
+            /* k = k1 + k2 [M], k1 and k2 Arrhenius with D = 300, E = 0
+             * (Table 2, CustomH2o2) */
+            double k1 = arr300(r->p[0], r->p[1], r->p[2], T);
+            double k2 = arr300(r->p[3], r->p[4], r->p[5], T);
+            kf[k] = (k1 + k2 * Mair) * ipow(mppb, nr - 1);
+            break;
+        }
+        case OM_CUSTOM_OH_HNO3: {
+            /* k = k0 + k3[M] / (1 + k3[M] / k2), all Arrhenius with D = 300,
+             * E = 0 (Table 2, CustomOhHno3) */
+            double k0 = arr300(r->p[0], r->p[1], r->p[2], T);
+            double k2 = arr300(r->p[3], r->p[4], r->p[5], T);
+            double k3M = arr300(r->p[6], r->p[7], r->p[8], T) * Mair;
+            kf[k] = (k0 + k3M / (1.0 + k3M / k2)) * ipow(mppb, nr - 1);
+            break;
+        }
+        case OM_COND_ARRHENIUS: {
+            /* Arrhenius in a condensed phase instance, M^(1-nr) s^-1 for the
+             * aqueous phase (Table 2, CondensedPhaseArrhenius): the rate in
+             * M s^-1 is k prod c with c = y phi, returned to ppb s^-1 by
+             * dividing by phi, so kf = k phi^(nr - 1). */
+            int b = r->section;
+            double L = env[m->env_section_base + 3 * b + 2];
+            if (!(L > 0.0)) break;
+            double A = r->p[0], B = r->p[1], C = r->p[2], D = r->p[3], E = r->p[4];
+            double kk = A * exp(C / T) * pow(T / D, B) * (1.0 + E * P);
+            double phi = 1e-9 * P / (RGAS * T * 1000.0 * L);
+            kf[k] = kk * ipow(phi, nr - 1);
             break;
         }
         }

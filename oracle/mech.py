@@ -18,10 +18,14 @@ from dataclasses import dataclass, field
 KB = 1.380649e-23
 
 TYPE_CODE = {"ARRHENIUS": 0, "TROE": 1, "PHOTOLYSIS": 2, "EMISSION": 3,
-             "FIRST_ORDER_LOSS": 4, "HL_PHASE_TRANSFER": 5, "AQUEOUS_REVERSIBLE": 6}
+             "FIRST_ORDER_LOSS": 4, "HL_PHASE_TRANSFER": 5, "AQUEOUS_REVERSIBLE": 6,
+             "CUSTOM_H2O2": 7, "CUSTOM_OH_HNO3": 8, "CONDENSED_ARRHENIUS": 9,
+             "SIMPOL_PHASE_TRANSFER": 10}
 RUNTIME = ("PHOTOLYSIS", "EMISSION", "FIRST_ORDER_LOSS")
-SECTIONED = ("HL_PHASE_TRANSFER", "AQUEOUS_REVERSIBLE")
-REVERSIBLE = ("HL_PHASE_TRANSFER", "AQUEOUS_REVERSIBLE")
+SECTIONED = ("HL_PHASE_TRANSFER", "AQUEOUS_REVERSIBLE", "CONDENSED_ARRHENIUS",
+             "SIMPOL_PHASE_TRANSFER")
+REVERSIBLE = ("HL_PHASE_TRANSFER", "AQUEOUS_REVERSIBLE", "SIMPOL_PHASE_TRANSFER")
+WATER_MOLARITY = 1000.0 / 18.015  # mol L^-1, default total molarity of a condensed phase
 MAXSP = 4
 
 
@@ -117,6 +121,18 @@ def parse(text) -> Mechanism:
                     procs.append(Process(t, [(index[r["gas"]], 1)], [(sp(r["aqueous"]), 1.0)],
                                          [r["H298"], r["C_H"], r["alpha"], r["Dg"], r["MW"]],
                                          section=b))
+                elif t == "SIMPOL_PHASE_TRANSFER":
+                    B = list(r["B"]) + [0.0] * (4 - len(r["B"]))
+                    procs.append(Process(t, [(index[r["gas"]], 1)], [(sp(r["aqueous"]), 1.0)],
+                                         B[:4] + [r["alpha"], r["Dg"], r["MW"],
+                                                  r.get("c_tot", WATER_MOLARITY)],
+                                         section=b))
+                elif t == "CONDENSED_ARRHENIUS":
+                    rs = _merge([(sp(k), int(v)) for k, v in r["reactants"].items()])
+                    ps = _merge([(sp(k), float(v)) for k, v in r.get("products", {}).items()])
+                    C = r["C"] if "C" in r else -r.get("Ea", 0.0) / KB
+                    procs.append(Process(t, rs, ps, [r["A"], r.get("B", 0.0), C, r.get("D", 300.0),
+                                                     r.get("E", 0.0)], section=b))
                 else:
                     rs = _merge([(sp(k), int(v)) for k, v in r["reactants"].items()])
                     ps = _merge([(sp(k), float(int(v))) for k, v in r["products"].items()])
@@ -136,6 +152,12 @@ def parse(text) -> Mechanism:
                 params = [r["k0_A"], r.get("k0_B", 0.0), r.get("k0_C", 0.0),
                           r["kinf_A"], r.get("kinf_B", 0.0), r.get("kinf_C", 0.0),
                           r.get("Fc", 0.6), r.get("N", 1.0)]
+            elif t == "CUSTOM_H2O2":
+                params = [r[f"k{i}_{c}"] if c == "A" else r.get(f"k{i}_{c}", 0.0)
+                          for i in (1, 2) for c in "ABC"]
+            elif t == "CUSTOM_OH_HNO3":
+                params = [r[f"k{i}_{c}"] if c == "A" else r.get(f"k{i}_{c}", 0.0)
+                          for i in (0, 2, 3) for c in "ABC"]
             else:  # PHOTOLYSIS
                 params = []
             procs.append(Process(t, rs, ps, params,

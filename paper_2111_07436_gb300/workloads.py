@@ -33,6 +33,17 @@ Reaction types and their fields (units follow Table 2 of the paper):
                        Dg [m^2 s^-1], MW [kg mol^-1]      (one per section)
     AQUEOUS_REVERSIBLE reactants{name:int}, products{name:int}, A (K_eq at
                        298 K, M^(np-nr)), C [K], kr [M^(1-np) s^-1]
+    CUSTOM_H2O2        reactants, products, k1_A, k1_B, k1_C, k2_A, k2_B, k2_C
+                       (k = k1 + k2 [M], each A exp(C/T) (T/300)^B)
+    CUSTOM_OH_HNO3     reactants, products, k0_*, k2_*, k3_* as above
+                       (k = k0 + k3[M] / (1 + k3[M]/k2))
+    CONDENSED_ARRHENIUS reactants{name:int}, products{name:float} (phase
+                       species), A [M^(1-nr) s^-1], B, C, D, E as ARRHENIUS
+                                                          (one per section)
+    SIMPOL_PHASE_TRANSFER gas, aqueous, B [B1 (K), B2, B3 (K^-1), B4]
+                       (log10 p0/atm = B1/T + B2 + B3 T + B4 ln T), alpha,
+                       Dg, MW, c_tot [M] (condensed-phase total molarity,
+                       default that of water)               (one per section)
 
 Per-cell environment vector (the solver reads only this; "value" fields are
 the defaults a host model would copy in):
@@ -53,7 +64,8 @@ from dataclasses import dataclass
 import numpy as np
 
 RUNTIME_TYPES = ("PHOTOLYSIS", "EMISSION", "FIRST_ORDER_LOSS")
-SECTION_TYPES = ("HL_PHASE_TRANSFER", "AQUEOUS_REVERSIBLE")
+SECTION_TYPES = ("HL_PHASE_TRANSFER", "AQUEOUS_REVERSIBLE", "CONDENSED_ARRHENIUS",
+                 "SIMPOL_PHASE_TRANSFER")
 
 
 def _logu(rng, lo, hi, size=None):
@@ -247,6 +259,81 @@ def small_multiphase_mechanism(seed=104):
     """8 gas species + 8 sections x 20 aqueous species = 168 species."""
     return add_aqueous_sections(small_gas_mechanism(), seed=seed, n_henry=5,
                                 n_split_eq=2, n_simple_eq=1)
+
+
+def process_variety_mechanism(seed=106, n_sections=4):
+    """Every process type of Table 2 that this solver implements, in one
+    mechanism: the 8-species gas mechanism plus an HOx/NOy/isoprene block
+    (CUSTOM_H2O2 for HO2 + HO2, CUSTOM_OH_HNO3 for OH + HNO3, the isoprene
+    oxidation of Table 9 with its rate constants and yields) and a condensed
+    phase per section with Henry's-law uptake of H2O2 and SO2, SIMPOL.1
+    partitioning of the two isoprene products (Table 9's B parameters),
+    condensed-phase Arrhenius chemistry and one aqueous equilibrium.
+    Parameters the paper does not print are drawn here (custom rate
+    constants near their usual magnitudes; transfer parameters as in
+    add_aqueous_sections)."""
+    rng = np.random.default_rng(seed)
+    mech = json.loads(json.dumps(small_gas_mechanism()))
+    extra = ["HO2", "H2O2", "OH", "HNO3", "NO3", "O3", "ISOP", "ISOPP1", "ISOPP2", "SO2"]
+    mech["species"] += [{"name": s, "atoms": 1} for s in extra]
+
+    def arr(A, C):
+        return {"A": float(A), "B": 0.0, "C": float(C), "D": 300.0, "E": 0.0}
+
+    def drawn(prefix, A, C):  # A exp(C/T) around a usual magnitude
+        return {f"{prefix}_A": float(A * _logu(rng, 0.5, 2.0)), f"{prefix}_B": 0.0,
+                f"{prefix}_C": float(C + rng.uniform(-100.0, 100.0))}
+
+    rx = mech["reactions"]
+    rx += [
+        {"type": "CUSTOM_H2O2", "reactants": {"HO2": 2}, "products": {"H2O2": 1.0},
+         **drawn("k1", 3e-13, 460.0), **drawn("k2", 2e-33, 920.0)},
+        {"type": "CUSTOM_OH_HNO3", "reactants": {"OH": 1, "HNO3": 1}, "products": {"NO3": 1.0},
+         **drawn("k0", 2.4e-14, 460.0), **drawn("k2", 2.7e-17, 2199.0), **drawn("k3", 6.5e-34, 1335.0)},
+        {"type": "PHOTOLYSIS", "reactants": {"H2O2": 1}, "products": {"OH": 2.0},
+         "value": float(_logu(rng, 1e-6, 1e-5))},
+        {"type": "PHOTOLYSIS", "reactants": {"NO3": 1}, "products": {"HNO3": 1.0},
+         "value": float(_logu(rng, 1e-3, 1e-1))},
+        {"type": "ARRHENIUS", "reactants": {"OH": 1, "O3": 1}, "products": {"HO2": 1.0},
+         **arr(1.7e-12, -940.0)},
+        # isoprene oxidation, Table 9 (mass-based yields)
+        {"type": "ARRHENIUS", "reactants": {"ISOP": 1, "OH": 1}, "products": {"ISOPP1": 0.192},
+         **arr(2.54e-11, 407.6)},
+        {"type": "ARRHENIUS", "reactants": {"ISOP": 1, "O3": 1}, "products": {"ISOPP2": 0.215},
+         **arr(7.86e-15, -1912.0)},
+        {"type": "EMISSION", "species": "ISOP", "value": float(_logu(rng, 1e-4, 1e-3))},
+        {"type": "EMISSION", "species": "O3", "value": float(_logu(rng, 1e-4, 1e-3))},
+        {"type": "FIRST_ORDER_LOSS", "species": "HNO3", "value": float(_logu(rng, 1e-5, 1e-4))},
+    ]
+    ph = ["H2O2aq", "SO2aq", "HSO3", "SULF", "SOA1", "SOA2", "OLIG"]
+
+    def transfer():
+        return {"alpha": float(rng.uniform(0.01, 1.0)), "Dg": float(1e-5 * rng.uniform(0.5, 2.0)),
+                "MW": float(rng.uniform(30.0, 150.0)) * 1e-3}
+
+    rx += [
+        {"type": "HL_PHASE_TRANSFER", "gas": "H2O2", "aqueous": "H2O2aq",
+         "H298": float(_logu(rng, 1e4, 1e5)) / 101325.0, "C_H": float(rng.uniform(2000.0, 6000.0)),
+         **transfer()},
+        {"type": "HL_PHASE_TRANSFER", "gas": "SO2", "aqueous": "SO2aq",
+         "H298": float(_logu(rng, 0.5, 2.0)) / 101325.0, "C_H": float(rng.uniform(2000.0, 6000.0)),
+         **transfer()},
+        {"type": "SIMPOL_PHASE_TRANSFER", "gas": "ISOPP1", "aqueous": "SOA1",
+         "B": [3.81e3, -2.13e1, 0.0, 0.0], **transfer()},
+        {"type": "SIMPOL_PHASE_TRANSFER", "gas": "ISOPP2", "aqueous": "SOA2",
+         "B": [3.81e3, -2.09e1, 0.0, 0.0], **transfer()},
+        {"type": "AQUEOUS_REVERSIBLE", "reactants": {"SO2aq": 1}, "products": {"HSO3": 1},
+         "A": float(_logu(rng, 1e-2, 1e1)), "C": 0.0, "kr": float(_logu(rng, 1e-1, 1e2))},
+        {"type": "CONDENSED_ARRHENIUS", "reactants": {"H2O2aq": 1, "HSO3": 1},
+         "products": {"SULF": 1.0}, "A": float(_logu(rng, 1e5, 1e7)), "B": 0.0,
+         "C": float(rng.uniform(-4000.0, -3000.0)), "D": 300.0, "E": 0.0},
+        {"type": "CONDENSED_ARRHENIUS", "reactants": {"SOA1": 1}, "products": {"OLIG": 1.0},
+         "A": float(_logu(rng, 1e-5, 1e-3)), "B": 0.0, "C": 0.0, "D": 300.0, "E": 0.0},
+    ]
+    mech["name"] = f"process-variety-{len(mech['species'])}+aq{n_sections}x{len(ph)}"
+    mech["phases"] = {"aqueous": [{"name": p, "atoms": 1} for p in ph]}
+    mech["aerosol"] = {"phase": "aqueous", "sections": n_sections}
+    return mech
 
 
 # --------------------------------------------------------------------------

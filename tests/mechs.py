@@ -43,3 +43,26 @@ def henry(gas, aq, H298, C_H=0.0, alpha=0.5, Dg=1e-5, MW=0.05):
 def aqrev(reactants, products, A, kr, C=0.0):
     return {"type": "AQUEOUS_REVERSIBLE", "reactants": reactants, "products": products,
             "A": A, "C": C, "kr": kr}
+
+
+def custom_h2o2(reactants, products, k1_A, k2_A, k1_B=0.0, k1_C=0.0, k2_B=0.0, k2_C=0.0):
+    return {"type": "CUSTOM_H2O2", "reactants": reactants, "products": products,
+            "k1_A": k1_A, "k1_B": k1_B, "k1_C": k1_C, "k2_A": k2_A, "k2_B": k2_B, "k2_C": k2_C}
+
+
+def custom_oh_hno3(reactants, products, k0_A, k2_A, k3_A, k0_C=0.0, k2_C=0.0, k3_C=0.0):
+    return {"type": "CUSTOM_OH_HNO3", "reactants": reactants, "products": products,
+            "k0_A": k0_A, "k0_C": k0_C, "k2_A": k2_A, "k2_C": k2_C, "k3_A": k3_A, "k3_C": k3_C}
+
+
+def condensed_arrhenius(reactants, products, A, B=0.0, C=0.0, D=300.0, E=0.0):
+    return {"type": "CONDENSED_ARRHENIUS", "reactants": reactants, "products": products,
+            "A": A, "B": B, "C": C, "D": D, "E": E}
+
+
+def simpol(gas, aq, B, alpha=0.5, Dg=1e-5, MW=0.05, c_tot=None):
+    d = {"type": "SIMPOL_PHASE_TRANSFER", "gas": gas, "aqueous": aq, "B": list(B),
+         "alpha": alpha, "Dg": Dg, "MW": MW}
+    if c_tot is not None:
+        d["c_tot"] = c_tot
+    return d

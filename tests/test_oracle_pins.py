@@ -122,9 +122,136 @@ def test_aqueous_constants_use_molarity_per_ppb():
     assert kr[1] == pytest.approx(7.0 * phi, rel=1e-9)
 
 
+def test_custom_h2o2_adds_a_pressure_term():
+    # k = k1 + k2 [M] (Table 2, CustomH2o2)
+    T, P = STP
+    mppb = LOSCHMIDT_CM3 * 1e-9
+    m = oracle.Mechanism(M.mech(["H", "X"], [
+        M.custom_h2o2({"H": 2}, {"X": 1}, k1_A=3e-13, k1_B=1.5, k1_C=460.0, k2_A=0.0),
+        M.arrhenius({"H": 2}, {"X": 1}, A=3e-13, B=1.5, C=460.0, D=300.0),
+        M.custom_h2o2({"H": 2}, {"X": 1}, k1_A=0.0, k2_A=2e-33),
+        M.custom_h2o2({"H": 2}, {"X": 1}, k1_A=0.0, k2_A=2e-33, k2_C=T * math.log(2.0)),
+        M.custom_h2o2({"H": 2}, {"X": 1}, k1_A=3e-13, k1_C=460.0, k2_A=2e-33, k2_C=920.0),
+        M.custom_h2o2({"H": 2}, {"X": 1}, k1_A=0.0, k2_A=2e-33, k2_C=920.0),
+        M.custom_h2o2({"H": 2}, {"X": 1}, k1_A=3e-13, k1_C=460.0, k2_A=0.0),
+    ]))
+    kf, kr = m.rate_constants(env_of(m, T, P))
+    assert not kr.any()
+    # without the pressure term it is the Arrhenius rate constant (D = 300 K)
+    assert kf[0] == pytest.approx(kf[1], rel=1e-14)
+    # the pressure term is k2 times the air number density (Loschmidt at STP)
+    assert kf[2] / mppb == pytest.approx(2e-33 * LOSCHMIDT_CM3, rel=1e-9)
+    assert kf[3] / kf[2] == pytest.approx(2.0, rel=1e-14)      # k2's own exp(C/T)
+    assert kf[4] == pytest.approx(kf[5] + kf[6], rel=1e-14)    # the two terms add
+    # (T/300)^B of the k2 term, at the same T and P
+    m2 = oracle.Mechanism(M.mech(["H", "X"], [
+        M.custom_h2o2({"H": 2}, {"X": 1}, k1_A=0.0, k2_A=2e-33),
+        {**M.custom_h2o2({"H": 2}, {"X": 1}, k1_A=0.0, k2_A=2e-33), "k2_B": 1.0}]))
+    kf2, _ = m2.rate_constants(env_of(m2, 600.0, 5e4))
+    assert kf2[1] / kf2[0] == pytest.approx(2.0, rel=1e-14)
+
+
+def test_custom_oh_hno3_limits():
+    # k = k0 + k3[M] / (1 + k3[M]/k2) (Table 2, CustomOhHno3): linear in [M]
+    # at low pressure, k0 + k2 at high pressure, k0 + k2/2 where k3[M] = k2
+    T, P = STP
+    Mair = LOSCHMIDT_CM3
+    k0, k2 = 2.4e-14, 2.7e-17
+    rx = lambda **kw: M.custom_oh_hno3({"O": 1, "N": 1}, {"X": 1}, **kw)
+    m = oracle.Mechanism(M.mech(["O", "N", "X"], [
+        rx(k0_A=0.0, k2_A=k2, k3_A=1e-7 * k2 / Mair),
+        rx(k0_A=k0, k2_A=k2, k3_A=1e7 * k2 / Mair),
+        rx(k0_A=k0, k2_A=k2, k3_A=k2 / Mair),
+        rx(k0_A=k0, k2_A=k2, k3_A=0.0),
+    ]))
+    kf, kr = m.rate_constants(env_of(m, T, P))
+    k = kf / (Mair * 1e-9)  # back to cm^3 s^-1 (bimolecular)
+    assert k[0] == pytest.approx(1e-7 * k2, rel=1e-6)
+    assert k[1] == pytest.approx(k0 + k2, rel=1e-6)
+    assert k[2] == pytest.approx(k0 + 0.5 * k2, rel=1e-9)
+    assert k[3] == pytest.approx(k0, rel=1e-9)
+    assert not kr.any()
+
+
+def test_condensed_arrhenius_works_in_molarity():
+    # rates in M s^-1 (Table 2, CondensedPhaseArrhenius): a first-order
+    # process needs no unit factor, a second-order one the molarity per ppb
+    T, P = STP
+    L = 1e-6
+    phi = 1e-9 * (1000.0 / MOLAR_VOLUME_STP) / (1000.0 * L)  # M per ppb at STP
+    m = oracle.Mechanism(M.mech(["G"], [
+        M.condensed_arrhenius({"a": 1}, {"b": 1}, A=0.7),
+        M.condensed_arrhenius({"a": 1, "b": 1}, {"c": 1}, A=5e3),
+        M.condensed_arrhenius({"a": 2}, {"c": 0.5}, A=5e3, C=T * math.log(2.0)),
+    ], phase=["a", "b", "c"], sections=2))
+    kf, kr = m.rate_constants(env_of(m, T, P, sections=[(1e-6, 1e8, L), (1e-6, 1e8, 0.0)]))
+    # instances: process 0 in sections 0 and 1, then process 1, then process 2
+    assert kf[0] == pytest.approx(0.7, rel=1e-15)
+    assert kf[2] == pytest.approx(5e3 * phi, rel=1e-9)
+    assert kf[4] == pytest.approx(1e4 * phi, rel=1e-9)
+    assert kf[1] == kf[3] == kf[5] == 0.0  # section 1 holds no condensed phase
+    assert not kr.any()
+
+
+def test_condensed_second_order_decay_in_molarity():
+    # 2a -> b at k [M^-1 s^-1]: dc/dt = -2 k c^2, so 1/c = 1/c0 + 2 k t in molarity
+    T, P, L = 290.0, 9.5e4, 3e-7
+    k = 40.0
+    m = oracle.Mechanism(M.mech(["G"], [M.condensed_arrhenius({"a": 2}, {"b": 1}, A=k)],
+                                phase=["a", "b"], sections=1))
+    env = env_of(m, T, P, sections=[(1e-6, 1e8, L)])
+    to_M = 1e-9 * P / (8.314462618 * T) / (1000.0 * L)
+    y = _integrate(m, np.array([0.0, 5.0, 0.0]), env, 100.0)
+    c = 1.0 / (1.0 / (5.0 * to_M) + 2 * k * 100.0)
+    assert y[1] * to_M == pytest.approx(c, rel=1e-8)
+    assert y[2] == pytest.approx((5.0 - y[1]) / 2, rel=1e-10)
+
+
+# SIMPOL.1 parameters of isoprene products (Table 9): B1 [K], B2, B3 [1/K], B4
+SOA_B = (3.81e3, -21.3, 0.0, 0.0)
+
+
+def test_simpol_partition_follows_raoults_law():
+    # Reading: ideal solution of fixed molarity c_tot, so at equilibrium
+    # y_g P = (c_a / c_tot) p0, i.e. y_a / y_g = c_tot R T L / p0 with the
+    # SIMPOL.1 vapour pressure log10 p0 [atm] = B1/T + B2 + B3 T + B4 ln T
+    T, P, L, c_tot = 290.0, 1e5, 4e-12, 7.0
+    mt = dict(alpha=0.1, Dg=1e-5, MW=0.15)
+    m = oracle.Mechanism(M.mech(["G"], [
+        M.simpol("G", "a", SOA_B, c_tot=c_tot, **mt),
+        M.henry("G", "a", H298=1.0, **mt),
+        M.simpol("G", "a", (0.0, 0.0, 0.01, 0.0), c_tot=c_tot, **mt),
+        M.simpol("G", "a", (0.0, 0.0, 0.0, 0.5), c_tot=c_tot, **mt),
+        M.simpol("G", "a", SOA_B, **mt),
+    ], phase=["a"], sections=1))
+    kf, kr = m.rate_constants(env_of(m, T, P, sections=[(2e-7, 1e9, L)]))
+    p0 = 10.0 ** (SOA_B[0] / T + SOA_B[1])
+    assert kf[0] / kr[0] == pytest.approx(c_tot * R_LATM * T * L / p0, rel=1e-8)
+    assert kf[0] == pytest.approx(kf[1], rel=1e-15)  # condensation as for Henry's law
+    assert kf[2] / kr[2] == pytest.approx(c_tot * R_LATM * T * L / 10.0 ** (0.01 * T), rel=1e-8)
+    assert kf[3] / kr[3] == pytest.approx(c_tot * R_LATM * T * L / T ** (0.5 * math.log(10.0)), rel=1e-8)
+    # the default solvent is water, 55.5 mol per litre
+    assert (kf[4] / kr[4]) / (kf[0] / kr[0]) == pytest.approx(1000.0 / 18.015 / c_tot, rel=1e-12)
+
+
+def test_simpol_two_compartment_relaxation():
+    T, P, L = 290.0, 1e5, 4e-12
+    m = oracle.Mechanism(M.mech(["G"], [M.simpol("G", "a", SOA_B, alpha=0.1, c_tot=7.0)],
+                                phase=["a"], sections=1))
+    env = env_of(m, T, P, sections=[(2e-7, 1e9, L)])
+    kf, kr = m.rate_constants(env)
+    y0 = np.array([3.0, 0.5])
+    for t in (0.3 / (kf[0] + kr[0]), 5.0 / (kf[0] + kr[0])):
+        y = _integrate(m, y0, env, t)
+        geq = 3.5 * kr[0] / (kf[0] + kr[0])
+        assert y[0] == pytest.approx(geq + (3.0 - geq) * math.exp(-(kf[0] + kr[0]) * t), rel=1e-8)
+        assert y.sum() == pytest.approx(3.5, rel=1e-12)
+
+
 # ---------------------------------------------------------------- f and J
 
-@pytest.mark.parametrize("wl_mech", ["small_gas_mechanism", "small_multiphase_mechanism"])
+@pytest.mark.parametrize("wl_mech", ["small_gas_mechanism", "small_multiphase_mechanism",
+                                     "process_variety_mechanism"])
 def test_jacobian_matches_central_differences(wl_mech):
     import json
     from paper_2111_07436_gb300 import workloads as w

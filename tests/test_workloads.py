@@ -77,3 +77,14 @@ def test_night_and_cloud_options():
     assert 0.07 < cloudy.mean() < 0.13
     assert ((lwc[cloudy] >= 1e-7) & (lwc[cloudy] <= 1e-6 + 1e-18)).all()
     json.dumps(mj)
+
+
+def test_process_variety_mechanism_holds_every_process_type():
+    mj = w.process_variety_mechanism()
+    types = {r["type"] for r in mj["reactions"]}
+    assert types == {"ARRHENIUS", "TROE", "PHOTOLYSIS", "EMISSION", "FIRST_ORDER_LOSS",
+                     "HL_PHASE_TRANSFER", "AQUEOUS_REVERSIBLE", "CUSTOM_H2O2", "CUSTOM_OH_HNO3",
+                     "CONDENSED_ARRHENIUS", "SIMPOL_PHASE_TRANSFER"}
+    assert json.dumps(mj) == json.dumps(w.process_variety_mechanism())
+    lay = w.layout(mj)
+    assert len(lay.species) == 18 + 4 * 7
