@@ -96,6 +96,10 @@ typedef struct {
  * *out is NULL, a message is copied to err (if errlen > 0) and
  * CAMP_E_PARSE / CAMP_E_UNSUPPORTED / CAMP_E_CUDA is returned.
  * Schema: see paper_2111_07436_gb300/workloads.py (module docstring).
+ * Process types (Table 2): ARRHENIUS, TROE, PHOTOLYSIS, EMISSION,
+ * FIRST_ORDER_LOSS, CUSTOM_H2O2, CUSTOM_OH_HNO3 (gas phase);
+ * HL_PHASE_TRANSFER, SIMPOL_PHASE_TRANSFER, AQUEOUS_REVERSIBLE,
+ * CONDENSED_ARRHENIUS (one instance per aerosol section).
  */
 int camp_mech_load(const char *json, size_t len, camp_mech **out, char *err, size_t errlen);
 

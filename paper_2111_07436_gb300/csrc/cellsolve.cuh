@@ -92,12 +92,29 @@ __device__ __forceinline__ double ipowd(double x, int k) {
     return r;
 }
 
+// A exp(C/T) (T/300)^B: the Arrhenius terms of the Troe and custom rate
+// constants (D = 300 K, E = 0)
+__device__ __forceinline__ double arr300(const double *par, double T) {
+    return __ldg(par) * exp(__ldg(par + 2) / T) * pow(T / 300.0, __ldg(par + 1));
+}
+
+// Condensation constant of one section, s^-1: N particles of radius rad,
+// each 4 pi rad Dg f_fs(Kn, alpha) with the Fuchs-Sutugin factor and
+// Kn = 3 Dg / (cbar rad), cbar = sqrt(8 R T / (pi MW))
+__device__ __forceinline__ double condensation(double rad, double Np, double alpha, double Dg,
+                                               double MW, double T) {
+    double cbar = sqrt(8.0 * RG * T / (PI_D * MW));
+    double Kn = 3.0 * Dg / cbar / rad;
+    double ffs = 0.75 * alpha * (1.0 + Kn) / (Kn * Kn + Kn + 0.283 * Kn * alpha + 0.75 * alpha);
+    return Np * 4.0 * PI_D * rad * Dg * ffs;
+}
+
 __device__ inline void rate_constant(const DevMech &m, int k, const double *__restrict__ env,
                                      double &kf, double &kr) {
     const double T = env[0], P = env[1];
     const double Mair = P / (KB * T) * 1e-6;  // molec cm^-3
     const double mppb = Mair * 1e-9;          // molec cm^-3 per ppb
-    const double *par = m.rpar + 8 * k;
+    const double *par = m.rpar + CAMP_NPAR * k;
     const int nr = __ldg(m.rnr + k);
     kf = 0.0;
     kr = 0.0;
@@ -111,12 +128,22 @@ __device__ inline void rate_constant(const DevMech &m, int k, const double *__re
     }
     case CAMP_P_TROE: {
         // k0[M] / (1 + k0[M]/kinf) * Fc^(1 / (1 + (log10(k0[M]/kinf)/N)^2))
-        double k0 = __ldg(par) * exp(__ldg(par + 2) / T) * pow(T / 300.0, __ldg(par + 1));
-        double ki = __ldg(par + 3) * exp(__ldg(par + 5) / T) * pow(T / 300.0, __ldg(par + 4));
+        double k0 = arr300(par, T);
+        double ki = arr300(par + 3, T);
         double x = k0 * Mair / ki;
         double lg = log10(x) / __ldg(par + 7);
         double kk = k0 * Mair / (1.0 + x) * pow(__ldg(par + 6), 1.0 / (1.0 + lg * lg));
         kf = kk * ipowd(mppb, nr - 1);
+        break;
+    }
+    case CAMP_P_CUSTOM_H2O2:
+        // k1 + k2 [M]
+        kf = (arr300(par, T) + arr300(par + 3, T) * Mair) * ipowd(mppb, nr - 1);
+        break;
+    case CAMP_P_CUSTOM_OH_HNO3: {
+        // k0 + k3[M] / (1 + k3[M] / k2)
+        double k3M = arr300(par + 6, T) * Mair;
+        kf = (arr300(par, T) + k3M / (1.0 + k3M / arr300(par + 3, T))) * ipowd(mppb, nr - 1);
         break;
     }
     case CAMP_P_PHOTOLYSIS:
@@ -124,23 +151,29 @@ __device__ inline void rate_constant(const DevMech &m, int k, const double *__re
     case CAMP_P_LOSS:
         kf = env[__ldg(m.rslot + k)];
         break;
-    case CAMP_P_HENRY: {
-        // H(T) [M/Pa]; k_c = 4 pi r Dg f_fs(Kn, alpha) per particle, times N;
-        // evaporation constant k_c / (H_cc L) with H_cc = 1000 H R T
+    case CAMP_P_HENRY:
+    case CAMP_P_SIMPOL: {
+        // condensation k_c per section; evaporation k_c / (H_cc L) with
+        // H_cc = 1000 H R T.  Henry: H(T) [M/Pa] from H298 and C.  SIMPOL:
+        // H = c_tot / p0 with the SIMPOL.1 vapour pressure
+        // log10 p0 [atm] = B1/T + B2 + B3 T + B4 ln T (Raoult's law in a
+        // condensed phase of fixed total molarity c_tot)
         const int b = __ldg(m.rslot + k);
         const double rad = env[m.env_sec_base + 3 * b];
         const double Np = env[m.env_sec_base + 3 * b + 1];
         const double L = env[m.env_sec_base + 3 * b + 2];
         if (!(L > 0.0 && Np > 0.0 && rad > 0.0)) break;
-        double H = __ldg(par) * exp(__ldg(par + 1) * (1.0 / T - 1.0 / 298.0));
-        double alpha = __ldg(par + 2), Dg = __ldg(par + 3), MW = __ldg(par + 4);
-        double Hcc = 1000.0 * H * RG * T;
-        double cbar = sqrt(8.0 * RG * T / (PI_D * MW));
-        double Kn = 3.0 * Dg / cbar / rad;
-        double ffs = 0.75 * alpha * (1.0 + Kn) / (Kn * Kn + Kn + 0.283 * Kn * alpha + 0.75 * alpha);
-        double kb = Np * 4.0 * PI_D * rad * Dg * ffs;
+        double H, kb;
+        if (__ldg(m.rtype + k) == CAMP_P_HENRY) {
+            H = __ldg(par) * exp(__ldg(par + 1) * (1.0 / T - 1.0 / 298.0));
+            kb = condensation(rad, Np, __ldg(par + 2), __ldg(par + 3), __ldg(par + 4), T);
+        } else {
+            double lg = __ldg(par) / T + __ldg(par + 1) + __ldg(par + 2) * T + __ldg(par + 3) * log(T);
+            H = __ldg(par + 7) / (101325.0 * exp10(lg));
+            kb = condensation(rad, Np, __ldg(par + 4), __ldg(par + 5), __ldg(par + 6), T);
+        }
         kf = kb;
-        kr = kb / (Hcc * L);
+        kr = kb / (1000.0 * H * RG * T * L);
         break;
     }
     case CAMP_P_AQREV: {
@@ -154,6 +187,18 @@ __device__ inline void rate_constant(const DevMech &m, int k, const double *__re
         double phi = 1e-9 * P / (RG * T * 1000.0 * L);
         kf = Keq * krev * ipowd(phi, nr - 1);
         kr = krev * ipowd(phi, __ldg(m.rnp + k) - 1);
+        break;
+    }
+    case CAMP_P_COND_ARRHENIUS: {
+        // Arrhenius in the section's condensed phase, M^(1-nr) s^-1:
+        // kf = k phi^(nr - 1) in ppb units
+        const int b = __ldg(m.rslot + k);
+        const double L = env[m.env_sec_base + 3 * b + 2];
+        if (!(L > 0.0)) break;
+        double kk = __ldg(par) * exp(__ldg(par + 2) / T) * pow(T / __ldg(par + 3), __ldg(par + 1)) *
+                    (1.0 + __ldg(par + 4) * P);
+        double phi = 1e-9 * P / (RG * T * 1000.0 * L);
+        kf = kk * ipowd(phi, nr - 1);
         break;
     }
     }
@@ -349,16 +394,15 @@ __device__ __forceinline__ bool bad_pivot(LT u) {
     return !(fabs(u) > tiny_pivot<LT>()) || !isfinite(u);
 }
 
-// Dense trailing block, right-looking in panels of W = 4 pivots.  For each
+// Dense trailing block, right-looking in panels of W pivots.  For each
 // panel: (1) factor its W columns over the rows below (lane l owns rows
 // l + 32 t); (2) forward-substitute the W pivot rows to the right of the
 // panel with the panel's unit lower triangle (lane l owns columns l + 32 t);
 // (3) one rank-W update of the trailing block, each entry loaded and stored
 // once per panel (the W multipliers of a row are broadcast loads).
 // Pivots are checked and replaced by their reciprocals.
-template <int NS, typename LT>
+template <int NS, int W, typename LT>
 __device__ __forceinline__ bool dense_factor(LT *A, int D, int LD, int lane, unsigned gm) {
-    constexpr int W = 4;
     bool bad = false;
     for (int kp = 0; kp < D; kp += W) {
         const int w = min(W, D - kp);
@@ -400,6 +444,7 @@ __device__ __forceinline__ bool dense_factor(LT *A, int D, int LD, int lane, uns
                 LT v = (LT)0;
                 if (act[t] && r < w) {
                     v = A[(kp + r) * LD + j];
+#pragma unroll
                     for (int p = 0; p < r; p++) v -= A[(kp + r) * LD + kp + p] * u[p][t];
                     A[(kp + r) * LD + j] = v;
                 }
@@ -442,7 +487,7 @@ __device__ __forceinline__ bool dense_factor(LT *A, int D, int LD, int lane, uns
                 }
             }
         }
-        if (i < D) {
+        if (i < D) {  // odd number of trailing rows: the last one alone
             const LT *l0p = A + i * LD + kp;
             LT l0[W];
 #pragma unroll
@@ -462,6 +507,9 @@ __device__ __forceinline__ bool dense_factor(LT *A, int D, int LD, int lane, uns
     }
     return bad;
 }
+
+// panel width of the dense factorisation
+constexpr int DENSE_W = 4;
 
 template <int G, typename LT>
 __device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigned gm) {
@@ -496,10 +544,10 @@ __device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigne
     LT *A = lu + m.dbase;
     switch ((m.D + 31) >> 5) {
     case 0: break;
-    case 1: bad |= dense_factor<1, LT>(A, m.D, m.LD, lane, gm); break;
-    case 2: bad |= dense_factor<2, LT>(A, m.D, m.LD, lane, gm); break;
-    case 3: bad |= dense_factor<3, LT>(A, m.D, m.LD, lane, gm); break;
-    default: bad |= dense_factor<4, LT>(A, m.D, m.LD, lane, gm); break;
+    case 1: bad |= dense_factor<1, DENSE_W, LT>(A, m.D, m.LD, lane, gm); break;
+    case 2: bad |= dense_factor<2, DENSE_W, LT>(A, m.D, m.LD, lane, gm); break;
+    case 3: bad |= dense_factor<3, DENSE_W, LT>(A, m.D, m.LD, lane, gm); break;
+    default: bad |= dense_factor<4, DENSE_W, LT>(A, m.D, m.LD, lane, gm); break;
     }
     return !__any_sync(gm, bad);
 }

@@ -19,8 +19,14 @@ enum {
     CAMP_P_EMISSION = 3,
     CAMP_P_LOSS = 4,
     CAMP_P_HENRY = 5,
-    CAMP_P_AQREV = 6
+    CAMP_P_AQREV = 6,
+    CAMP_P_CUSTOM_H2O2 = 7,
+    CAMP_P_CUSTOM_OH_HNO3 = 8,
+    CAMP_P_COND_ARRHENIUS = 9,
+    CAMP_P_SIMPOL = 10
 };
+
+#define CAMP_NPAR 10  // rate parameters per process
 
 // LU op encoding for the sparse (row-wise) part of the factorisation
 #define CAMP_OP_DIV 0x80000000u
@@ -36,7 +42,7 @@ struct DevMech {
 
     // --- rate constants (process order) ---
     const int *rtype;     // [R]
-    const double *rpar;   // [R][8]
+    const double *rpar;   // [R][CAMP_NPAR]
     const int *rslot;     // [R] env slot (runtime types) or section (section types)
     const int *rnr;       // [R] total reactant multiplicity
     const int *rnp;       // [R] total product multiplicity (reversible types)

@@ -31,13 +31,39 @@ static int type_code(const std::string &t) {
     if (t == "FIRST_ORDER_LOSS") return CAMP_P_LOSS;
     if (t == "HL_PHASE_TRANSFER") return CAMP_P_HENRY;
     if (t == "AQUEOUS_REVERSIBLE") return CAMP_P_AQREV;
+    if (t == "CUSTOM_H2O2") return CAMP_P_CUSTOM_H2O2;
+    if (t == "CUSTOM_OH_HNO3") return CAMP_P_CUSTOM_OH_HNO3;
+    if (t == "CONDENSED_ARRHENIUS") return CAMP_P_COND_ARRHENIUS;
+    if (t == "SIMPOL_PHASE_TRANSFER") return CAMP_P_SIMPOL;
     throw std::runtime_error("unknown reaction type '" + t + "'");
 }
 
 static bool is_runtime(int t) {
     return t == CAMP_P_PHOTOLYSIS || t == CAMP_P_EMISSION || t == CAMP_P_LOSS;
 }
-static bool is_sectioned(int t) { return t == CAMP_P_HENRY || t == CAMP_P_AQREV; }
+static bool is_sectioned(int t) {
+    return t == CAMP_P_HENRY || t == CAMP_P_AQREV || t == CAMP_P_COND_ARRHENIUS || t == CAMP_P_SIMPOL;
+}
+
+// total molarity of a condensed phase when a SIMPOL process names none: water
+static const double kWaterMolarity = 1000.0 / 18.015;
+
+// Arrhenius parameters A, B, C (from C or Ea), D, E into par[0..4]
+static void arrhenius_params(const Value &r, double *par) {
+    par[0] = r.number("A");
+    par[1] = r.number_or("B", 0.0);
+    par[2] = r.find("C") ? r.number("C") : -r.number_or("Ea", 0.0) / kBoltzmann;
+    par[3] = r.number_or("D", 300.0);
+    par[4] = r.number_or("E", 0.0);
+}
+
+// A, B, C of the Arrhenius terms <prefix>_A/_B/_C (D = 300 K, E = 0)
+static void arr300_params(const Value &r, const char *prefix, double *par) {
+    const std::string p(prefix);
+    par[0] = r.number(p + "_A");
+    par[1] = r.number_or(p + "_B", 0.0);
+    par[2] = r.number_or(p + "_C", 0.0);
+}
 
 template <class T>
 static void add_coef(std::vector<std::pair<int, T>> &v, int idx, T c) {
@@ -102,6 +128,23 @@ static void read_processes(const Value &root, HostMech &h) {
                     p.par[2] = r.number("alpha");
                     p.par[3] = r.number("Dg");
                     p.par[4] = r.number("MW");
+                } else if (t == CAMP_P_SIMPOL) {
+                    p.react.emplace_back(idx(r.string("gas")), 1);
+                    p.prod.emplace_back(idx(pre + r.string("aqueous")), 1.0);
+                    const Value &B = r.at("B");
+                    if (B.kind != Value::Array || B.arr.empty() || B.arr.size() > 4)
+                        throw std::runtime_error("SIMPOL 'B' must hold 1 to 4 numbers");
+                    for (size_t i = 0; i < B.arr.size(); i++) p.par[i] = B.arr[i].num;
+                    p.par[4] = r.number("alpha");
+                    p.par[5] = r.number("Dg");
+                    p.par[6] = r.number("MW");
+                    p.par[7] = r.number_or("c_tot", kWaterMolarity);
+                } else if (t == CAMP_P_COND_ARRHENIUS) {
+                    for (auto &kv : r.at("reactants").obj)
+                        add_coef(p.react, idx(pre + kv.first), as_multiplicity(kv.second.num, "stoichiometry"));
+                    if (const Value *pr = r.find("products"))
+                        for (auto &kv : pr->obj) add_coef(p.prod, idx(pre + kv.first), kv.second.num);
+                    arrhenius_params(r, p.par);
                 } else {
                     for (auto &kv : r.at("reactants").obj)
                         add_coef(p.react, idx(pre + kv.first), as_multiplicity(kv.second.num, "stoichiometry"));
@@ -127,11 +170,14 @@ static void read_processes(const Value &root, HostMech &h) {
             if (const Value *pr = r.find("products"))
                 for (auto &kv : pr->obj) add_coef(p.prod, idx(kv.first), kv.second.num);
             if (t == CAMP_P_ARRHENIUS) {
-                p.par[0] = r.number("A");
-                p.par[1] = r.number_or("B", 0.0);
-                p.par[2] = r.find("C") ? r.number("C") : -r.number_or("Ea", 0.0) / kBoltzmann;
-                p.par[3] = r.number_or("D", 300.0);
-                p.par[4] = r.number_or("E", 0.0);
+                arrhenius_params(r, p.par);
+            } else if (t == CAMP_P_CUSTOM_H2O2) {
+                arr300_params(r, "k1", p.par);
+                arr300_params(r, "k2", p.par + 3);
+            } else if (t == CAMP_P_CUSTOM_OH_HNO3) {
+                arr300_params(r, "k0", p.par);
+                arr300_params(r, "k2", p.par + 3);
+                arr300_params(r, "k3", p.par + 6);
             } else if (t == CAMP_P_TROE) {
                 p.par[0] = r.number("k0_A");
                 p.par[1] = r.number_or("k0_B", 0.0);
@@ -364,7 +410,7 @@ static void build_tables(HostMech &h) {
 
     // rate constants and rate terms
     h.rtype.resize(R); h.rslot.resize(R); h.rnr.resize(R); h.rnp.resize(R);
-    h.rpar.assign((size_t)R * 8, 0.0);
+    h.rpar.assign((size_t)R * CAMP_NPAR, 0.0);
     h.rfac.assign((size_t)R * 6, -1);
     h.rrev.assign(R, -1);
     h.n_rev = 0;
@@ -374,7 +420,7 @@ static void build_tables(HostMech &h) {
         const Process &p = h.procs[k];
         h.rtype[k] = p.type;
         h.rslot[k] = p.slot;
-        for (int i = 0; i < 8; i++) h.rpar[(size_t)k * 8 + i] = p.par[i];
+        for (int i = 0; i < CAMP_NPAR; i++) h.rpar[(size_t)k * CAMP_NPAR + i] = p.par[i];
         int c = 0, nr = 0, np = 0;
         for (auto &e : p.react)
             for (int m = 0; m < e.second; m++) { h.rfac[(size_t)k * 6 + c++] = ip[e.first]; nr++; }

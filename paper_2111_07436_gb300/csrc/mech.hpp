@@ -15,9 +15,11 @@ struct Process {
     int type = 0;
     std::vector<std::pair<int, int>> react;    // (species, multiplicity), distinct
     std::vector<std::pair<int, double>> prod;  // (species, yield), distinct
-    double par[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double par[CAMP_NPAR] = {};
     int slot = -1;                             // env slot or section
-    bool reversible() const { return type == CAMP_P_HENRY || type == CAMP_P_AQREV; }
+    bool reversible() const {
+        return type == CAMP_P_HENRY || type == CAMP_P_AQREV || type == CAMP_P_SIMPOL;
+    }
 };
 
 // Host image of one compiled mechanism.  Integer structure follows the rules

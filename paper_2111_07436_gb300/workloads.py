@@ -316,7 +316,7 @@ def process_variety_mechanism(seed=106, n_sections=4):
          "H298": float(_logu(rng, 1e4, 1e5)) / 101325.0, "C_H": float(rng.uniform(2000.0, 6000.0)),
          **transfer()},
         {"type": "HL_PHASE_TRANSFER", "gas": "SO2", "aqueous": "SO2aq",
-         "H298": float(_logu(rng, 0.5, 2.0)) / 101325.0, "C_H": float(rng.uniform(2000.0, 6000.0)),
+         "H298": float(_logu(rng, 1e2, 1e3)) / 101325.0, "C_H": float(rng.uniform(2000.0, 6000.0)),
          **transfer()},
         {"type": "SIMPOL_PHASE_TRANSFER", "gas": "ISOPP1", "aqueous": "SOA1",
          "B": [3.81e3, -2.13e1, 0.0, 0.0], **transfer()},

@@ -162,3 +162,22 @@ def test_stats_are_close_to_the_oracle(mechs):
     # same controller: the FP64 form takes the oracle's step sequence on most cells
     assert np.mean(sg[:, 0] == so[:, 0]) > 0.5
     assert abs(sg[:, 0].mean() / so[:, 0].mean() - 1) < 0.1
+
+
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+def test_every_process_type(form):
+    """CustomH2o2, CustomOhHno3, CondensedPhaseArrhenius and SIMPOL phase
+    transfer beside the other types (Table 2), over dry, hazy and cloudy
+    cells."""
+    mj = w.process_variety_mechanism()
+    text = json.dumps(mj)
+    gm, om = camp.Mechanism(text), oracle.Mechanism(text)
+    y0, env = w.cells(mj, 150, seed=61)
+    y1, env1 = w.cells(mj, 60, seed=62, cloud_fraction=0.5)
+    y0, env = np.concatenate([y0, y1]), np.concatenate([env, env1])
+    yg, st = _gpu_solve(gm, y0, env, 180.0, 1e-4, 1e-5, *form)
+    yo, sto, _ = om.solve(y0, env, 180.0, 1e-4, 1e-5)
+    assert (st == 0).all() and (sto == 0).all()
+    parity.check(om, y0, env, 180.0, 1e-4, 1e-5, yg, yo)
+    n_gas = len(mj["species"])
+    assert (yo[:, n_gas:] > 0).any()  # the condensed phase takes part

@@ -26,6 +26,8 @@ def _mechs():
     out["tiny_aq"] = w.add_aqueous_sections(w.gas_mechanism("t", 6, 3, 1, 1, 1, 1, seed=77, max_occupancy=8),
                                             seed=78, n_sections=2, n_phase_species=5, n_henry=2,
                                             n_split_eq=1, n_simple_eq=1)
+    out["variety"] = w.process_variety_mechanism()
+    out["variety_1sec"] = w.process_variety_mechanism(seed=9, n_sections=1)
     return out
 
 
