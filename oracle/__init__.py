@@ -56,15 +56,25 @@ def lib():
         L.om_lu_solve.argtypes = [ctypes.c_int, _dp, _ip, _dp]
         L.om_bdf_coefficients.argtypes = [ctypes.c_int, _dp, _dp]
         L.om_integrate.argtypes = [mp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp,
-                                   ctypes.c_int, ctypes.c_int, ctypes.c_double, _ip]
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_double, _ip, _dp]
         L.om_integrate.restype = ctypes.c_int
         L.om_solve.argtypes = [mp, ctypes.c_int64, _dp, _dp, ctypes.c_double, ctypes.c_double,
-                               _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _ip, _ip,
+                               _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _ip, _ip, _dp,
                                ctypes.c_int]
         L.om_bdf_step.argtypes = [mp, _dp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                   _dp, ctypes.c_int, _dp, _dp]
         L.om_bdf_step.restype = ctypes.c_double
     return _lib
+
+
+def _opt(step, size):
+    """An optional in/out float64 array as a pointer (None -> NULL)."""
+    if step is None:
+        return None
+    if not (isinstance(step, np.ndarray) and step.dtype == np.float64 and step.flags.c_contiguous
+            and step.size == size):
+        raise ValueError("step must be a contiguous float64 array of one value per cell")
+    return _p(step)
 
 
 def _p(a, t=_dp):
@@ -135,17 +145,22 @@ class Mechanism:
             raise ValueError("atol must be a scalar or one value per species")
         return a
 
-    def integrate(self, y0, env, dt, rtol, atol, max_steps=10000, hmin_frac=1e-10):
-        """One cell: returns (y, status, stats[steps, newton, jac, errfail])."""
+    def integrate(self, y0, env, dt, rtol, atol, max_steps=10000, hmin_frac=1e-10, step=None):
+        """One cell: returns (y, status, stats[steps, newton, jac, errfail]).
+        step: None (cold start) or a 1-element float64 array, in/out: the
+        warm-start step size (see camp_oracle.c, integrate_cell)."""
         y = _f64(y0).copy()
         a = self._atol(atol)
         st = np.zeros(4, dtype=np.int32)
         s = lib().om_integrate(self._ptr, _p(_f64(env)), _p(y), dt, rtol, _p(a), a.size,
-                               max_steps, hmin_frac, _p(st, _ip))
+                               max_steps, hmin_frac, _p(st, _ip), _opt(step, 1))
         return y, s, st
 
-    def solve(self, y0, env, dt, rtol, atol, threads=None, max_steps=10000, hmin_frac=1e-10):
-        """Many cells, y0 [C, n] and env [C, n_env]: returns (y, status, stats [C, 4])."""
+    def solve(self, y0, env, dt, rtol, atol, threads=None, max_steps=10000, hmin_frac=1e-10,
+              step=None):
+        """Many cells, y0 [C, n] and env [C, n_env]: returns (y, status, stats [C, 4]).
+        step: None (cold starts) or a float64 array [C], in/out warm-start
+        step sizes."""
         y = _f64(y0).copy()
         env = _f64(env)
         C = y.shape[0]
@@ -156,7 +171,7 @@ class Mechanism:
         stats = np.zeros((C, 4), dtype=np.int32)
         threads = threads or os.cpu_count() or 1
         lib().om_solve(self._ptr, C, _p(y), _p(env), dt, rtol, _p(a), a.size, max_steps,
-                       hmin_frac, _p(status, _ip), _p(stats, _ip), threads)
+                       hmin_frac, _p(status, _ip), _p(stats, _ip), _opt(step, C), threads)
         return y, status, stats
 
     def bdf_step(self, env, z, q, h, rtol, atol):

@@ -500,9 +500,18 @@ static double initial_step(om_ctx *c, const double *y0, const double *f0, const 
 
 /* Integrate one cell over [0, dt].  y in/out (unchanged unless status 0);
  * stats (may be NULL): steps, Newton iterations, Jacobian evaluations,
- * error-test failures. */
+ * error-test failures.
+ * step (may be NULL: every call a cold start, the paper's behaviour): warm
+ * start across consecutive calls for the same cell.  On input *step > 0
+ * replaces the initial-step estimate (the integration still starts at order
+ * 1, with h = min(*step, dt)); on output *step is the step size the
+ * controller held before the final step was cut to land on dt, or 0 if the
+ * cell failed. */
 static int integrate_cell(const om_mech *m, const double *env, double *y, double dt, double rtol,
-                          const double *atol, int atol_len, const om_opts *o, int *stats) {
+                          const double *atol, int atol_len, const om_opts *o, int *stats,
+                          double *step) {
+    const double h_in = step ? *step : 0.0;
+    if (step) *step = 0.0;
     int n = m->n_species;
     for (int i = 0; i < n; i++) if (!isfinite(y[i])) return OM_NONFINITE;
     for (int i = 0; i < m->n_env; i++) if (!isfinite(env[i])) return OM_NONFINITE;
@@ -525,7 +534,8 @@ static int integrate_cell(const om_mech *m, const double *env, double *y, double
     for (int i = 0; i < n; i++) w[i] = 1.0 / (rtol * fabs(y[i]) + atol[atol_len == 1 ? 0 : i]);
     fval(&c, y, f);
     if (!all_finite(n, f)) { status = OM_NONFINITE; goto done; }
-    double h = initial_step(&c, y, f, w, dt, y1, f1);
+    double h = h_in > 0.0 ? fmin(h_in, dt) : initial_step(&c, y, f, w, dt, y1, f1);
+    double h_held = h;  /* the step before any cut to land on dt */
     for (int i = 0; i < n; i++) { z[i] = y[i]; z[n + i] = h * f[i]; }
 
     while (t < T) {
@@ -535,6 +545,7 @@ static int integrate_cell(const om_mech *m, const double *env, double *y, double
         double err;
         for (;;) {                               /* attempts at one step */
             last = 0;
+            h_held = h;
             if (t + h >= T) {
                 if (t + h > T) { double eta = (T - t) / h; rescale(n, q, z, eta); h = T - t; }
                 last = 1;
@@ -623,6 +634,7 @@ static int integrate_cell(const om_mech *m, const double *env, double *y, double
         ep_valid = 1;
     }
     for (int i = 0; i < n; i++) y[i] = z[i];
+    if (step) *step = h_held;
 done:
     if (stats) {
         stats[0] = nst;
@@ -637,11 +649,12 @@ done:
 
 /* ---- public entry points (called through ctypes) ----------------------- */
 int om_integrate(const om_mech *m, const double *env, double *y, double dt, double rtol,
-                 const double *atol, int atol_len, int max_steps, double hmin_frac, int *stats) {
+                 const double *atol, int atol_len, int max_steps, double hmin_frac, int *stats,
+                 double *step) {
     om_opts o = {max_steps, hmin_frac};
     pthread_once(&coef_once, coef_init);
     if (stats) memset(stats, 0, 4 * sizeof(int));
-    return integrate_cell(m, env, y, dt, rtol, atol, atol_len, &o, stats);
+    return integrate_cell(m, env, y, dt, rtol, atol, atol_len, &o, stats, step);
 }
 
 typedef struct {
@@ -654,6 +667,7 @@ typedef struct {
     int atol_len;
     om_opts o;
     int *status, *stats;
+    double *step;
     int64_t next;
     pthread_mutex_t lock;
 } om_job;
@@ -670,7 +684,7 @@ static void *worker(void *arg) {
         memcpy(yc, j->y + cell * n, sizeof(double) * n);
         int st[4] = {0, 0, 0, 0};
         int s = integrate_cell(j->m, j->env + cell * ne, yc, j->dt, j->rtol, j->atol,
-                               j->atol_len, &j->o, st);
+                               j->atol_len, &j->o, st, j->step ? j->step + cell : NULL);
         if (s == OM_OK) memcpy(j->y + cell * n, yc, sizeof(double) * n);
         j->status[cell] = s;
         if (j->stats) memcpy(j->stats + 4 * cell, st, sizeof(st));
@@ -681,13 +695,14 @@ static void *worker(void *arg) {
 
 /* Integrate n_cells independent cells, y [n_cells][n] in/out, env
  * [n_cells][n_env], with n_threads host threads.  Cells whose status is not 0
- * keep their input state. */
+ * keep their input state.  step [n_cells] (may be NULL): warm start, as in
+ * integrate_cell. */
 void om_solve(const om_mech *m, int64_t n_cells, double *y, const double *env, double dt,
               double rtol, const double *atol, int atol_len, int max_steps, double hmin_frac,
-              int *status, int *stats, int n_threads) {
+              int *status, int *stats, double *step, int n_threads) {
     pthread_once(&coef_once, coef_init);
     om_job j = {m, n_cells, y, env, dt, rtol, atol, atol_len, {max_steps, hmin_frac},
-                status, stats, 0, PTHREAD_MUTEX_INITIALIZER};
+                status, stats, step, 0, PTHREAD_MUTEX_INITIALIZER};
     if (n_threads < 1) n_threads = 1;
     pthread_t *th = malloc(sizeof(pthread_t) * n_threads);
     for (int i = 0; i < n_threads; i++) pthread_create(&th[i], NULL, worker, &j);

@@ -411,6 +411,52 @@ def test_first_order_chain_bateman():
     assert lay.species[:3] == ["A", "B", "C"]
 
 
+def test_warm_start_keeps_the_analytic_solution_and_saves_steps():
+    """Opt-in warm start: the step size carried across consecutive calls.
+    Whatever the carried value, the A -> B -> C chain stays on its Bateman
+    solution; carried from the previous call it takes fewer steps over 60
+    consecutive calls than cold starts do."""
+    import json
+    from paper_2111_07436_gb300 import workloads as w
+    mj = w.small_gas_mechanism()
+    m = oracle.Mechanism(json.dumps(mj))
+    y0, env = w.cells(mj, 1, seed=201, T=298.0, P=101300.0, sza=False)
+    y0, env = y0[0], env[0]
+    k1, k2 = env[2], env[3]
+    A0, B0, C0 = y0[:3]
+    t = 60.0
+    A = A0 * math.exp(-k1 * t)
+    B = B0 * math.exp(-k2 * t) + A0 * k1 / (k2 - k1) * (math.exp(-k1 * t) - math.exp(-k2 * t))
+    for h in (1e-6, 1.0, 1e4):
+        step = np.array([h])
+        y, s, _ = m.integrate(y0, env, t, 1e-10, 1e-14, step=step)
+        assert s == 0 and 0.0 < step[0] <= 10.0 * t
+        np.testing.assert_allclose(y[:3], [A, B, A0 + B0 + C0 - A - B], rtol=1e-8)
+    # 60 consecutive calls of 60 s: warm chains take fewer steps than cold
+    # ones, and their global error stays proportional to rtol within the
+    # bound of the tolerance-proportionality pin (100 rtol)
+    T = 3600.0
+    A = A0 * math.exp(-k1 * T)
+    B = B0 * math.exp(-k2 * T) + A0 * k1 / (k2 - k1) * (math.exp(-k1 * T) - math.exp(-k2 * T))
+    exact = np.array([A, B, A0 + B0 + C0 - A - B])
+    for rtol in (1e-4, 1e-6):
+        totals = []
+        for warm in (False, True):
+            y, step, n = y0.copy(), np.array([0.0]), 0
+            for _ in range(60):
+                y, s, st = m.integrate(y, env, 60.0, rtol, 1e-5 * rtol / 1e-4,
+                                       step=step if warm else None)
+                assert s == 0
+                n += st[0]
+            totals.append(n)
+            np.testing.assert_allclose(y[:3], exact, rtol=100 * rtol)
+        assert totals[1] < totals[0]
+    # a failed cell hands back 0 (the next call starts cold)
+    step = np.array([5.0])
+    _, s, _ = m.integrate(y0, env, 1e4, 1e-8, 1e-12, max_steps=3, step=step)
+    assert s == 1 and step[0] == 0.0
+
+
 def test_reversible_pair_relaxes_to_equilibrium():
     kfw, kbw = 0.3, 0.05  # A <-> B with K_eq kr = 0.3, kr = 0.05 (linear in ppb)
     m = oracle.Mechanism(M.mech(["G"], [M.aqrev({"a": 1}, {"b": 1}, A=kfw / kbw, kr=kbw)],
