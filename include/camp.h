@@ -162,6 +162,17 @@ typedef struct {
                                 camp_workspace_bytes() bytes; NULL: the
                                 mechanism's own (then calls on one mechanism
                                 must not overlap on the GPU) */
+    double *step;            /* optional device [n_cells], in/out: warm start
+                                across consecutive calls for the same cells
+                                (an opt-in; NULL = every call a cold start,
+                                the paper's behaviour, Sect. 2.4.2).  In: a
+                                value > 0 replaces the initial-step estimate
+                                (the cell still starts at order 1, with
+                                h = min(value, dt)).  Out: the step size the
+                                controller held before its final step was cut
+                                to land on dt; 0 for a cell whose status is
+                                not 0.  camp_solve_host and
+                                camp_solve_host_static take a host array. */
 } camp_solve_opts;
 
 /* Fill *o with the defaults for `variant`. */
@@ -247,6 +258,7 @@ typedef struct {
     int32_t *status;
     int32_t *stats;      /* optional, as camp_solve_opts.stats */
     void *workspace;     /* optional, as camp_solve_opts.workspace */
+    double *step;        /* optional, as camp_solve_opts.step */
 } camp_group;
 
 int camp_solve_batch(const camp_group *groups, int32_t n_groups, double dt, double rtol,

@@ -45,13 +45,14 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("max_steps", ctypes.c_int32), ("cells_per_block", ctypes.c_int32),
                 ("hmin_frac", ctypes.c_double), ("stats", ctypes.c_void_p),
-                ("workspace", ctypes.c_void_p)]
+                ("workspace", ctypes.c_void_p), ("step", ctypes.c_void_p)]
 
 
 class Group(ctypes.Structure):
     _fields_ = [("mech", ctypes.c_void_p), ("n_cells", ctypes.c_int64), ("state", ctypes.c_void_p),
                 ("env", ctypes.c_void_p), ("atol", ctypes.c_void_p), ("atol_len", ctypes.c_int32),
-                ("status", ctypes.c_void_p), ("stats", ctypes.c_void_p), ("workspace", ctypes.c_void_p)]
+                ("status", ctypes.c_void_p), ("stats", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("step", ctypes.c_void_p)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -192,12 +193,13 @@ class Mechanism:
 
     def solve(self, state, env, dt, rtol, atol, status=None, variant=VARIANT_MIXED,
               persistent=None, max_steps=10000, cells_per_block=0, stats=None, workspace=None,
-              stream=None):
+              stream=None, step=None):
         """Integrate every cell over [0, dt] in place (asynchronous on `stream`).
 
         state [C, n] / env [C, n_env]: float64 CUDA tensors; status: int32
-        CUDA tensor [C] (allocated if None); stats: optional int32 [C, NSTATS].
-        Returns status.
+        CUDA tensor [C] (allocated if None); stats: optional int32 [C, NSTATS];
+        step: optional float64 CUDA tensor [C], in/out warm-start step sizes
+        (camp_solve_opts.step).  Returns status.
         """
         import torch
         C = state.shape[0]
@@ -207,6 +209,9 @@ class Mechanism:
             status = torch.empty(C, dtype=torch.int32, device=state.device)
         a = atol if isinstance(atol, torch.Tensor) else self._atol(atol, state.device)
         o = self.opts(variant, persistent, max_steps, cells_per_block, stats, workspace)
+        if step is not None:
+            _dev_f64(step, (C,), "step")
+            o.step = step.data_ptr()
         _check(lib().camp_solve(self._h, C, _ptr(state), _ptr(env), float(dt), float(rtol), _ptr(a),
                                 a.numel(), _ptr(status), ctypes.byref(o), _stream(stream)))
         return status
@@ -236,9 +241,10 @@ class Mechanism:
         return o
 
     def solve_host(self, state, env, dt, rtol, atol, variant=VARIANT_MIXED, persistent=None,
-                   max_steps=10000, cells_per_block=0, stats=None, stream=None):
+                   max_steps=10000, cells_per_block=0, stats=None, stream=None, step=None):
         """Host arrays (numpy float64, C-contiguous; pinned torch tensors also
-        work): state is updated in place; returns the status array."""
+        work): state is updated in place; returns the status array.  step:
+        optional float64 array [C], in/out warm-start step sizes."""
         st = state if isinstance(state, np.ndarray) else state.numpy()
         ev = env if isinstance(env, np.ndarray) else env.numpy()
         if st.dtype != np.float64 or not st.flags.c_contiguous or st.shape[1] != self.n:
@@ -254,6 +260,10 @@ class Mechanism:
         o.max_steps = max_steps
         o.cells_per_block = cells_per_block
         o.stats = stats.ctypes.data if stats is not None else None
+        if step is not None:
+            if step.dtype != np.float64 or not step.flags.c_contiguous or step.shape != (st.shape[0],):
+                raise CampError("step must be C-contiguous float64 [C]")
+            o.step = step.ctypes.data
         _check(lib().camp_solve_host(self._h, st.shape[0], ctypes.c_void_p(st.ctypes.data),
                                      ctypes.c_void_p(ev.ctypes.data), float(dt), float(rtol),
                                      ctypes.c_void_p(a.ctypes.data), a.size,
@@ -373,7 +383,7 @@ def workspace(device):
 
 def solve_batch(groups, dt, rtol, variant=VARIANT_MIXED, stream=None):
     """groups: list of dicts {mech, state, env, atol (tensor), status, stats?,
-    workspace?} of device tensors; one call, one persistent grid per group."""
+    workspace?, step?} of device tensors; one call, one persistent grid per group."""
     arr = (Group * len(groups))()
     for i, g in enumerate(groups):
         m = g["mech"]
@@ -383,7 +393,8 @@ def solve_batch(groups, dt, rtol, variant=VARIANT_MIXED, stream=None):
         arr[i] = Group(m._h.value, C, g["state"].data_ptr(), g["env"].data_ptr(), g["atol"].data_ptr(),
                        g["atol"].numel(), g["status"].data_ptr(),
                        g["stats"].data_ptr() if g.get("stats") is not None else None,
-                       g["workspace"].data_ptr() if g.get("workspace") is not None else None)
+                       g["workspace"].data_ptr() if g.get("workspace") is not None else None,
+                       g["step"].data_ptr() if g.get("step") is not None else None)
     o = SolveOpts()
     lib().camp_solve_opts_default(ctypes.byref(o), variant)
     _check(lib().camp_solve_batch(arr, len(groups), float(dt), float(rtol), ctypes.byref(o), _stream(stream)))

@@ -242,6 +242,7 @@ void camp_solve_opts_default(camp_solve_opts *o, int variant) {
     o->hmin_frac = 1e-10;
     o->stats = nullptr;
     o->workspace = nullptr;
+    o->step = nullptr;
 }
 
 size_t camp_workspace_bytes(void) { return 256; }
@@ -304,6 +305,7 @@ int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double
     a.atol_len = atol_len;
     a.status = status;
     a.stats = o.stats;
+    a.step = o.step;
     a.max_steps = o.max_steps;
     a.hmin_frac = o.hmin_frac;
     a.cpb = cpb;
@@ -346,7 +348,9 @@ int camp_solve_host(const camp_mech *mc, int64_t n_cells, double *state, const d
     const size_t b_stat = ((size_t)n_cells * 4 + 15) & ~(size_t)15, b_atol = (n * 8 + 15) & ~(size_t)15;
     const size_t b_stats = (size_t)n_cells * 4 * CAMP_NSTATS;
     int32_t *host_stats = opts ? opts->stats : nullptr;
-    const size_t need = b_state + b_env + b_stat + b_atol + (host_stats ? b_stats : 0);
+    double *host_step = opts ? opts->step : nullptr;
+    const size_t b_step = host_step ? (((size_t)n_cells * 8 + 15) & ~(size_t)15) : 0;
+    const size_t need = b_state + b_env + b_stat + b_atol + b_step + (host_stats ? b_stats : 0);
     std::lock_guard<std::mutex> lk(m->stage_mu);
     if (m->stage_bytes < need) {
         if (m->stage) cudaFree(m->stage);
@@ -360,19 +364,23 @@ int camp_solve_host(const camp_mech *mc, int64_t n_cells, double *state, const d
     double *d_env = (double *)(base + b_state);
     int32_t *d_status = (int32_t *)(base + b_state + b_env);
     double *d_atol = (double *)(base + b_state + b_env + b_stat);
-    int32_t *d_stats = host_stats ? (int32_t *)(base + b_state + b_env + b_stat + b_atol) : nullptr;
+    double *d_step = host_step ? (double *)(base + b_state + b_env + b_stat + b_atol) : nullptr;
+    int32_t *d_stats = host_stats ? (int32_t *)(base + b_state + b_env + b_stat + b_atol + b_step) : nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(cudaMemcpyAsync(d_state, state, b_state, cudaMemcpyHostToDevice, s));
+    if (host_step) CUDA_TRY(cudaMemcpyAsync(d_step, host_step, (size_t)n_cells * 8, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(d_env, env, b_env, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(d_atol, atol, (size_t)atol_len * 8, cudaMemcpyHostToDevice, s));
     camp_solve_opts o;
     camp_solve_opts_default(&o, opts ? opts->variant : CAMP_VARIANT_MIXED);
     if (opts) o = *opts;
     o.stats = d_stats;
+    o.step = d_step;
     o.workspace = nullptr;
     int rc = camp_solve(m, n_cells, d_state, d_env, dt, rtol, d_atol, atol_len, d_status, &o, stream);
     if (rc != CAMP_OK) return rc;
     CUDA_TRY(cudaMemcpyAsync(state, d_state, b_state, cudaMemcpyDeviceToHost, s));
+    if (host_step) CUDA_TRY(cudaMemcpyAsync(host_step, d_step, (size_t)n_cells * 8, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(status, d_status, (size_t)n_cells * 4, cudaMemcpyDeviceToHost, s));
     if (host_stats)
         CUDA_TRY(cudaMemcpyAsync(host_stats, d_stats, b_stats, cudaMemcpyDeviceToHost, s));
@@ -418,6 +426,7 @@ int camp_solve_batch(const camp_group *groups, int32_t n_groups, double dt, doub
         if (opts) o = *opts;
         o.stats = gr.stats;
         o.workspace = gr.workspace;
+        o.step = gr.step;
         if (o.persistent < 0) o.persistent = 1;
         if (!o.workspace && n_groups > 1 && o.persistent)
             return fail(CAMP_E_INVAL, "each group of a multi-group persistent solve needs its own workspace");

@@ -509,7 +509,7 @@ __device__ __forceinline__ bool dense_factor(LT *A, int D, int LD, int lane, uns
 }
 
 // panel width of the dense factorisation
-constexpr int DENSE_W = 4;
+constexpr int DENSE_W = 8;
 
 template <int G, typename LT>
 __device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigned gm) {
@@ -575,6 +575,7 @@ __device__ __forceinline__ void dense_subst(const LT *A, int D, int LD, LT *xb, 
     for (int kb = 0; kb < NS; kb++) {
         const int k0 = 32 * kb, k1 = min(D, k0 + 32);
         int k = k0;
+#pragma unroll 2
         for (; k + 1 < k1; k += 2) {
             const int o = k - k0;
             const LT xk = __shfl_sync(gm, xr[kb], o);
@@ -607,6 +608,7 @@ __device__ __forceinline__ void dense_subst(const LT *A, int D, int LD, LT *xb, 
     for (int kb = NS - 1; kb >= 0; kb--) {
         const int k0 = 32 * kb, k1 = min(D, k0 + 32);
         int k = k1 - 1;
+#pragma unroll 2
         for (; k - 1 >= k0; k -= 2) {
             const int o = k - k0;  // pivots k and k-1
             const LT xk = __shfl_sync(gm, xr[kb], o) * A[k * LD + k];
@@ -648,11 +650,12 @@ __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, uns
     LT *x = c.x;
     const LT *lu = c.lu;
     __syncwarp(gm);
-    // forward, sparse rows and the L21 part of block rows
-    for (int L = 0; L < m.n_flev; L++) {
-        int b = __ldg(m.flev_ptr + L), e = __ldg(m.flev_ptr + L + 1);
+    // forward, sparse rows and the L21 part of block rows (rows without L
+    // entries keep their value)
+    for (int L = 0; L < m.n_slev; L++) {
+        int b = __ldg(m.slev_ptr + L), e = __ldg(m.slev_ptr + L + 1);
         for (int r = b + lane; r < e; r += G) {
-            int i = __ldg(m.frow + r);
+            int i = __ldg(m.srow + r);
             LT s = x[i], s2 = (LT)0;
             int qb = __ldg(m.sl_ptr + i), qe = __ldg(m.sl_ptr + i + 1);
             int q = qb;
@@ -777,13 +780,17 @@ struct CellStats {
 
 // ---- one cell over [0, dt] ---------------------------------------------------
 // y_cell/env_cell: this cell's rows (declaration order).  Returns the status;
-// the state is written back only on success.
+// the state is written back only on success.  step_io (null: cold start):
+// warm start, in: a value > 0 replaces the initial-step estimate; out: the
+// step held before the final cut to dt, 0 on failure.
 template <int G, int NPL, typename LT>
 __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__restrict__ y_cell,
                               const double *__restrict__ env_cell, double dt, double rtol,
                               const double *__restrict__ atol, int atol_len, int max_steps,
-                              double hmin_frac, int lane, unsigned gm, CellStats &st) {
+                              double hmin_frac, double *step_io, int lane, unsigned gm,
+                              CellStats &st) {
     const int n = m.n;
+    const double h_in = step_io ? *step_io : 0.0;
     st.steps = st.newton = st.jac = st.errfail = st.ordsum = 0;
 
     // inputs must be finite
@@ -807,7 +814,12 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
         atl[s] = a;
         e[s] = ep[s] = 0.0;
     }
-    if (__any_sync(gm, bad)) return ST_NONFINITE;
+    // a cell that fails hands back no step (the next call starts cold)
+    auto fail_early = [&](int code) {
+        if (step_io && lane == 0) *step_io = 0.0;
+        return code;
+    };
+    if (__any_sync(gm, bad)) return fail_early(ST_NONFINITE);
 
     for (int k = lane; k < m.R; k += G) {
         double a, b;
@@ -835,11 +847,14 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
     const double T = dt, hmin = hmin_frac * dt;
     set_weights();
     eval_f<G, NPL, LT>(m, c, z[0], f, lane, gm);
-    if (any_nonfinite(f)) return ST_NONFINITE;
+    if (any_nonfinite(f)) return fail_early(ST_NONFINITE);
 
-    // initial step: Hairer, Norsett & Wanner's starting-step estimate for order 1
+    // initial step: the carried one, else Hairer, Norsett & Wanner's
+    // starting-step estimate for order 1
     double h;
-    {
+    if (h_in > 0.0) {
+        h = fmin(h_in, T);
+    } else {
         double d0 = wrms<G, NPL>(m, z[0], w, gm), d1 = wrms<G, NPL>(m, f, w, gm);
         double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
         if (h0 > T) h0 = T;
@@ -861,6 +876,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
     }
 
     int q = 1, qwait = 2, nst = 0, nst_lu = 0;
+    double h_held = h;
     bool have_lu = false, need_setup = true, ep_valid = false;
     double t = 0.0, gamma_lu = 0.0, rgamma_lu = 0.0;
     int status = ST_OK;
@@ -880,6 +896,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
         bool accepted = false;
         while (!accepted) {
             last = false;
+            h_held = h;
             if (t + h >= T) {
                 if (t + h > T) {
                     double eta = (T - t) / h;
@@ -1069,6 +1086,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
             if (p < n) y_cell[__ldg(m.perm + p)] = z[0][s];
         }
     }
+    if (step_io && lane == 0) *step_io = status == ST_OK ? h_held : 0.0;
     return status;
 }
 

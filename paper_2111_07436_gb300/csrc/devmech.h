@@ -108,7 +108,11 @@ struct DevMech {
     const int *fops_ptr;  // [n+1]
     const uint32_t *fops; // encoded DIV/UPD ops
 
-    // forward substitution of the sparse part: rows by level (flev), entries
+    // forward substitution of the sparse part: the rows that have L entries,
+    // by level (rows within a level ordered to balance the lanes), entries
+    int n_slev;
+    const int *slev_ptr;  // [n_slev+1] into srow
+    const int *srow;
     const int *sl_ptr;    // [n+1]
     const int *sl_off;    // storage offset of L(i,k)
     const int *sl_col;    // k

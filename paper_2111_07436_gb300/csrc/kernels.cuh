@@ -38,7 +38,7 @@ __global__ void __maxnreg__(NPL >= 6 ? 232 : 168) k_solve(DevMech m, SolveArgs a
         CellStats st;
         int s = integrate_cell<G, NPL, LT>(m, c, a.state + cell * m.n, a.env + cell * m.n_env, a.dt,
                                            a.rtol, a.atol, a.atol_len, a.max_steps, a.hmin_frac,
-                                           lane, gm, st);
+                                           a.step ? a.step + cell : nullptr, lane, gm, st);
         if (lane == 0) {
             a.status[cell] = s;
             if (a.stats) {

@@ -15,6 +15,7 @@ struct SolveArgs {
     int atol_len;
     int32_t *status;
     int32_t *stats;
+    double *step;                   // warm-start step sizes [n_cells] or null
     int max_steps;
     double hmin_frac;
     int cpb;                        // cells per block

@@ -403,6 +403,33 @@ static void build_structure(HostMech &h) {
     }
 }
 
+// Order the rows of one level, rows[b, e), so that the G = 32 lanes get even
+// work: lane l takes positions b + l, b + l + 32, ...  Rows go heaviest
+// first to the lane with the least work among those with a free position.
+template <class Cost>
+static void balance_level(std::vector<int> &rows, int b, int e, Cost cost) {
+    const int len = e - b;
+    if (len <= 32) {  // one row per lane: order only
+        std::stable_sort(rows.begin() + b, rows.begin() + e, [&](int x, int y) { return cost(x) > cost(y); });
+        return;
+    }
+    std::vector<int> sorted(rows.begin() + b, rows.begin() + e);
+    std::stable_sort(sorted.begin(), sorted.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    std::vector<long long> load(32, 0);
+    std::vector<std::vector<int>> mine(32);
+    std::vector<int> cap(32);
+    for (int l = 0; l < 32; l++) cap[l] = (len - l + 31) / 32;
+    for (int r : sorted) {
+        int best = -1;
+        for (int l = 0; l < 32; l++)
+            if ((int)mine[l].size() < cap[l] && (best < 0 || load[l] < load[best])) best = l;
+        mine[best].push_back(r);
+        load[best] += cost(r);
+    }
+    for (int l = 0; l < 32; l++)
+        for (size_t k = 0; k < mine[l].size(); k++) rows[b + l + 32 * (int)k] = mine[l][k];
+}
+
 // ---- device tables -----------------------------------------------------------
 static void build_tables(HostMech &h) {
     const int n = h.n, R = (int)h.procs.size();
@@ -630,6 +657,23 @@ static void build_tables(HostMech &h) {
         h.sl_ptr.push_back((int)h.sl_off.size());
         h.su_ptr.push_back((int)h.su_off.size());
     }
+    // the factorisation's levels balanced by update count; the forward
+    // substitution skips rows without L entries and balances by entry count
+    for (size_t l = 0; l + 1 < h.flev_ptr.size(); l++)
+        balance_level(h.frow, h.flev_ptr[l], h.flev_ptr[l + 1],
+                      [&](int i) { return h.fops_ptr[i + 1] - h.fops_ptr[i] + 1; });
+    h.slev_ptr.assign(1, 0);
+    h.srow.clear();
+    for (size_t l = 0; l + 1 < h.flev_ptr.size(); l++) {
+        for (int r = h.flev_ptr[l]; r < h.flev_ptr[l + 1]; r++) {
+            const int i = h.frow[r];
+            if (h.sl_ptr[i + 1] > h.sl_ptr[i]) h.srow.push_back(i);
+        }
+        if ((int)h.srow.size() == h.slev_ptr.back()) continue;
+        h.slev_ptr.push_back((int)h.srow.size());
+        const int b = h.slev_ptr[h.slev_ptr.size() - 2], e = h.slev_ptr.back();
+        balance_level(h.srow, b, e, [&](int i) { return h.sl_ptr[i + 1] - h.sl_ptr[i] + 1; });
+    }
     std::vector<int> bl(n, 0);
     int maxb = -1;
     for (int i = h.d - 1; i >= 0; i--) {
@@ -646,6 +690,8 @@ static void build_tables(HostMech &h) {
     for (int l = 0; l <= maxb; l++) {
         for (int i = 0; i < h.d; i++) if (bl[i] == l) h.brow.push_back(i);
         h.blev_ptr.push_back((int)h.brow.size());
+        const int b = h.blev_ptr[h.blev_ptr.size() - 2], e = h.blev_ptr.back();
+        balance_level(h.brow, b, e, [&](int i) { return h.su_ptr[i + 1] - h.su_ptr[i] + 1; });
     }
 }
 
@@ -732,6 +778,9 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.fops_ptr = pk.put(h.fops_ptr);
     dm.fops = pk.put(h.fops);
     dm.sl_ptr = pk.put(h.sl_ptr);
+    dm.n_slev = (int)h.slev_ptr.size() - 1;
+    dm.slev_ptr = pk.put(h.slev_ptr);
+    dm.srow = pk.put(h.srow);
     dm.sl_off = pk.put(h.sl_off);
     dm.sl_col = pk.put(h.sl_col);
     dm.n_blev = (int)h.blev_ptr.size() - 1;

@@ -49,6 +49,7 @@ struct HostMech {
     std::vector<int> flev_ptr, frow, fops_ptr;
     std::vector<uint32_t> fops;
     std::vector<int> sl_ptr, sl_off, sl_col;
+    std::vector<int> slev_ptr, srow;  // forward substitution: rows with L entries, by level
     std::vector<int> blev_ptr, brow, su_ptr, su_off, su_col, udiag;
     long long factor_updates = 0;  // multiply-adds one device factorisation executes
     // algorithmic work of the method, from the symbolic structure

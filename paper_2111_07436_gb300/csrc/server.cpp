@@ -93,6 +93,7 @@ struct camp_server {
             camp_solve_opts o = r->opts;
             o.workspace = workspaces[r->slot];
             o.stats = nullptr;
+            o.step = nullptr;  // chunks are independent: always a cold start
             rc = camp_solve(r->mech, r->n_cells, d_state, d_env, r->dt, r->rtol, d_atol, 1, d_status, &o, s);
         }
         if (e == cudaSuccess && rc == CAMP_OK) e = cudaMemcpyAsync(r->state, d_state, bs, cudaMemcpyDeviceToHost, s);

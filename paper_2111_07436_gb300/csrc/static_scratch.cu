@@ -34,13 +34,15 @@ extern "C" int camp_solve_host_static(const camp_mech *m, int64_t n_cells, doubl
     if (atol_len != 1 && atol_len != inf.n_species)
         return camp_record_error(CAMP_E_INVAL, "atol_len must be 1 or n_species");
     int32_t *host_stats = opts ? opts->stats : nullptr;
+    double *host_step = opts ? opts->step : nullptr;
+    const size_t b_step = host_step ? al256((size_t)n_cells * 8) : 0;
     const size_t b_state = al256((size_t)n_cells * inf.n_species * 8);
     const size_t b_env = al256((size_t)n_cells * inf.n_env * 8);
     const size_t b_status = al256((size_t)n_cells * 4);
     const size_t b_atol = al256((size_t)atol_len * 8);
     const size_t b_stats = host_stats ? al256((size_t)n_cells * 4 * CAMP_NSTATS) : 0;
     const size_t b_ws = al256(camp_workspace_bytes());
-    const size_t need = b_state + b_env + b_status + b_atol + b_stats + b_ws;
+    const size_t need = b_state + b_env + b_status + b_atol + b_stats + b_ws + b_step;
     if (need > (size_t)CAMP_STATIC_SCRATCH_BYTES) {
         std::string msg = "chunk needs " + std::to_string(need) + " bytes of staging, more than the " +
                           std::to_string((size_t)CAMP_STATIC_SCRATCH_BYTES) +
@@ -67,18 +69,21 @@ extern "C" int camp_solve_host_static(const camp_mech *m, int64_t n_cells, doubl
     double *d_atol = (double *)(base + b_state + b_env + b_status);
     int32_t *d_stats = host_stats ? (int32_t *)(base + b_state + b_env + b_status + b_atol) : nullptr;
     void *d_ws = base + b_state + b_env + b_status + b_atol + b_stats;
+    double *d_step = host_step ? (double *)(base + b_state + b_env + b_status + b_atol + b_stats + b_ws) : nullptr;
 
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n_state = (size_t)n_cells * inf.n_species * 8, n_env = (size_t)n_cells * inf.n_env * 8;
     cudaError_t e = cudaMemcpyAsync(d_state, state, n_state, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_env, env, n_env, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_atol, atol, (size_t)atol_len * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && host_step) e = cudaMemcpyAsync(d_step, host_step, (size_t)n_cells * 8, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess)
         return camp_record_error(CAMP_E_CUDA, (std::string("staging copy: ") + cudaGetErrorString(e)).c_str());
     camp_solve_opts o;
     camp_solve_opts_default(&o, opts ? opts->variant : CAMP_VARIANT_MIXED);
     if (opts) o = *opts;
     o.stats = d_stats;
+    o.step = d_step;
     o.workspace = d_ws;  // the persistent grid's counter: zeroed by camp_solve
     int rc = camp_solve(m, n_cells, d_state, d_env, dt, rtol, d_atol, atol_len, d_status, &o, stream);
     if (rc != CAMP_OK) return rc;
@@ -86,6 +91,8 @@ extern "C" int camp_solve_host_static(const camp_mech *m, int64_t n_cells, doubl
     if (e == cudaSuccess) e = cudaMemcpyAsync(status, d_status, (size_t)n_cells * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && host_stats)
         e = cudaMemcpyAsync(host_stats, d_stats, (size_t)n_cells * 4 * CAMP_NSTATS, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && host_step)
+        e = cudaMemcpyAsync(host_step, d_step, (size_t)n_cells * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess)
         return camp_record_error(CAMP_E_CUDA, (std::string("result copy: ") + cudaGetErrorString(e)).c_str());
