@@ -275,9 +275,11 @@ def main():
            "vs_baseline": None, "dtype": "f64 state / f32 J+LU" if variant == camp.VARIANT_MIXED else "f64",
            "data": "synthetic (seeded generator shaped like the paper's gas mechanism)",
            "config": config, "form": f"{a.variant} {'persistent' if persistent else 'static'}",
-           "ok_cells": ok, "gpu_launches": a.steps,
+           "ok_cells": ok, "gpu_launches": a.steps * wl.n_outer,
            "work": {"bdf_steps": steps, "newton_iters": newton, "lu_setups": jac, "mean_order": qbar,
-                    "steps_per_cell": steps / C},
+                    "steps_per_cell": steps / C,
+                    "per_s": {k: v * wl.n_outer * world / (ms / 1e3) for k, v in
+                              (("bdf_steps", steps), ("newton_iters", newton), ("lu_setups", jac))}},
            "plain_fp64": plain, "mixed_over_plain": (value / world / plain["value"]) if plain else None,
            "roofline": roof, "hbm_io_gbs": hbm, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary()}
     print(json.dumps(out))

@@ -204,6 +204,27 @@ __device__ inline void rate_constant(const DevMech &m, int k, const double *__re
     }
 }
 
+// FP64 values into and out of the LU precision
+template <typename LT> __device__ __forceinline__ LT to_lu(double x);
+template <> __device__ __forceinline__ float to_lu<float>(double x) { return (float)x; }
+template <> __device__ __forceinline__ double to_lu<double>(double x) { return x; }
+__device__ __forceinline__ double from_lu(float x) { return (double)x; }
+__device__ __forceinline__ double from_lu(double x) { return x; }
+
+// One lane's term (x w)^2 of the Newton update's squared norm, in the LU
+// precision.  In FP32 a weight beyond the format's range (atol below ~3e-39
+// on a species near zero) is held at its largest value and the product at
+// 1e18, so the sum stays finite; either only arises far from convergence.
+// A non-finite x is caught separately.
+__device__ __forceinline__ float upd_term(float x, double w) {
+    const float t = fminf(fabsf(x * fminf((float)w, 3.4e38f)), 1e18f);
+    return t * t;
+}
+__device__ __forceinline__ double upd_term(double x, double w) {
+    const double t = x * w;
+    return t * t;
+}
+
 // finite test on the exponent bits (integer pipe, not the FP64 pipe)
 __device__ __forceinline__ bool finite_bits(double x) {
     return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
@@ -236,8 +257,8 @@ __device__ __forceinline__ double rate_term(const DevMech &m, int k, const doubl
 }
 
 __device__ __forceinline__ double gather_entry(const DevMech &m, int q, const double *rs) {
-    const int4 g = __ldg(m.fpack + q);
-    return __hiloint2double(g.y, g.x) * rs[g.z];
+    const int g = __ldg(m.fpk + q);
+    return __ldg(m.fcoef + hi16(g)) * rs[lo16(g)];
 }
 
 // y (own positions, registers) -> f (own positions).  The per-position sums
@@ -258,15 +279,16 @@ __device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, c
         double *fs = c.ys;  // y is no longer needed
         const int b0 = __ldg(m.flane_ptr + lane), b1 = __ldg(m.flane_ptr + lane + 1);
         for (int i = b0; i < b1; i++) {
-            const int4 job = __ldg(m.flane_job + i);
+            const int2 job = __ldg(m.fjob + i);
+            const int end = job.x + hi16(job.y);
             double acc = 0.0, acc2 = 0.0;
-            int q = job.y;
-            for (; q + 1 < job.z; q += 2) {
+            int q = job.x;
+            for (; q + 1 < end; q += 2) {
                 acc += gather_entry(m, q, c.rs);
                 acc2 += gather_entry(m, q + 1, c.rs);
             }
-            if (q < job.z) acc += gather_entry(m, q, c.rs);
-            fs[job.x] = acc + acc2;
+            if (q < end) acc += gather_entry(m, q, c.rs);
+            fs[lo16(job.y)] = acc + acc2;
         }
         __syncwarp(gm);
 #pragma unroll
@@ -768,10 +790,14 @@ __device__ __forceinline__ float ctl_powf(float x, float p) {
 }
 
 // 1/d for d > 0 to ~1e-14 relative: an FP32 estimate refined by one
-// Newton-Raphson step w <- w (2 - d w) in FP64.
+// Newton-Raphson step w <- w (2 - d w) in FP64; outside the FP32 normal
+// range a division
 __device__ __forceinline__ double recip_refined(double d) {
-    double w = (double)__frcp_rn((float)d);
-    return w * fma(-d, w, 2.0);
+    if (d > 1e-37 && d < 1e37) {
+        const double w = (double)__frcp_rn((float)d);
+        return w * fma(-d, w, 2.0);
+    }
+    return 1.0 / d;
 }
 
 struct CellStats {
@@ -932,7 +958,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                 LT dprev2 = (LT)0;
 #pragma unroll
                 for (int s = 0; s < NPL; s++) e[s] = 0.0;
-                const LT scale = (gamma != gamma_lu) ? (LT)2 / ((LT)1 + (LT)(gamma * rgamma_lu)) : (LT)1;
+                const LT scale = (gamma != gamma_lu) ? (LT)2 / ((LT)1 + to_lu<LT>(gamma * rgamma_lu)) : (LT)1;
                 for (int it = 0; it < NEWTON_MAXIT; it++) {
 #pragma unroll
                     for (int s = 0; s < NPL; s++) t1[s] = z[0][s] + e[s];
@@ -942,7 +968,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
 #pragma unroll
                     for (int s = 0; s < NPL; s++) {
                         int p = lane + G * s;
-                        if (p < n) c.x[p] = (LT)(-(e[s] - gamma * f[s] + z[1][s] * rl1));
+                        if (p < n) c.x[p] = to_lu<LT>(-(e[s] - gamma * f[s] + z[1][s] * rl1));
                     }
                     substitute<G, LT>(m, c, lane, gm);
                     // the update's norm in the LU precision (it only steers the iteration)
@@ -953,9 +979,8 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                         int p = lane + G * s;
                         LT xl = (p < n) ? c.x[p] : (LT)0;
                         xl *= scale;
-                        e[s] += (double)xl;
-                        LT a = xl * (LT)w[s];
-                        dsq += a * a;
+                        e[s] += from_lu(xl);
+                        dsq += upd_term(xl, w[s]);
                         nf |= !isfinite(xl);
                     }
                     const LT dn2 = gsum_t<G, LT>(dsq, gm) * (LT)m.rn;

@@ -64,10 +64,11 @@ struct DevMech {
     // rate term k: x = fwd0 | fwd1 << 16, y = fwd2 | rv << 16,
     //              z = rev0 | rev1 << 16, w = rev2  (16-bit fields, 0xffff = none)
     const int4 *rpack;    // [R]
-    // gather entry q: (x, y) = bits of the FP64 coefficient, z = process
-    const int4 *fpack;    // [nf]
-    // lane job i: x = position, y = first entry, z = end entry
-    const int4 *flane_job;// [n], lanes' jobs in flane_ptr ranges
+    // gather entry q: process | index into fcoef << 16
+    const int *fpk;       // [nf]
+    const double *fcoef;  // the mechanism's distinct net coefficients
+    // lane job i: x = first entry, y = position | entry count << 16
+    const int2 *fjob;     // [n], lanes' jobs in flane_ptr ranges
     // Jacobian non-zero t: x = first entry, y = end entry, z = LU offset, w = diagonal
     const int4 *jnz;      // [nnzJ]
     // Jacobian entry q: x = bits of the FP32 coefficient, y = constant index

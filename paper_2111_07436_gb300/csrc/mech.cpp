@@ -240,20 +240,34 @@ static void pack_records(HostMech &h) {
         o[2] = field16(f[3]) | (field16(f[4]) << 16);
         o[3] = field16(f[5]);
     }
-    h.fpack.assign(h.fk.size() * 4, 0);
-    for (size_t q = 0; q < h.fk.size(); q++) {
-        uint64_t bits;
-        std::memcpy(&bits, &h.fc[q], 8);
-        h.fpack[q * 4 + 0] = (int)(uint32_t)(bits & 0xffffffffu);
-        h.fpack[q * 4 + 1] = (int)(uint32_t)(bits >> 32);
-        h.fpack[q * 4 + 2] = h.fk[q];
+    // gather entries as 4 bytes each: process | index into the table of the
+    // mechanism's distinct coefficients << 16
+    h.fcoef.clear();
+    h.fpk.assign(h.fk.size(), 0);
+    {
+        std::unordered_map<uint64_t, int> seen;
+        for (size_t q = 0; q < h.fk.size(); q++) {
+            uint64_t bits;
+            std::memcpy(&bits, &h.fc[q], 8);
+            auto it = seen.find(bits);
+            int ci;
+            if (it == seen.end()) {
+                ci = (int)h.fcoef.size();
+                seen.emplace(bits, ci);
+                h.fcoef.push_back(h.fc[q]);
+            } else {
+                ci = it->second;
+            }
+            if (h.fk[q] > 0xffff || ci > 0xffff) throw std::runtime_error("forcing table does not fit 16-bit fields");
+            h.fpk[q] = h.fk[q] | (ci << 16);
+        }
     }
-    h.flane_job.assign((size_t)n * 4, 0);
+    // lane jobs: (first entry, position | entry count << 16)
+    h.fjob.assign((size_t)n * 2, 0);
     for (int i = 0; i < n; i++) {
         int p = h.flane_pos[i];
-        h.flane_job[(size_t)i * 4 + 0] = p;
-        h.flane_job[(size_t)i * 4 + 1] = h.fptr[p];
-        h.flane_job[(size_t)i * 4 + 2] = h.fptr[p + 1];
+        h.fjob[(size_t)i * 2 + 0] = h.fptr[p];
+        h.fjob[(size_t)i * 2 + 1] = p | ((h.fptr[p + 1] - h.fptr[p]) << 16);
     }
     const int nnzJ = (int)h.colidx.size();
     h.jnz.assign((size_t)nnzJ * 4, 0);
@@ -487,7 +501,7 @@ static void build_tables(HostMech &h) {
             for (int l = 1; l < 32; l++)
                 if (load[l] < load[best]) best = l;
             lanes[best].push_back(p);
-            load[best] += std::max(1, h.fptr[p + 1] - h.fptr[p]);
+            load[best] += h.fptr[p + 1] - h.fptr[p] + 2;  // entries plus the per-sum cost
         }
         h.flane_ptr.assign(1, 0);
         h.flane_pos.clear();
@@ -792,8 +806,9 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.udiag = pk.put(h.udiag);
     dm.perm = pk.put(h.perm);
     dm.rpack = reinterpret_cast<const int4 *>(pk.put(h.rpack));
-    dm.fpack = reinterpret_cast<const int4 *>(pk.put(h.fpack));
-    dm.flane_job = reinterpret_cast<const int4 *>(pk.put(h.flane_job));
+    dm.fpk = pk.put(h.fpk);
+    dm.fcoef = pk.put(h.fcoef);
+    dm.fjob = reinterpret_cast<const int2 *>(pk.put(h.fjob));
     dm.jnz = reinterpret_cast<const int4 *>(pk.put(h.jnz));
     dm.jpack = reinterpret_cast<const int4 *>(pk.put(h.jpack));
     dm.sl_pack = pk.put(h.sl_pack);

@@ -40,7 +40,9 @@ struct HostMech {
     std::vector<int> fptr, fk;
     std::vector<double> fc;
     std::vector<int> flane_ptr, flane_pos;
-    std::vector<int> rpack, fpack, flane_job, jnz, jpack, sl_pack, su_pack;  // int4 records as 4 ints
+    std::vector<int> rpack, jnz, jpack, sl_pack, su_pack;  // int4 records as 4 ints
+    std::vector<int> fpk, fjob;   // forcing gather entries and lane jobs (see DevMech)
+    std::vector<double> fcoef;
     std::vector<int> jl_ptr, jl_rec;
     std::vector<int> jptr, jdst, jdiag, jk, jo;
     std::vector<double> jc;

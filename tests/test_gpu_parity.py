@@ -181,3 +181,21 @@ def test_every_process_type(form):
     parity.check(om, y0, env, 180.0, 1e-4, 1e-5, yg, yo)
     n_gas = len(mj["species"])
     assert (yo[:, n_gas:] > 0).any()  # the condensed phase takes part
+
+
+@pytest.mark.parametrize("variant", [camp.VARIANT_FP64, camp.VARIANT_MIXED])
+def test_atol_below_the_fp32_range(cuda, variant):
+    """An error weight 1/(rtol |y| + atol) beyond FP32's range (atol 1e-40 on
+    a species that starts at zero) must come out as in the oracle."""
+    from tests import mechs as M
+    text = M.mech(["E", "L", "A", "B"], [M.emission("E", 0.3), M.loss("L", 2e-3),
+                                         M.arrhenius({"A": 1, "B": 1}, {"E": 1.0}, A=1e-12)])
+    gm, om = camp.Mechanism(text), oracle.Mechanism(text)
+    env = np.zeros((3, om.n_env))
+    env[:, 0], env[:, 1], env[:, 2], env[:, 3] = 298.0, 1e5, 0.3, 2e-3
+    y0 = np.array([[0.0, 4.0, 1.0, 2.0], [0.0, 1.0, 0.0, 0.0], [1e-3, 0.0, 5.0, 5.0]])
+    atol = np.array([1e-40, 1e-5, 1e-5, 1e-5])
+    yg, st = _gpu_solve(gm, y0, env, 600.0, 1e-4, atol, variant, False)
+    yo, sto, _ = om.solve(y0, env, 600.0, 1e-4, atol)
+    assert (st == 0).all() and (sto == 0).all()
+    parity.check(om, y0, env, 600.0, 1e-4, atol, yg, yo)
