@@ -52,7 +52,16 @@ __host__ __device__ inline CellSmem cell_smem(int n, int R, int n_rev, int nlu, 
     c.rs = o; o = align16(o + 8 * R);
     c.kf = o; o = align16(o + 8 * R);
     c.kr = o; o = align16(o + 8 * n_rev);
-    c.x = o;  o = align16(o + lu_elem * n);
+    // the substitution vector shares the rate-term scratch when it fits:
+    // the rate terms live only inside one f evaluation, the vector only
+    // inside one Newton solve, and the Jacobian assembly keeps its FP32
+    // copy of y in ys instead
+    if (8 * R >= lu_elem * n) {
+        c.x = c.rs;
+    } else {
+        c.x = o;
+        o = align16(o + lu_elem * n);
+    }
     c.lu = o; o = align16(o + lu_elem * nlu);
     c.bytes = o;
     return c;
@@ -261,18 +270,13 @@ __device__ __forceinline__ double gather_entry(const DevMech &m, int q, const do
     return __ldg(m.fcoef + hi16(g)) * rs[lo16(g)];
 }
 
-// y (own positions, registers) -> f (own positions).  The per-position sums
-// are spread over the lanes by the compiler's balanced assignment (32-lane
-// groups) and handed back through shared memory (reusing ys).
+// y in c.ys (written by the caller, who also made it visible to the group)
+// -> f (own positions).  The per-position sums are spread over the lanes by
+// the compiler's balanced assignment (32-lane groups) and handed back
+// through shared memory (reusing ys).
 template <int G, int NPL, typename LT>
-__device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, const double (&y)[NPL],
-                                       double (&f)[NPL], int lane, unsigned gm) {
-#pragma unroll
-    for (int s = 0; s < NPL; s++) {
-        int p = lane + G * s;
-        if (p < m.n) c.ys[p] = y[s];
-    }
-    __syncwarp(gm);
+__device__ __forceinline__ void eval_f_ys(const DevMech &m, const CellPtr<LT> &c, double (&f)[NPL],
+                                          int lane, unsigned gm) {
     for (int k = lane; k < m.R; k += G) c.rs[k] = rate_term(m, k, c.ys, c.kf[k], c.kr);
     __syncwarp(gm);
     if (G == 32) {
@@ -311,6 +315,33 @@ __device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, c
     }
 }
 
+// y (own positions, registers) -> f (own positions)
+template <int G, int NPL, typename LT>
+__device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, const double (&y)[NPL],
+                                       double (&f)[NPL], int lane, unsigned gm) {
+#pragma unroll
+    for (int s = 0; s < NPL; s++) {
+        int p = lane + G * s;
+        if (p < m.n) c.ys[p] = y[s];
+    }
+    __syncwarp(gm);
+    eval_f_ys<G, NPL, LT>(m, c, f, lane, gm);
+}
+
+// f at y = a + b u (own positions), without a register copy of y
+template <int G, int NPL, typename LT>
+__device__ __forceinline__ void eval_f_at(const DevMech &m, const CellPtr<LT> &c, const double (&a)[NPL],
+                                          double b, const double (&u)[NPL], double (&f)[NPL], int lane,
+                                          unsigned gm) {
+#pragma unroll
+    for (int s = 0; s < NPL; s++) {
+        int p = lane + G * s;
+        if (p < m.n) c.ys[p] = a[s] + b * u[s];
+    }
+    __syncwarp(gm);
+    eval_f_ys<G, NPL, LT>(m, c, f, lane, gm);
+}
+
 // ---- Jacobian gather: J (or M = I - gamma J) at ys into LU storage -----------
 // mode 0: write M = I - gamma J into c.lu (zeroing fill and block entries)
 // mode 1: write J values to out[nnzJ] (species-CSR order)
@@ -322,10 +353,18 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
                                          int lane, unsigned gm, int mode, double *out) {
     const LT *kfv, *krv, *yv;
     if constexpr (sizeof(LT) == 4) {
-        LT *kf32 = (LT *)c.rs, *kr32 = kf32 + m.R, *y32 = c.x;
+        LT *kf32 = (LT *)c.rs, *kr32 = kf32 + m.R, *y32 = (LT *)c.ys;
         for (int k = lane; k < m.R; k += G) kf32[k] = (LT)c.kf[k];
         for (int k = lane; k < m.n_rev; k += G) kr32[k] = (LT)c.kr[k];
-        for (int p = lane; p < m.n; p += G) y32[p] = (LT)c.ys[p];
+        // y to FP32 in place, G positions at a time: a chunk's FP32 values
+        // overwrite only FP64 values of this or earlier chunks, and the
+        // group reads its chunk before any lane writes it
+        for (int b0 = 0; b0 < m.n; b0 += G) {
+            const int p = b0 + lane;
+            const double v = p < m.n ? c.ys[p] : 0.0;
+            __syncwarp(gm);
+            if (p < m.n) y32[p] = (LT)v;
+        }
         kfv = kf32;
         krv = kr32;
         yv = y32;
@@ -822,22 +861,16 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
     // inputs must be finite
     bool bad = false;
     for (int i = lane; i < m.n_env; i += G) bad |= !finite_bits(env_cell[i]);
-    double z[QMAX + 1][NPL], e[NPL], ep[NPL], w[NPL], f[NPL], t1[NPL];
-    double atl[NPL];
+    double z[QMAX + 1][NPL], e[NPL], ep[NPL], w[NPL], f[NPL];
 #pragma unroll
     for (int s = 0; s < NPL; s++) {
         int p = lane + G * s;
-        double v = 0.0, a = 1.0;
-        if (p < n) {
-            int sp = __ldg(m.perm + p);
-            v = y_cell[sp];
-            a = atol[atol_len == 1 ? 0 : sp];
-        }
+        double v = 0.0;
+        if (p < n) v = y_cell[__ldg(m.perm + p)];
         bad |= !finite_bits(v);
 #pragma unroll
         for (int j = 0; j <= QMAX; j++) z[j][s] = 0.0;
         z[0][s] = v;
-        atl[s] = a;
         e[s] = ep[s] = 0.0;
     }
     // a cell that fails hands back no step (the next call starts cold)
@@ -856,11 +889,14 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
     }
     __syncwarp(gm);
 
+    // atol is re-read (an L1 hit) rather than held in registers
     auto set_weights = [&]() {
 #pragma unroll
         for (int s = 0; s < NPL; s++) {
             int p = lane + G * s;
-            w[s] = (p < n) ? recip_refined(fma(rtol, fabs(z[0][s]), atl[s])) : 0.0;
+            double a = 1.0;
+            if (p < n) a = atol_len == 1 ? __ldg(atol) : __ldg(atol + __ldg(m.perm + p));
+            w[s] = (p < n) ? recip_refined(fma(rtol, fabs(z[0][s]), a)) : 0.0;
         }
     };
     auto any_nonfinite = [&](const double(&v)[NPL]) {
@@ -884,12 +920,10 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
         double d0 = wrms<G, NPL>(m, z[0], w, gm), d1 = wrms<G, NPL>(m, f, w, gm);
         double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
         if (h0 > T) h0 = T;
+        eval_f_at<G, NPL, LT>(m, c, z[0], h0, f, e, lane, gm);
 #pragma unroll
-        for (int s = 0; s < NPL; s++) t1[s] = z[0][s] + h0 * f[s];
-        eval_f<G, NPL, LT>(m, c, t1, e, lane, gm);
-#pragma unroll
-        for (int s = 0; s < NPL; s++) t1[s] = e[s] - f[s];
-        double d2 = wrms<G, NPL>(m, t1, w, gm) / h0;
+        for (int s = 0; s < NPL; s++) ep[s] = e[s] - f[s];  // ep is free until the first step ends
+        double d2 = wrms<G, NPL>(m, ep, w, gm) / h0;
         double dm = d1 > d2 ? d1 : d2;
         double h1 = (dm <= 1e-15) ? fmax(1e-6, h0 * 1e-3) : sqrt(0.01 / dm);
         h = fmin(100.0 * h0, h1);
@@ -960,9 +994,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                 for (int s = 0; s < NPL; s++) e[s] = 0.0;
                 const LT scale = (gamma != gamma_lu) ? (LT)2 / ((LT)1 + to_lu<LT>(gamma * rgamma_lu)) : (LT)1;
                 for (int it = 0; it < NEWTON_MAXIT; it++) {
-#pragma unroll
-                    for (int s = 0; s < NPL; s++) t1[s] = z[0][s] + e[s];
-                    eval_f<G, NPL, LT>(m, c, t1, f, lane, gm);
+                    eval_f_at<G, NPL, LT>(m, c, z[0], 1.0, e, f, lane, gm);
                     st.newton++;
                     if (any_nonfinite(f)) break;
 #pragma unroll

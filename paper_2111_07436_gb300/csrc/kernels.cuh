@@ -20,8 +20,11 @@ __device__ __forceinline__ unsigned group_mask() {
 // The whole solve: each group of G lanes integrates one cell at a time.  With
 // `queue` null the mapping is static (cell = block * cpb + group); otherwise
 // the groups take cells from the counter until it passes n_cells.
+// Register caps: the FP32-LU form is limited by registers and shared memory
+// together (168 a lane fits 12 one-warp cells per SM; 224 fits 9), the FP64
+// form by shared memory alone, so it may take the architectural maximum.
 template <int G, int NPL, typename LT>
-__global__ void __maxnreg__(NPL >= 6 ? 232 : 168) k_solve(DevMech m, SolveArgs a) {
+__global__ void __maxnreg__(sizeof(LT) == 8 ? 255 : (NPL >= 6 ? 224 : 168)) k_solve(DevMech m, SolveArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int group = threadIdx.x / G, lane = threadIdx.x % G;
     const unsigned gm = group_mask<G>();

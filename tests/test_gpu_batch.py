@@ -108,3 +108,55 @@ def test_autotune_picks_a_valid_launch(groups):
     g["mech"].solve(tb, e, 180.0, 1e-4, 1e-5, persistent=True, cells_per_block=1)
     torch.cuda.synchronize()
     assert torch.equal(ta, tb)
+
+
+def test_full_size_uneven_batch_sampled(cuda):
+    """The uneven-stiffness workload at its full size (131072 cells, the
+    benchmark's seeds) in the launch configuration the benchmark times:
+    autotuned, both mechanisms in one camp_solve_batch call captured in a
+    CUDA graph; then the plain FP64 form, one static launch per mechanism.
+    A seeded sample of each group is re-solved by the oracle."""
+    import torch
+    gs, _ = w.uneven_batch(131072)
+    G = []
+    for mj, y, env in gs:
+        G.append({"mj": mj, "mech": camp.Mechanism(json.dumps(mj)), "y0": y, "env_np": env,
+                  "y0_d": torch.tensor(y, device=cuda), "env": torch.tensor(env, device=cuda),
+                  "state": torch.empty(y.shape, dtype=torch.float64, device=cuda),
+                  "status": torch.empty(len(y), dtype=torch.int32, device=cuda),
+                  "atol": torch.full((1,), 1e-5, dtype=torch.float64, device=cuda),
+                  "workspace": camp.workspace(cuda)})
+    for g in G:
+        k = min(4096, len(g["y0"]))
+        g["mech"].autotune(g["y0_d"][:k].contiguous(), g["env"][:k].contiguous(), 180.0, 1e-4, g["atol"])
+    side = torch.cuda.Stream()
+
+    def step():
+        for g in G:
+            g["state"].copy_(g["y0_d"])
+        camp.solve_batch([{k: g[k] for k in ("mech", "state", "env", "atol", "status", "workspace")}
+                          for g in G], 180.0, 1e-4, stream=side)
+
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        step()
+    graph.replay()
+    torch.cuda.synchronize()
+    mixed = [(g["state"].cpu().numpy(), g["status"].cpu().numpy()) for g in G]
+    for g in G:
+        g["state"].copy_(g["y0_d"])
+        g["mech"].solve(g["state"], g["env"], 180.0, 1e-4, g["atol"], status=g["status"],
+                        variant=camp.VARIANT_FP64, persistent=False)
+    torch.cuda.synchronize()
+    plain = [(g["state"].cpu().numpy(), g["status"].cpu().numpy()) for g in G]
+    for gi, g in enumerate(G):
+        assert (mixed[gi][1] == 0).all() and (plain[gi][1] == 0).all()
+        idx = np.sort(np.random.default_rng(7 + gi).choice(len(g["y0"]), 20, replace=False))
+        om = oracle.Mechanism(json.dumps(g["mj"]))
+        yo, so, _ = om.solve(g["y0"][idx], g["env_np"][idx], 180.0, 1e-4, 1e-5)
+        assert (so == 0).all()
+        for y_gpu, _ in (mixed[gi], plain[gi]):
+            parity.check(om, g["y0"][idx], g["env_np"][idx], 180.0, 1e-4, 1e-5, y_gpu[idx], yo)
