@@ -99,7 +99,13 @@ typedef struct {
  * Process types (Table 2): ARRHENIUS, TROE, PHOTOLYSIS, EMISSION,
  * FIRST_ORDER_LOSS, CUSTOM_H2O2, CUSTOM_OH_HNO3 (gas phase);
  * HL_PHASE_TRANSFER, SIMPOL_PHASE_TRANSFER, AQUEOUS_REVERSIBLE,
- * CONDENSED_ARRHENIUS (one instance per aerosol section).
+ * CONDENSED_ARRHENIUS (one instance per aerosol section, or per
+ * computational particle in the particle-resolved representation,
+ * SingleParticle of Sect. 2.2.3, Table 6).
+ * Limits: at most 2048 species (up to 256 a cell runs on one warp, beyond
+ * that on a block of 64, 128 or 256 threads), 32767 stored LU values, and a
+ * per-cell working set that fits one SM's shared memory; larger mechanisms
+ * return CAMP_E_UNSUPPORTED or CAMP_E_PARSE with the reason.
  */
 int camp_mech_load(const char *json, size_t len, camp_mech **out, char *err, size_t errlen);
 

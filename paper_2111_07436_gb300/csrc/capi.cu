@@ -45,7 +45,9 @@ int fail(int code, const std::string &msg) {
             return fail(CAMP_E_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-const int kMaxSmem = 227 * 1024;
+// dynamic shared memory one block may use (227 KB less room for a block
+// group's static reduction scratch)
+const int kMaxSmem = 227 * 1024 - 256;
 
 int check_device(const camp_mech *m) {
     if (!m->on_device) return fail(CAMP_E_INVAL, "mechanism was compiled without device tables");
@@ -56,26 +58,33 @@ int check_device(const camp_mech *m) {
     return CAMP_OK;
 }
 
-template <int NPL>
+template <int G, int NPL>
 cudaError_t forcing_npl(const DevMech &m, long long n_cells, const double *state, const double *env,
                         double *f, cudaStream_t s) {
-    auto kern = campdev::k_forcing<32, NPL, double>;
+    auto kern = campdev::k_forcing<G, NPL, double>;
     int smem = camp_cell_smem_bytes(m, 8);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)n_cells, 32, smem, s>>>(m, n_cells, state, env, f);
+    kern<<<(unsigned)n_cells, G, smem, s>>>(m, n_cells, state, env, f);
     return cudaGetLastError();
 }
 }  // namespace
 
 int camp_record_error(int code, const char *msg) { return fail(code, msg); }
 
-int camp_pick_npl(int n) {
+int camp_pick_shape(int n) {
     const int need = (n + 31) / 32;
     const int avail[] = {1, 2, 3, 4, 6, 8};
     for (int a : avail)
         if (a >= need) return a;
+    for (int warps = 2; warps <= 8; warps *= 2)  // blocks of 64, 128, 256 threads, 8 slots a lane
+        if (n <= 8 * 32 * warps) return CAMP_SHAPE_BLOCK + warps;
     return -1;
+}
+
+int camp_group_size(int n) {
+    const int sh = camp_pick_shape(n);
+    return sh > CAMP_SHAPE_BLOCK ? 32 * (sh - CAMP_SHAPE_BLOCK) : 32;
 }
 
 int camp_cell_smem_bytes(const DevMech &m, int lu_elem) {
@@ -91,13 +100,16 @@ cudaError_t camp_launch_rates(const DevMech &m, long long n_cells, const double 
 
 cudaError_t camp_launch_forcing(const DevMech &m, long long n_cells, const double *state,
                                 const double *env, double *f, cudaStream_t s) {
-    switch (camp_pick_npl(m.n)) {
-    case 1: return forcing_npl<1>(m, n_cells, state, env, f, s);
-    case 2: return forcing_npl<2>(m, n_cells, state, env, f, s);
-    case 3: return forcing_npl<3>(m, n_cells, state, env, f, s);
-    case 4: return forcing_npl<4>(m, n_cells, state, env, f, s);
-    case 6: return forcing_npl<6>(m, n_cells, state, env, f, s);
-    case 8: return forcing_npl<8>(m, n_cells, state, env, f, s);
+    switch (camp_pick_shape(m.n)) {
+    case 1: return forcing_npl<32, 1>(m, n_cells, state, env, f, s);
+    case 2: return forcing_npl<32, 2>(m, n_cells, state, env, f, s);
+    case 3: return forcing_npl<32, 3>(m, n_cells, state, env, f, s);
+    case 4: return forcing_npl<32, 4>(m, n_cells, state, env, f, s);
+    case 6: return forcing_npl<32, 6>(m, n_cells, state, env, f, s);
+    case 8: return forcing_npl<32, 8>(m, n_cells, state, env, f, s);
+    case CAMP_SHAPE_BLOCK + 2: return forcing_npl<64, 8>(m, n_cells, state, env, f, s);
+    case CAMP_SHAPE_BLOCK + 4: return forcing_npl<128, 8>(m, n_cells, state, env, f, s);
+    case CAMP_SHAPE_BLOCK + 8: return forcing_npl<256, 8>(m, n_cells, state, env, f, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -126,13 +138,13 @@ static int mech_build(const char *json, size_t len, camp_mech **out, char *err, 
         delete m;
         return report(CAMP_E_PARSE, e.what());
     }
-    if (camp_pick_npl(m->h.n) < 0) {
+    if (camp_pick_shape(m->h.n) < 0) {
         delete m;
-        return report(CAMP_E_UNSUPPORTED, "more than 256 species");
+        return report(CAMP_E_UNSUPPORTED, "more than 2048 species");
     }
     DevMech probe{};
     std::vector<unsigned char> img = camp::pack_tables(m->h, probe, nullptr);
-    if (camp_cell_smem_bytes(probe, 8) > kMaxSmem) {
+    if (camp_cell_smem_bytes(probe, 4) > kMaxSmem) {
         delete m;
         return report(CAMP_E_UNSUPPORTED, "per-cell working set exceeds shared memory");
     }
@@ -285,7 +297,8 @@ int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double
     if (cpb <= 0) {  // most resident cells per SM, fewest cells per block on ties
         int best = 0;
         cpb = 1;
-        for (int c2 = 1; c2 <= 4; c2++) {
+        const int max_cpb = camp_group_size(m->h.n) > 32 ? 1 : 4;
+        for (int c2 = 1; c2 <= max_cpb; c2++) {
             if (c2 * smem_cell > kMaxSmem) break;
             int per_sm = 0;
             CUDA_TRY(occupancy(c2, &per_sm));
@@ -294,6 +307,9 @@ int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double
     }
     cpb = std::min(cpb, 4);
     while (cpb > 1 && cpb * smem_cell > kMaxSmem) cpb--;
+    if (camp_group_size(m->h.n) > 32) cpb = 1;  // one cell per block of threads
+    if (smem_cell > kMaxSmem)
+        return fail(CAMP_E_UNSUPPORTED, "one cell of this form needs more shared memory than a block may have");
 
     SolveArgs a;
     a.n_cells = n_cells;
@@ -461,6 +477,7 @@ int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const doub
         for (int ci = 0; ci < 4 && rc == CAMP_OK; ci++) {
             const int smem_cell = camp_cell_smem_bytes(m->dm, variant == CAMP_VARIANT_MIXED ? 4 : 8);
             if (cpbs[ci] * smem_cell > kMaxSmem) continue;
+            if (cpbs[ci] > 1 && camp_group_size(m->h.n) > 32) continue;  // a block is one cell
             camp_solve_opts o;
             camp_solve_opts_default(&o, variant);
             o.persistent = pers;

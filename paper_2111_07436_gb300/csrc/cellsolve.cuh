@@ -83,11 +83,40 @@ struct CellPtr {
 };
 
 // ---- group primitives --------------------------------------------------------
+// A cell is integrated by a group of G lanes: G = 32 lanes of one warp, or a
+// whole block of G > 32 threads (one cell per block, for mechanisms too large
+// for one warp's registers).  Control flow is uniform across a group, so
+// these are safe wherever the group takes them together.
+template <int G>
+__device__ __forceinline__ void gsync(unsigned gm) {
+    if constexpr (G <= 32) __syncwarp(gm);
+    else __syncthreads();
+}
+template <int G>
+__device__ __forceinline__ bool gany(bool v, unsigned gm) {
+    if constexpr (G <= 32) return __any_sync(gm, v) != 0;
+    else return __syncthreads_or(v) != 0;
+}
+// Sum over the group, the same value in every lane (for a block: a fixed
+// order over its warps' partial sums, so every thread gets identical bits)
 template <int G, typename T>
 __device__ __forceinline__ T gsum_t(T v, unsigned gm) {
+    if constexpr (G <= 32) {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gm, v, o, G);
-    return __shfl_sync(gm, v, 0, G);
+        for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gm, v, o, G);
+        return __shfl_sync(gm, v, 0, G);
+    } else {
+        __shared__ double part[G / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        __syncthreads();  // the previous sum's reads are done
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = (double)v;
+        __syncthreads();
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < G / 32; i++) t += part[i];
+        return (T)t;
+    }
 }
 template <int G>
 __device__ __forceinline__ double gsum(double v, unsigned gm) {
@@ -278,7 +307,7 @@ template <int G, int NPL, typename LT>
 __device__ __forceinline__ void eval_f_ys(const DevMech &m, const CellPtr<LT> &c, double (&f)[NPL],
                                           int lane, unsigned gm) {
     for (int k = lane; k < m.R; k += G) c.rs[k] = rate_term(m, k, c.ys, c.kf[k], c.kr);
-    __syncwarp(gm);
+    gsync<G>(gm);
     if (G == 32) {
         double *fs = c.ys;  // y is no longer needed
         const int b0 = __ldg(m.flane_ptr + lane), b1 = __ldg(m.flane_ptr + lane + 1);
@@ -294,13 +323,13 @@ __device__ __forceinline__ void eval_f_ys(const DevMech &m, const CellPtr<LT> &c
             if (q < end) acc += gather_entry(m, q, c.rs);
             fs[lo16(job.y)] = acc + acc2;
         }
-        __syncwarp(gm);
+        gsync<G>(gm);
 #pragma unroll
         for (int s = 0; s < NPL; s++) {
             int p = lane + G * s;
             f[s] = (p < m.n) ? fs[p] : 0.0;
         }
-        __syncwarp(gm);
+        gsync<G>(gm);
     } else {
 #pragma unroll
         for (int s = 0; s < NPL; s++) {
@@ -312,6 +341,7 @@ __device__ __forceinline__ void eval_f_ys(const DevMech &m, const CellPtr<LT> &c
             }
             f[s] = acc;
         }
+        gsync<G>(gm);  // the rate terms are read before anyone reuses their scratch
     }
 }
 
@@ -324,7 +354,7 @@ __device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, c
         int p = lane + G * s;
         if (p < m.n) c.ys[p] = y[s];
     }
-    __syncwarp(gm);
+    gsync<G>(gm);
     eval_f_ys<G, NPL, LT>(m, c, f, lane, gm);
 }
 
@@ -338,7 +368,7 @@ __device__ __forceinline__ void eval_f_at(const DevMech &m, const CellPtr<LT> &c
         int p = lane + G * s;
         if (p < m.n) c.ys[p] = a[s] + b * u[s];
     }
-    __syncwarp(gm);
+    gsync<G>(gm);
     eval_f_ys<G, NPL, LT>(m, c, f, lane, gm);
 }
 
@@ -362,7 +392,7 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
         for (int b0 = 0; b0 < m.n; b0 += G) {
             const int p = b0 + lane;
             const double v = p < m.n ? c.ys[p] : 0.0;
-            __syncwarp(gm);
+            gsync<G>(gm);
             if (p < m.n) y32[p] = (LT)v;
         }
         kfv = kf32;
@@ -381,7 +411,7 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
         for (int i = lane; i < nv; i += G) z4[i] = zero;
         for (int i = nv * V + lane; i < m.nlu; i += G) c.lu[i] = (LT)0;
     }
-    __syncwarp(gm);
+    gsync<G>(gm);
     const LT g = (LT)gamma;
     if constexpr (sizeof(LT) == 4) {
         if (G == 32) {
@@ -405,7 +435,7 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
                     acc = (LT)0;
                 }
             }
-            __syncwarp(gm);
+            gsync<G>(gm);
             return;
         }
     }
@@ -436,7 +466,7 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
         else
             out[t] = (double)acc;
     }
-    __syncwarp(gm);
+    gsync<G>(gm);
 }
 
 template <typename LT> __device__ __forceinline__ LT tiny_pivot();
@@ -600,17 +630,21 @@ __device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigne
                 lu[di] = recip(u);
             }
         }
-        __syncwarp(gm);
+        gsync<G>(gm);
     }
+    // the dense block is one warp's work (a block group's first warp)
     LT *A = lu + m.dbase;
-    switch ((m.D + 31) >> 5) {
-    case 0: break;
-    case 1: bad |= dense_factor<1, DENSE_W, LT>(A, m.D, m.LD, lane, gm); break;
-    case 2: bad |= dense_factor<2, DENSE_W, LT>(A, m.D, m.LD, lane, gm); break;
-    case 3: bad |= dense_factor<3, DENSE_W, LT>(A, m.D, m.LD, lane, gm); break;
-    default: bad |= dense_factor<4, DENSE_W, LT>(A, m.D, m.LD, lane, gm); break;
+    if (G <= 32 || lane < 32) {
+        const unsigned wm = G <= 32 ? gm : 0xffffffffu;
+        switch ((m.D + 31) >> 5) {
+        case 0: break;
+        case 1: bad |= dense_factor<1, DENSE_W, LT>(A, m.D, m.LD, lane, wm); break;
+        case 2: bad |= dense_factor<2, DENSE_W, LT>(A, m.D, m.LD, lane, wm); break;
+        case 3: bad |= dense_factor<3, DENSE_W, LT>(A, m.D, m.LD, lane, wm); break;
+        default: bad |= dense_factor<4, DENSE_W, LT>(A, m.D, m.LD, lane, wm); break;
+        }
     }
-    return !__any_sync(gm, bad);
+    return !gany<G>(bad, gm);
 }
 
 // ---- substitution: solves (LU) x = x in place (c.x holds the right side) -----
@@ -710,7 +744,7 @@ template <int G, typename LT>
 __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, unsigned gm) {
     LT *x = c.x;
     const LT *lu = c.lu;
-    __syncwarp(gm);
+    gsync<G>(gm);
     // forward, sparse rows and the L21 part of block rows (rows without L
     // entries keep their value)
     for (int L = 0; L < m.n_slev; L++) {
@@ -731,17 +765,20 @@ __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, uns
             }
             x[i] = s - s2;
         }
-        __syncwarp(gm);
+        gsync<G>(gm);
     }
     const LT *A = lu + m.dbase;
-    switch ((m.D + 31) >> 5) {
-    case 0: break;
-    case 1: dense_subst<1, LT>(A, m.D, m.LD, x + m.d, lane, gm); break;
-    case 2: dense_subst<2, LT>(A, m.D, m.LD, x + m.d, lane, gm); break;
-    case 3: dense_subst<3, LT>(A, m.D, m.LD, x + m.d, lane, gm); break;
-    default: dense_subst<4, LT>(A, m.D, m.LD, x + m.d, lane, gm); break;
+    if (G <= 32 || lane < 32) {
+        const unsigned wm = G <= 32 ? gm : 0xffffffffu;
+        switch ((m.D + 31) >> 5) {
+        case 0: break;
+        case 1: dense_subst<1, LT>(A, m.D, m.LD, x + m.d, lane, wm); break;
+        case 2: dense_subst<2, LT>(A, m.D, m.LD, x + m.d, lane, wm); break;
+        case 3: dense_subst<3, LT>(A, m.D, m.LD, x + m.d, lane, wm); break;
+        default: dense_subst<4, LT>(A, m.D, m.LD, x + m.d, lane, wm); break;
+        }
     }
-    __syncwarp(gm);
+    gsync<G>(gm);
     // backward, sparse rows by level
     for (int L = 0; L < m.n_blev; L++) {
         int b = __ldg(m.blev_ptr + L), e = __ldg(m.blev_ptr + L + 1);
@@ -761,7 +798,7 @@ __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, uns
             }
             x[i] = (s - s2) * lu[__ldg(m.udiag + i)];
         }
-        __syncwarp(gm);
+        gsync<G>(gm);
     }
 }
 
@@ -878,7 +915,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
         if (step_io && lane == 0) *step_io = 0.0;
         return code;
     };
-    if (__any_sync(gm, bad)) return fail_early(ST_NONFINITE);
+    if (gany<G>(bad, gm)) return fail_early(ST_NONFINITE);
 
     for (int k = lane; k < m.R; k += G) {
         double a, b;
@@ -887,7 +924,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
         const int rv = __ldg(m.rrev + k);
         if (rv >= 0) c.kr[rv] = b;
     }
-    __syncwarp(gm);
+    gsync<G>(gm);
 
     // atol is re-read (an L1 hit) rather than held in registers
     auto set_weights = [&]() {
@@ -903,7 +940,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
         bool b2 = false;
 #pragma unroll
         for (int s = 0; s < NPL; s++) b2 |= !finite_bits(v[s]);
-        return __any_sync(gm, b2) != 0;
+        return gany<G>(b2, gm) != 0;
     };
 
     const double T = dt, hmin = hmin_frac * dt;
@@ -975,7 +1012,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                     int p = lane + G * s;
                     if (p < n) c.ys[p] = z[0][s];
                 }
-                __syncwarp(gm);
+                gsync<G>(gm);
                 assemble<G, LT>(m, c, gamma, lane, gm, 0, nullptr);
                 lu_fail = !factor<G, LT>(m, c, lane, gm);
                 st.jac++;
@@ -1016,7 +1053,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                         nf |= !isfinite(xl);
                     }
                     const LT dn2 = gsum_t<G, LT>(dsq, gm) * (LT)m.rn;
-                    if (__any_sync(gm, nf) || !isfinite(dn2)) break;
+                    if (gany<G>(nf, gm) || !isfinite(dn2)) break;
                     LT test2 = dn2;
                     if (it > 0) {
                         const LT rho2 = dn2 / dprev2;

@@ -9,7 +9,7 @@ namespace campdev {
 
 template <int G>
 __device__ __forceinline__ unsigned group_mask() {
-    if constexpr (G == 32) {
+    if constexpr (G >= 32) {
         return 0xffffffffu;
     } else {
         const int sub = (threadIdx.x & 31) / G;
@@ -20,11 +20,13 @@ __device__ __forceinline__ unsigned group_mask() {
 // The whole solve: each group of G lanes integrates one cell at a time.  With
 // `queue` null the mapping is static (cell = block * cpb + group); otherwise
 // the groups take cells from the counter until it passes n_cells.
-// Register caps: the FP32-LU form is limited by registers and shared memory
-// together (168 a lane fits 12 one-warp cells per SM; 224 fits 9), the FP64
-// form by shared memory alone, so it may take the architectural maximum.
+// Register caps: the FP32-LU form with one-warp cells is limited by
+// registers and shared memory together (168 a lane fits 12 cells per SM;
+// 224 fits 9); the FP64 form and block cells may take the architectural
+// maximum.
 template <int G, int NPL, typename LT>
-__global__ void __maxnreg__(sizeof(LT) == 8 ? 255 : (NPL >= 6 ? 224 : 168)) k_solve(DevMech m, SolveArgs a) {
+__global__ void __maxnreg__((sizeof(LT) == 8 || G > 32) ? 255 : (NPL >= 6 ? 224 : 168))
+    k_solve(DevMech m, SolveArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int group = threadIdx.x / G, lane = threadIdx.x % G;
     const unsigned gm = group_mask<G>();
@@ -33,9 +35,17 @@ __global__ void __maxnreg__(sizeof(LT) == 8 ? 255 : (NPL >= 6 ? 224 : 168)) k_so
     long long cell = a.queue ? 0 : (long long)blockIdx.x * a.cpb + group;
     for (;;) {
         if (a.queue) {
-            unsigned long long v = 0;
-            if (lane == 0) v = atomicAdd(a.queue, 1ull);
-            cell = (long long)__shfl_sync(gm, v, 0, G);
+            if constexpr (G <= 32) {
+                unsigned long long v = 0;
+                if (lane == 0) v = atomicAdd(a.queue, 1ull);
+                cell = (long long)__shfl_sync(gm, v, 0, G);
+            } else {  // one cell per block: broadcast through shared memory
+                __shared__ unsigned long long next;
+                if (threadIdx.x == 0) next = atomicAdd(a.queue, 1ull);
+                __syncthreads();
+                cell = (long long)next;
+                __syncthreads();
+            }
         }
         if (cell >= a.n_cells) break;
         CellStats st;
@@ -54,7 +64,7 @@ __global__ void __maxnreg__(sizeof(LT) == 8 ? 255 : (NPL >= 6 ? 224 : 168)) k_so
             }
         }
         if (!a.queue) break;
-        __syncwarp(gm);
+        gsync<G>(gm);
     }
 }
 
@@ -88,7 +98,7 @@ __device__ __forceinline__ void load_cell(const DevMech &m, const CellPtr<LT> &c
         yr[s] = p < m.n ? y[__ldg(m.perm + p)] : 0.0;
         if (p < m.n) c.ys[p] = yr[s];
     }
-    __syncwarp(gm);
+    gsync<G>(gm);
 }
 
 // f(y) of every cell, [cell][n] in declaration order.

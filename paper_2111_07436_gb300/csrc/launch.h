@@ -22,9 +22,15 @@ struct SolveArgs {
     unsigned long long *queue;      // work counter (persistent form) or null
 };
 
-// Register slots per lane instantiated for G = 32: a mechanism with n species
-// uses the smallest entry >= ceil(n / 32); n <= 256.
-int camp_pick_npl(int n);
+// Cell shapes instantiated: one warp per cell (G = 32 lanes) with NPL
+// register slots per lane, NPL in {1, 2, 3, 4, 6, 8} (n <= 256); or one
+// block of G = 64, 128 or 256 threads per cell with 8 slots per lane
+// (n <= 8 G), coded as CAMP_SHAPE_BLOCK + G / 32.  camp_pick_shape returns
+// the smallest shape that holds n species, or -1 (n > 2048).
+#define CAMP_SHAPE_BLOCK 100
+int camp_pick_shape(int n);
+// lanes per cell of that shape
+int camp_group_size(int n);
 
 // Shared-memory bytes per cell for LU element size 4 or 8.
 int camp_cell_smem_bytes(const DevMech &m, int lu_elem);

@@ -8,42 +8,49 @@
 
 namespace {
 using LT = CAMP_LT;
-constexpr int G = 32;
 
-// Raise a kernel's dynamic shared-memory limit once to the maximum, so that
+// Raise a kernel's dynamic shared-memory limit once to the maximum (the
+// block's 227 KB less the kernel's own static shared memory), so that
 // launches (possibly inside stream capture) make no further attribute calls.
-// One flag per kernel instantiation (the tag), not per function type.
+// One flag per kernel instantiation (the tag), not per function type.  A
+// failed call also clears the runtime's last-error state, so that it is not
+// reported again by a later, healthy launch.
 template <int Tag, class K>
 cudaError_t allow_smem(K kern) {
     static int done_dev = -1;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || done_dev == dev) return e;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 227 * 1024 - (int)fa.sharedSizeBytes);
     if (e == cudaSuccess) done_dev = dev;
+    else (void)cudaGetLastError();
     return e;
 }
 
-template <int NPL>
+template <int G, int NPL>
 cudaError_t launch_solve_npl(const DevMech &m, const SolveArgs &a, int grid, cudaStream_t s) {
     auto kern = campdev::k_solve<G, NPL, LT>;
     int smem = camp_cell_smem_bytes(m, (int)sizeof(LT)) * a.cpb;
-    cudaError_t e = allow_smem<NPL>(kern);
+    cudaError_t e = allow_smem<G * 16 + NPL>(kern);
     if (e != cudaSuccess) return e;
     kern<<<grid, G * a.cpb, smem, s>>>(m, a);
     return cudaGetLastError();
 }
 
-template <int NPL>
+template <int G, int NPL>
 cudaError_t occupancy_npl(const DevMech &m, int cpb, int *blocks) {
     auto kern = campdev::k_solve<G, NPL, LT>;
     int smem = camp_cell_smem_bytes(m, (int)sizeof(LT)) * cpb;
-    cudaError_t e = allow_smem<NPL>(kern);
+    cudaError_t e = allow_smem<G * 16 + NPL>(kern);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, G * cpb, smem);
 }
 
-template <int NPL>
+template <int G, int NPL>
 cudaError_t launch_jac_npl(const DevMech &m, long long n_cells, const double *state,
                            const double *env, double *jac, cudaStream_t s) {
     auto kern = campdev::k_jacobian<G, NPL, LT>;
@@ -54,7 +61,7 @@ cudaError_t launch_jac_npl(const DevMech &m, long long n_cells, const double *st
     return cudaGetLastError();
 }
 
-template <int NPL>
+template <int G, int NPL>
 cudaError_t launch_lu_npl(const DevMech &m, long long n_cells, const double *state,
                           const double *env, double gamma, const double *b, double *x, int *status,
                           cudaStream_t s) {
@@ -67,61 +74,44 @@ cudaError_t launch_lu_npl(const DevMech &m, long long n_cells, const double *sta
 }
 }  // namespace
 
-cudaError_t CAMP_FN(camp_launch_solve)(const DevMech &m, const SolveArgs &a, int grid, cudaStream_t s) {
-#define CALL(N) launch_solve_npl<N>(m, a, grid, s)
-    switch (camp_pick_npl(m.n)) {
-    case 1: return CALL(1);
-    case 2: return CALL(2);
-    case 3: return CALL(3);
-    case 4: return CALL(4);
-    case 6: return CALL(6);
-    case 8: return CALL(8);
-    default: return cudaErrorInvalidValue;
+// one case per instantiated cell shape (lanes per cell, register slots per lane)
+#define CAMP_DISPATCH_SHAPE(shape)                   \
+    switch (shape) {                                 \
+    case 1: return CALL(32, 1);                      \
+    case 2: return CALL(32, 2);                      \
+    case 3: return CALL(32, 3);                      \
+    case 4: return CALL(32, 4);                      \
+    case 6: return CALL(32, 6);                      \
+    case 8: return CALL(32, 8);                      \
+    case CAMP_SHAPE_BLOCK + 2: return CALL(64, 8);   \
+    case CAMP_SHAPE_BLOCK + 4: return CALL(128, 8);  \
+    case CAMP_SHAPE_BLOCK + 8: return CALL(256, 8);  \
+    default: return cudaErrorInvalidValue;           \
     }
+
+cudaError_t CAMP_FN(camp_launch_solve)(const DevMech &m, const SolveArgs &a, int grid, cudaStream_t s) {
+#define CALL(G_, N) launch_solve_npl<G_, N>(m, a, grid, s)
+    CAMP_DISPATCH_SHAPE(camp_pick_shape(m.n));
 #undef CALL
 }
 
 cudaError_t CAMP_FN(camp_occupancy)(const DevMech &m, int cpb, int *blocks) {
-#define CALL(N) occupancy_npl<N>(m, cpb, blocks)
-    switch (camp_pick_npl(m.n)) {
-    case 1: return CALL(1);
-    case 2: return CALL(2);
-    case 3: return CALL(3);
-    case 4: return CALL(4);
-    case 6: return CALL(6);
-    case 8: return CALL(8);
-    default: return cudaErrorInvalidValue;
-    }
+#define CALL(G_, N) occupancy_npl<G_, N>(m, cpb, blocks)
+    CAMP_DISPATCH_SHAPE(camp_pick_shape(m.n));
 #undef CALL
 }
 
 cudaError_t CAMP_FN(camp_launch_jacobian)(const DevMech &m, long long n_cells, const double *state,
                                           const double *env, double *jac, cudaStream_t s) {
-#define CALL(N) launch_jac_npl<N>(m, n_cells, state, env, jac, s)
-    switch (camp_pick_npl(m.n)) {
-    case 1: return CALL(1);
-    case 2: return CALL(2);
-    case 3: return CALL(3);
-    case 4: return CALL(4);
-    case 6: return CALL(6);
-    case 8: return CALL(8);
-    default: return cudaErrorInvalidValue;
-    }
+#define CALL(G_, N) launch_jac_npl<G_, N>(m, n_cells, state, env, jac, s)
+    CAMP_DISPATCH_SHAPE(camp_pick_shape(m.n));
 #undef CALL
 }
 
 cudaError_t CAMP_FN(camp_launch_lu_solve)(const DevMech &m, long long n_cells, const double *state,
                                           const double *env, double gamma, const double *b,
                                           double *x, int *status, cudaStream_t s) {
-#define CALL(N) launch_lu_npl<N>(m, n_cells, state, env, gamma, b, x, status, s)
-    switch (camp_pick_npl(m.n)) {
-    case 1: return CALL(1);
-    case 2: return CALL(2);
-    case 3: return CALL(3);
-    case 4: return CALL(4);
-    case 6: return CALL(6);
-    case 8: return CALL(8);
-    default: return cudaErrorInvalidValue;
-    }
+#define CALL(G_, N) launch_lu_npl<G_, N>(m, n_cells, state, env, gamma, b, x, status, s)
+    CAMP_DISPATCH_SHAPE(camp_pick_shape(m.n));
 #undef CALL
 }

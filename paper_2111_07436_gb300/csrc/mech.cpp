@@ -534,6 +534,7 @@ static void build_tables(HostMech &h) {
         for (int q = h.lu_rowptr[i]; q < h.lu_rowptr[i + 1]; q++)
             if (h.lu_colidx[q] >= h.d) lu_off[q] = h.dbase + (i - h.d) * h.LD + (h.lu_colidx[q] - h.d);
     h.nlu = h.dbase + h.D * h.LD;
+    if (h.nlu > 32767) throw std::runtime_error("LU storage too large for the packed tables (32767 values)");
     if (h.nlu > 32767) throw std::runtime_error("LU storage exceeds 32767 entries");
     auto off = [&](int i, int j) {
         auto b = h.lu_colidx.begin() + h.lu_rowptr[i], e = h.lu_colidx.begin() + h.lu_rowptr[i + 1];

@@ -18,7 +18,9 @@ figures, Sect. 2.3):
     {"name": str,
      "species": [{"name": str, "atoms": int}, ...],          # gas phase
      "phases": {"aqueous": [{"name": str, "atoms": int}, ...]},
-     "aerosol": {"phase": "aqueous", "sections": 8},         # optional
+     "aerosol": {"phase": "aqueous", "sections": 8,           # optional
+                 "representation": "particles"},   # optional: instances are
+                                                   # computational particles
      "reactions": [ {"type": ..., ...}, ... ]}
 
 Reaction types and their fields (units follow Table 2 of the paper):
@@ -336,6 +338,19 @@ def process_variety_mechanism(seed=106, n_sections=4):
     return mech
 
 
+def particle_resolved_mechanism(n_particles=128, seed=106):
+    """The process-variety mechanism with its condensed phase instanced once
+    per computational particle (the particle-resolved SingleParticle
+    representation, Sect. 2.2.3 and Table 6; the paper's box model used 10^4
+    particles, Sect. 4.1): the same instance expansion as the sections, with
+    many more instances, so the Jacobian is block-arrow (particle blocks coupled to the gas species
+    they exchange with).  18 gas species + 7 per particle."""
+    mech = process_variety_mechanism(seed=seed, n_sections=n_particles)
+    mech["name"] = f"particle-resolved-{n_particles}x7+gas18"
+    mech["aerosol"]["representation"] = "particles"
+    return mech
+
+
 # --------------------------------------------------------------------------
 # layout helpers (interface description only)
 # --------------------------------------------------------------------------
@@ -391,6 +406,11 @@ def cells(mech, n_cells, seed, T=None, P=None, sza=True, night_fraction=None,
     With cloud_fraction, that share of cells holds cloud water: a liquid water
     content uniform 0.1..1 g/m^3 spread over the sections in proportion to
     N r^3; the other cells of a sectional mechanism then hold no water (L = 0).
+    A particle-resolved mechanism (aerosol "representation": "particles")
+    gets per cell and particle a radius log-normal around 0.1 um (geometric
+    standard deviation 1.8, within 5 nm..10 um), the cell's number
+    concentration (log-uniform 1e2..1e4 cm^-3) shared evenly by its
+    computational particles, and L = N 4/3 pi r^3.
     """
     rng = np.random.default_rng(seed)
     lay = layout(mech)
@@ -411,7 +431,12 @@ def cells(mech, n_cells, seed, T=None, P=None, sza=True, night_fraction=None,
     for k, (d, kind) in enumerate(zip(lay.runtime_defaults, lay.runtime_kind)):
         env[:, 2 + k] = d * (mu if kind == "PHOTOLYSIS" else 1.0)
     base = 2 + len(lay.runtime_defaults)
-    if lay.n_sections:
+    if lay.n_sections and mech["aerosol"].get("representation") == "particles":
+        P = lay.n_sections
+        r = np.clip(np.exp(rng.normal(math.log(1e-7), math.log(1.8), (n_cells, P))), 5e-9, 1e-5)
+        N = np.repeat(_logu(rng, 1e8, 1e10, (n_cells, 1)) / P, P, axis=1)
+        L = N * (4.0 / 3.0) * math.pi * r ** 3
+    elif lay.n_sections:
         r = SECTION_RADII[: lay.n_sections]
         N = _logu(rng, 1e1, 1e4, (n_cells, lay.n_sections)) * 1e6
         L = N * (4.0 / 3.0) * math.pi * r[None, :] ** 3
@@ -421,8 +446,10 @@ def cells(mech, n_cells, seed, T=None, P=None, sza=True, night_fraction=None,
             share = N * r[None, :] ** 3
             share = share / share.sum(axis=1, keepdims=True)
             L = np.where(cloudy[:, None], lwc[:, None] * share, 0.0)
+        r = np.broadcast_to(r[None, :], (n_cells, lay.n_sections))
+    if lay.n_sections:
         for b in range(lay.n_sections):
-            env[:, base + 3 * b] = r[b]
+            env[:, base + 3 * b] = r[:, b]
             env[:, base + 3 * b + 1] = N[:, b]
             env[:, base + 3 * b + 2] = L[:, b]
     return y, env
@@ -484,7 +511,8 @@ def serving_requests(n_requests=2000, seed=205, gas_share=0.7, cells_lo=256, cel
 
 
 def workload(k: int) -> Workload:
-    """k = 1..3: the single-mechanism workloads (sizes in the docstrings)."""
+    """k = 1..3: the single-mechanism workloads (sizes in the docstrings);
+    k = 6: the particle-resolved workload."""
     if k == 1:
         return Workload("small-gas 1 cell, 60 x 60 s", small_gas_mechanism(), 1, 60.0, 60,
                         1e-4, 1e-5, 201, dict(T=298.0, P=101300.0, sza=False))
@@ -494,4 +522,7 @@ def workload(k: int) -> Workload:
     if k == 3:
         return Workload("multiphase-232 4096 cells, 300 s", multiphase_mechanism(), 4096, 300.0, 1,
                         1e-4, 1e-5, 203, {})
+    if k == 6:  # the particle-resolved shape (a row beyond the five configurations)
+        return Workload("particle-resolved 128 particles (914 species) 2048 cells, 180 s",
+                        particle_resolved_mechanism(128), 2048, 180.0, 1, 1e-4, 1e-5, 206, {})
     raise ValueError(k)

@@ -199,3 +199,20 @@ def test_atol_below_the_fp32_range(cuda, variant):
     yo, sto, _ = om.solve(y0, env, 600.0, 1e-4, atol)
     assert (st == 0).all() and (sto == 0).all()
     parity.check(om, y0, env, 600.0, 1e-4, atol, yg, yo)
+
+
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+@pytest.mark.parametrize("n_particles,C", [(40, 96), (100, 12)])
+def test_particle_resolved_cells(form, n_particles, C):
+    """The particle-resolved representation: one condensed-phase instance per
+    computational particle (298 and 718 species), integrated by a block of
+    64 or 128 threads per cell instead of one warp."""
+    mj = w.particle_resolved_mechanism(n_particles)
+    text = json.dumps(mj)
+    gm, om = camp.Mechanism(text), oracle.Mechanism(text)
+    y0, env = w.cells(mj, C, seed=71)
+    yg, st = _gpu_solve(gm, y0, env, 180.0, 1e-4, 1e-5, *form)
+    yo, sto, _ = om.solve(y0, env, 180.0, 1e-4, 1e-5)
+    assert (st == 0).all() and (sto == 0).all()
+    parity.check(om, y0, env, 180.0, 1e-4, 1e-5, yg, yo)
+    assert (yo[:, 18:] > 1e-5).sum() > C  # the particles take part

@@ -12,7 +12,8 @@ from paper_2111_07436_gb300 import camp, workloads as w
 pytestmark = pytest.mark.gpu
 
 MECHS = {"small": w.small_gas_mechanism(), "gas72": w.large_gas_mechanism(),
-         "multiphase232": w.multiphase_mechanism(), "variety": w.process_variety_mechanism()}
+         "multiphase232": w.multiphase_mechanism(), "variety": w.process_variety_mechanism(),
+         "particles40": w.particle_resolved_mechanism(40)}
 
 
 def _inputs(mj, C, seed):

@@ -27,6 +27,7 @@ def _mechs():
                                             seed=78, n_sections=2, n_phase_species=5, n_henry=2,
                                             n_split_eq=1, n_simple_eq=1)
     out["variety"] = w.process_variety_mechanism()
+    out["particles40"] = w.particle_resolved_mechanism(40)
     out["variety_1sec"] = w.process_variety_mechanism(seed=9, n_sections=1)
     return out
 

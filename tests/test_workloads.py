@@ -88,3 +88,17 @@ def test_process_variety_mechanism_holds_every_process_type():
     assert json.dumps(mj) == json.dumps(w.process_variety_mechanism())
     lay = w.layout(mj)
     assert len(lay.species) == 18 + 4 * 7
+
+
+def test_particle_resolved_inputs():
+    mj = w.particle_resolved_mechanism(64)
+    lay = w.layout(mj)
+    assert len(lay.species) == 18 + 64 * 7 and lay.n_sections == 64
+    y, env = w.cells(mj, 50, seed=3)
+    base = 2 + len(lay.runtime_defaults)
+    r, N, L = env[:, base::3], env[:, base + 1::3], env[:, base + 2::3]
+    assert r.shape == (50, 64) and ((r >= 5e-9) & (r <= 1e-5)).all()
+    assert 3e-8 < np.exp(np.log(r).mean()) < 3e-7               # log-normal around 0.1 um
+    assert np.allclose(N, N[:, :1]) and ((N.sum(axis=1) >= 1e8) & (N.sum(axis=1) <= 1e10)).all()
+    np.testing.assert_allclose(L, N * 4.0 / 3.0 * np.pi * r ** 3)
+    assert (y[:, 18:] == 0).all()
