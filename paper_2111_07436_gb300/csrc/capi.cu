@@ -77,18 +77,16 @@ int camp_pick_shape(int n) {
     const int avail[] = {1, 2, 3, 4, 6, 8};
     for (int a : avail)
         if (a >= need) return a;
-    for (int warps = 2; warps <= 8; warps *= 2)  // blocks of 64, 128, 256 threads, 8 slots a lane
-        if (n <= 8 * 32 * warps) return CAMP_SHAPE_BLOCK + warps;
+    // blocks of 64, 128, 256 threads with 8 slots a lane: the lane count the
+    // mechanism's per-lane tables are built for
+    if (n <= 2048) return CAMP_SHAPE_BLOCK + camp_cell_lanes(n) / 32;
     return -1;
 }
 
-int camp_group_size(int n) {
-    const int sh = camp_pick_shape(n);
-    return sh > CAMP_SHAPE_BLOCK ? 32 * (sh - CAMP_SHAPE_BLOCK) : 32;
-}
+int camp_group_size(int n) { return camp_cell_lanes(n); }
 
 int camp_cell_smem_bytes(const DevMech &m, int lu_elem) {
-    return campdev::cell_smem(m.n, m.R, m.n_rev, m.nlu, lu_elem).bytes;
+    return campdev::cell_smem(m.n, m.R, m.n_rev, m.nlu, lu_elem, m.n_part).bytes;
 }
 
 cudaError_t camp_launch_rates(const DevMech &m, long long n_cells, const double *env, double *kf,

@@ -45,11 +45,13 @@ struct CellSmem {
     int ys, rs, kf, kr, x, lu, bytes;
 };
 __host__ __device__ inline int align16(int b) { return (b + 15) & ~15; }
-__host__ __device__ inline CellSmem cell_smem(int n, int R, int n_rev, int nlu, int lu_elem) {
+// rs holds the R rate terms, then n_part partial sums (of split forcing sums
+// inside an f evaluation, of split substitution rows inside a solve)
+__host__ __device__ inline CellSmem cell_smem(int n, int R, int n_rev, int nlu, int lu_elem, int n_part) {
     CellSmem c;
     int o = 0;
     c.ys = o; o = align16(o + 8 * n);
-    c.rs = o; o = align16(o + 8 * R);
+    c.rs = o; o = align16(o + 8 * (R + n_part));
     c.kf = o; o = align16(o + 8 * R);
     c.kr = o; o = align16(o + 8 * n_rev);
     // the substitution vector shares the rate-term scratch when it fits:
@@ -72,7 +74,7 @@ struct CellPtr {
     double *ys, *rs, *kf, *kr;
     LT *x, *lu;
     __device__ CellPtr(char *base, const DevMech &m) {
-        CellSmem c = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT));
+        CellSmem c = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part);
         ys = (double *)(base + c.ys);
         rs = (double *)(base + c.rs);
         kf = (double *)(base + c.kf);
@@ -300,49 +302,47 @@ __device__ __forceinline__ double gather_entry(const DevMech &m, int q, const do
 }
 
 // y in c.ys (written by the caller, who also made it visible to the group)
-// -> f (own positions).  The per-position sums are spread over the lanes by
-// the compiler's balanced assignment (32-lane groups) and handed back
-// through shared memory (reusing ys).
+// -> f (own positions).  The per-position sums are spread over the cell's
+// lanes by the compiler's balanced assignment (long sums in chunks) and
+// handed back through shared memory (reusing ys).
 template <int G, int NPL, typename LT>
 __device__ __forceinline__ void eval_f_ys(const DevMech &m, const CellPtr<LT> &c, double (&f)[NPL],
                                           int lane, unsigned gm) {
     for (int k = lane; k < m.R; k += G) c.rs[k] = rate_term(m, k, c.ys, c.kf[k], c.kr);
     gsync<G>(gm);
-    if (G == 32) {
-        double *fs = c.ys;  // y is no longer needed
-        const int b0 = __ldg(m.flane_ptr + lane), b1 = __ldg(m.flane_ptr + lane + 1);
-        for (int i = b0; i < b1; i++) {
-            const int2 job = __ldg(m.fjob + i);
-            const int end = job.x + hi16(job.y);
-            double acc = 0.0, acc2 = 0.0;
-            int q = job.x;
-            for (; q + 1 < end; q += 2) {
-                acc += gather_entry(m, q, c.rs);
-                acc2 += gather_entry(m, q + 1, c.rs);
-            }
-            if (q < end) acc += gather_entry(m, q, c.rs);
-            fs[lo16(job.y)] = acc + acc2;
+    double *fs = c.ys;  // y is no longer needed
+    double *fp = c.rs + m.R;
+    const int b0 = __ldg(m.flane_ptr + lane), b1 = __ldg(m.flane_ptr + lane + 1);
+    for (int i = b0; i < b1; i++) {
+        const int2 job = __ldg(m.fjob + i);
+        const int end = job.x + hi16(job.y), dst = lo16(job.y);
+        double acc = 0.0, acc2 = 0.0;
+        int q = job.x;
+        for (; q + 1 < end; q += 2) {
+            acc += gather_entry(m, q, c.rs);
+            acc2 += gather_entry(m, q + 1, c.rs);
         }
-        gsync<G>(gm);
-#pragma unroll
-        for (int s = 0; s < NPL; s++) {
-            int p = lane + G * s;
-            f[s] = (p < m.n) ? fs[p] : 0.0;
-        }
-        gsync<G>(gm);
-    } else {
-#pragma unroll
-        for (int s = 0; s < NPL; s++) {
-            int p = lane + G * s;
-            double acc = 0.0;
-            if (p < m.n) {
-                int b = __ldg(m.fptr + p), e = __ldg(m.fptr + p + 1);
-                for (int q = b; q < e; q++) acc += gather_entry(m, q, c.rs);
-            }
-            f[s] = acc;
-        }
-        gsync<G>(gm);  // the rate terms are read before anyone reuses their scratch
+        if (q < end) acc += gather_entry(m, q, c.rs);
+        if (G == 32 || dst < m.n) fs[dst] = acc + acc2;  // one-warp cells have no split sums
+        else fp[dst - m.n] = acc + acc2;
     }
+    gsync<G>(gm);
+    if (G > 32 && m.n_fsplit > 0) {  // split sums: their partials in a fixed order
+        for (int i = lane; i < m.n_fsplit; i += G) {
+            const int2 sp = __ldg(m.fsplit + i);
+            const int first = lo16(sp.y), cnt = hi16(sp.y);
+            double t = 0.0;
+            for (int j = 0; j < cnt; j++) t += fp[first + j];
+            fs[sp.x] = t;
+        }
+        gsync<G>(gm);
+    }
+#pragma unroll
+    for (int s = 0; s < NPL; s++) {
+        int p = lane + G * s;
+        f[s] = (p < m.n) ? fs[p] : 0.0;
+    }
+    gsync<G>(gm);
 }
 
 // y (own positions, registers) -> f (own positions)
@@ -414,7 +414,7 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
     gsync<G>(gm);
     const LT g = (LT)gamma;
     if constexpr (sizeof(LT) == 4) {
-        if (G == 32) {
+        {
             // flat per-lane entry list: independent loads, one store per non-zero
             const int b = __ldg(m.jl_ptr + lane), e = __ldg(m.jl_ptr + lane + 1);
             LT acc = (LT)0;
@@ -602,35 +602,67 @@ __device__ __forceinline__ bool dense_factor(LT *A, int D, int LD, int lane, uns
 // panel width of the dense factorisation
 constexpr int DENSE_W = 8;
 
+// one op of the row-wise factorisation: a division makes the multiplier l
+// (lu[src] holds 1 / U(k,k)), an update subtracts l U(k,j) from its target,
+// an LU value or (bit 15 of the target; block cells only) a partial sum
+template <bool PART, typename LT>
+__device__ __forceinline__ void factor_op(uint32_t op, LT *lu, LT *part, int pbase, LT &l) {
+    const int t = CAMP_OP_TGT(op), s = CAMP_OP_SRC(op);
+    if (op & CAMP_OP_DIV) {
+        l = lu[t] * lu[s];
+        lu[t] = l;
+    } else if (PART && (t & 0x8000)) {
+        part[pbase + (t & 0x7fff)] -= l * lu[s];
+    } else {
+        lu[t] -= l * lu[s];
+    }
+}
+
+template <typename LT>
+__device__ __forceinline__ bool take_reciprocal(const DevMech &m, LT *lu, int i) {
+    const int di = __ldg(m.udiag + i);
+    const LT u = lu[di];
+    lu[di] = recip(u);
+    return bad_pivot(u);
+}
+
 template <int G, typename LT>
 __device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigned gm) {
     LT *lu = c.lu;
+    LT *part = (LT *)(c.rs + m.R);  // chunk partials: the rate scratch is free here
     bool bad = false;
     // sparse rows (and the sparse-pivot updates of the block rows), by level
     for (int L = 0; L < m.n_flev; L++) {
-        int b = __ldg(m.flev_ptr + L), e = __ldg(m.flev_ptr + L + 1);
+        const int b = __ldg(m.ljob_ptr + L), e = __ldg(m.ljob_ptr + L + 1);
         for (int r = b + lane; r < e; r += G) {
-            int i = __ldg(m.frow + r);
-            int qb = __ldg(m.fops_ptr + i), qe = __ldg(m.fops_ptr + i + 1);
+            const int4 jb = __ldg(m.ljob + r);
+            const int cnt = lo16(jb.y);
+            if constexpr (G > 32) {
+                for (int k = 0; k < hi16(jb.y); k++) part[jb.w + k] = (LT)0;
+            }
             LT l = (LT)0;
-            for (int q = qb; q < qe; q++) {
-                uint32_t op = __ldg(m.fops + q);
-                int t = CAMP_OP_TGT(op), s = CAMP_OP_SRC(op);
-                if (op & CAMP_OP_DIV) {
-                    l = lu[t] * lu[s];  // lu[s] holds 1 / U(k,k)
-                    lu[t] = l;
-                } else {
-                    lu[t] -= l * lu[s];
-                }
-            }
-            if (i < m.d) {
-                const int di = __ldg(m.udiag + i);
-                LT u = lu[di];
-                bad |= bad_pivot(u);
-                lu[di] = recip(u);
-            }
+            for (int q = jb.x; q < jb.x + cnt; q++) factor_op<(G > 32)>(__ldg(m.lops + q), lu, part, jb.w, l);
+            if (hi16(jb.z) & 1) bad |= take_reciprocal(m, lu, lo16(jb.z));
         }
         gsync<G>(gm);
+        if constexpr (G > 32) {  // rows cut into chunks: partials in order, then the tail
+            const int rb = __ldg(m.lred_ptr + L), re = __ldg(m.lred_ptr + L + 1);
+            for (int k = rb + lane; k < re; k += G) {
+                const int4 rd = __ldg(m.lred + k);
+                const int ns = lo16(rd.z), nch = hi16(rd.z);
+                for (int s = 0; s < ns; s++) {
+                    const int off = __ldg(m.lred_off + rd.y + s);
+                    LT t = lu[off];
+                    for (int ch = 0; ch < nch; ch++) t += part[rd.w + ch * ns + s];
+                    lu[off] = t;
+                }
+                const int2 tl = __ldg(m.ltail + k);
+                LT l = (LT)0;
+                for (int q = tl.x; q < tl.x + tl.y; q++) factor_op<false>(__ldg(m.lops + q), lu, part, 0, l);
+                if (hi16(rd.x) & 1) bad |= take_reciprocal(m, lu, lo16(rd.x));
+            }
+            if (re > rb) gsync<G>(gm);
+        }
     }
     // the dense block is one warp's work (a block group's first warp)
     LT *A = lu + m.dbase;
@@ -746,13 +778,16 @@ __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, uns
     const LT *lu = c.lu;
     gsync<G>(gm);
     // forward, sparse rows and the L21 part of block rows (rows without L
-    // entries keep their value)
+    // entries keep their value); split rows through partials (LU precision,
+    // after the rate terms: free while solving)
+    LT *xp = (LT *)(c.rs + m.R);
     for (int L = 0; L < m.n_slev; L++) {
         int b = __ldg(m.slev_ptr + L), e = __ldg(m.slev_ptr + L + 1);
         for (int r = b + lane; r < e; r += G) {
-            int i = __ldg(m.srow + r);
-            LT s = x[i], s2 = (LT)0;
-            int qb = __ldg(m.sl_ptr + i), qe = __ldg(m.sl_ptr + i + 1);
+            const int2 job = __ldg(m.sjob + r);
+            const int i = lo16(job.y);
+            LT s = (G == 32 || i < m.n) ? x[i] : (LT)0, s2 = (LT)0;  // one-warp cells: no split rows
+            int qb = job.x, qe = job.x + hi16(job.y);
             int q = qb;
             for (; q + 1 < qe; q += 2) {
                 const int e2 = __ldg(m.sl_pack + q), e3 = __ldg(m.sl_pack + q + 1);
@@ -763,9 +798,23 @@ __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, uns
                 const int e2 = __ldg(m.sl_pack + q);
                 s -= lu[lo16(e2)] * x[hi16(e2)];
             }
-            x[i] = s - s2;
+            if (G == 32 || i < m.n) x[i] = s - s2;
+            else xp[i - m.n] = s - s2;
         }
         gsync<G>(gm);
+        if constexpr (G > 32) {
+            const int sb = __ldg(m.ssplit_ptr + L), se = __ldg(m.ssplit_ptr + L + 1);
+            if (se > sb) {
+                for (int k = sb + lane; k < se; k += G) {
+                    const int2 sp = __ldg(m.ssplit + k);
+                    const int first = lo16(sp.y), cnt = hi16(sp.y);
+                    LT t = x[sp.x];
+                    for (int j = 0; j < cnt; j++) t += xp[first + j];
+                    x[sp.x] = t;
+                }
+                gsync<G>(gm);
+            }
+        }
     }
     const LT *A = lu + m.dbase;
     if (G <= 32 || lane < 32) {

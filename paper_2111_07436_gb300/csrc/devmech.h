@@ -28,6 +28,16 @@ enum {
 
 #define CAMP_NPAR 10  // rate parameters per process
 
+// Lanes that integrate one cell of an n-species mechanism: one warp up to
+// 256 species, else one block of 64, 128 or 256 threads (up to 8 species a
+// lane).  The per-lane tables below are built for this many lanes.
+inline int camp_cell_lanes(int n) {
+    if (n <= 256) return 32;
+    if (n <= 512) return 64;
+    if (n <= 1024) return 128;
+    return 256;
+}
+
 // LU op encoding for the sparse (row-wise) part of the factorisation
 #define CAMP_OP_DIV 0x80000000u
 #define CAMP_OP_TGT(op) ((int)((op)&0xFFFFu))
@@ -39,6 +49,7 @@ struct DevMech {
     int n_env;
     int env_sec_base; // env index of section 0's radius
     int npl32;        // ceil(n / 32)
+    int lanes;        // lanes per cell the per-lane tables were built for
 
     // --- rate constants (process order) ---
     const int *rtype;     // [R]
@@ -58,7 +69,7 @@ struct DevMech {
     const double *fc;     // [nf] net stoichiometric coefficient
     // positions each of the 32 lanes sums, balanced by gather length
     const int *flane_ptr; // [33]
-    const int *flane_pos; // [n]
+    const int *flane_pos; // [jobs] each job's destination (host reference)
 
     // --- the same tables packed so one 16-byte load serves one record ---
     // rate term k: x = fwd0 | fwd1 << 16, y = fwd2 | rv << 16,
@@ -67,8 +78,15 @@ struct DevMech {
     // gather entry q: process | index into fcoef << 16
     const int *fpk;       // [nf]
     const double *fcoef;  // the mechanism's distinct net coefficients
-    // lane job i: x = first entry, y = position | entry count << 16
-    const int2 *fjob;     // [n], lanes' jobs in flane_ptr ranges
+    // lane job i: x = first entry, y = destination | entry count << 16; a
+    // destination d < n is the position's f, d >= n the partial sum d - n of
+    // a position whose sum was split into chunks
+    const int2 *fjob;     // lanes' jobs in flane_ptr ranges
+    int n_part;           // partial sums of split forcing sums and substitution
+                          // rows (FP64 scratch after the rate terms)
+    int n_fsplit;         // positions whose sums are split
+    // split position i: x = position, y = first partial | chunk count << 16
+    const int2 *fsplit;   // [n_fsplit]
     // Jacobian non-zero t: x = first entry, y = end entry, z = LU offset, w = diagonal
     const int4 *jnz;      // [nnzJ]
     // Jacobian entry q: x = bits of the FP32 coefficient, y = constant index
@@ -107,13 +125,35 @@ struct DevMech {
     const int *flev_ptr;  // [n_flev+1] into frow
     const int *frow;      // rows (positions)
     const int *fops_ptr;  // [n+1]
-    const uint32_t *fops; // encoded DIV/UPD ops
+    const uint32_t *fops; // encoded DIV/UPD ops, row by row
+    // the same ops as lane jobs, by level (flev levels).  Job: x = first op in
+    // lops, y = op count | partial slots << 16, z = row | (1 << 16 if the job
+    // ends by taking the row's pivot reciprocal), w = partial base.  An update
+    // whose target has bit 15 set adds to partial w + (target & 0x7fff)
+    // instead of the LU value.  Per level, the rows cut into chunks then get
+    // a reduction (x = row | reciprocal flag << 16, y = first entry of
+    // lred_off, z = shared columns ns | chunks << 16, w = partial base; chunk
+    // c's slot s is w + c ns + s) and their tail ops (x = first op, y = count).
+    const int *ljob_ptr;  // [n_flev+1] into ljob
+    const int4 *ljob;
+    const uint32_t *lops;
+    const int *lred_ptr;  // [n_flev+1] into lred / ltail
+    const int4 *lred;
+    const int *lred_off;  // LU offsets of the shared columns
+    const int2 *ltail;
 
-    // forward substitution of the sparse part: the rows that have L entries,
-    // by level (rows within a level ordered to balance the lanes), entries
+    // forward substitution of the sparse part: lane jobs by level (jobs
+    // within a level ordered to balance the lanes) over the rows that have L
+    // entries.  Job: x = first entry, y = destination | entry count << 16; a
+    // destination d < n is row d, finished by the job, d >= n the partial
+    // dot product d - n of a row cut into chunks; the level's split rows
+    // (x = row, y = first partial | chunk count << 16) then subtract their
+    // partials in order.
     int n_slev;
-    const int *slev_ptr;  // [n_slev+1] into srow
-    const int *srow;
+    const int *slev_ptr;  // [n_slev+1] into sjob
+    const int2 *sjob;
+    const int *ssplit_ptr; // [n_slev+1] into ssplit
+    const int2 *ssplit;
     const int *sl_ptr;    // [n+1]
     const int *sl_off;    // storage offset of L(i,k)
     const int *sl_col;    // k

@@ -30,7 +30,7 @@ __global__ void __maxnreg__((sizeof(LT) == 8 || G > 32) ? 255 : (NPL >= 6 ? 224 
     extern __shared__ __align__(16) char smem[];
     const int group = threadIdx.x / G, lane = threadIdx.x % G;
     const unsigned gm = group_mask<G>();
-    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT));
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part);
     CellPtr<LT> c(smem + group * L.bytes, m);
     long long cell = a.queue ? 0 : (long long)blockIdx.x * a.cpb + group;
     for (;;) {
@@ -110,7 +110,7 @@ __global__ void k_forcing(DevMech m, long long n_cells, const double *state, con
     const unsigned gm = group_mask<G>();
     const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
     if (cell >= n_cells) return;
-    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT));
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part);
     CellPtr<LT> c(smem + group * L.bytes, m);
     double y[NPL], f[NPL];
     load_cell<G, NPL, LT>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
@@ -132,7 +132,7 @@ __global__ void k_jacobian(DevMech m, long long n_cells, const double *state, co
     const unsigned gm = group_mask<G>();
     const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
     if (cell >= n_cells) return;
-    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT));
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part);
     CellPtr<LT> c(smem + group * L.bytes, m);
     double y[NPL];
     load_cell<G, NPL, LT>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
@@ -150,7 +150,7 @@ __global__ void k_lu_solve(DevMech m, long long n_cells, const double *state, co
     const unsigned gm = group_mask<G>();
     const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
     if (cell >= n_cells) return;
-    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT));
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part);
     CellPtr<LT> c(smem + group * L.bytes, m);
     double y[NPL];
     load_cell<G, NPL, LT>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);

@@ -262,13 +262,7 @@ static void pack_records(HostMech &h) {
             h.fpk[q] = h.fk[q] | (ci << 16);
         }
     }
-    // lane jobs: (first entry, position | entry count << 16)
-    h.fjob.assign((size_t)n * 2, 0);
-    for (int i = 0; i < n; i++) {
-        int p = h.flane_pos[i];
-        h.fjob[(size_t)i * 2 + 0] = h.fptr[p];
-        h.fjob[(size_t)i * 2 + 1] = p | ((h.fptr[p + 1] - h.fptr[p]) << 16);
-    }
+
     const int nnzJ = (int)h.colidx.size();
     h.jnz.assign((size_t)nnzJ * 4, 0);
     for (int t = 0; t < nnzJ; t++) {
@@ -286,17 +280,18 @@ static void pack_records(HostMech &h) {
         h.jpack[q * 4 + 1] = h.jk[q];
         h.jpack[q * 4 + 2] = field16(h.jo[2 * q]) | (field16(h.jo[2 * q + 1]) << 16);
     }
-    // per-lane flat Jacobian entry lists, longest-processing-time over 32 lanes
+    // per-lane flat Jacobian entry lists, longest-processing-time over the lanes
     {
+        const int NL = camp_cell_lanes(n);
         std::vector<int> order(nnzJ);
         for (int t = 0; t < nnzJ; t++) order[t] = t;
         auto cnt = [&](int t) { return std::max(1, h.jptr[t + 1] - h.jptr[t]); };
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt(a) > cnt(b); });
-        std::vector<std::vector<int>> lanes(32);
-        std::vector<int> load(32, 0);
+        std::vector<std::vector<int>> lanes(NL);
+        std::vector<int> load(NL, 0);
         for (int t : order) {
             int best = 0;
-            for (int l = 1; l < 32; l++)
+            for (int l = 1; l < NL; l++)
                 if (load[l] < load[best]) best = l;
             lanes[best].push_back(t);
             load[best] += cnt(t);
@@ -417,31 +412,156 @@ static void build_structure(HostMech &h) {
     }
 }
 
-// Order the rows of one level, rows[b, e), so that the G = 32 lanes get even
-// work: lane l takes positions b + l, b + l + 32, ...  Rows go heaviest
+// Order the rows of one level, rows[b, e), so that the G lanes of a cell get
+// even work: lane l takes positions b + l, b + l + G, ...  Rows go heaviest
 // first to the lane with the least work among those with a free position.
 template <class Cost>
-static void balance_level(std::vector<int> &rows, int b, int e, Cost cost) {
+static void balance_level(std::vector<int> &rows, int b, int e, int G, Cost cost) {
     const int len = e - b;
-    if (len <= 32) {  // one row per lane: order only
+    if (len <= G) {  // one row per lane: order only
         std::stable_sort(rows.begin() + b, rows.begin() + e, [&](int x, int y) { return cost(x) > cost(y); });
         return;
     }
     std::vector<int> sorted(rows.begin() + b, rows.begin() + e);
     std::stable_sort(sorted.begin(), sorted.end(), [&](int x, int y) { return cost(x) > cost(y); });
-    std::vector<long long> load(32, 0);
-    std::vector<std::vector<int>> mine(32);
-    std::vector<int> cap(32);
-    for (int l = 0; l < 32; l++) cap[l] = (len - l + 31) / 32;
+    std::vector<long long> load(G, 0);
+    std::vector<std::vector<int>> mine(G);
+    std::vector<int> cap(G);
+    for (int l = 0; l < G; l++) cap[l] = (len - l + G - 1) / G;
     for (int r : sorted) {
         int best = -1;
-        for (int l = 0; l < 32; l++)
+        for (int l = 0; l < G; l++)
             if ((int)mine[l].size() < cap[l] && (best < 0 || load[l] < load[best])) best = l;
         mine[best].push_back(r);
         load[best] += cost(r);
     }
-    for (int l = 0; l < 32; l++)
-        for (size_t k = 0; k < mine[l].size(); k++) rows[b + l + 32 * (int)k] = mine[l][k];
+    for (int l = 0; l < G; l++)
+        for (size_t k = 0; k < mine[l].size(); k++) rows[b + l + G * (int)k] = mine[l][k];
+}
+
+// The sparse factorisation as lane jobs, level by level.  A row whose ops
+// far exceed its level's mean load per lane (the arrow rows of a
+// particle-resolved mechanism: one gas species against every particle) is
+// cut at pivot boundaries into chunks that run on different lanes: each
+// chunk's pivots read only columns no other chunk writes, and its updates of
+// columns that several chunks (or the rest of the row) write go to chunk
+// partial sums.  One lane then adds the partials in order and finishes the
+// row's remaining pivots (the tail).
+static void build_factor_jobs(HostMech &h) {
+    const int NL = camp_cell_lanes(h.n);
+    h.ljob_ptr.assign(1, 0);
+    h.ljob.clear();
+    h.lops.clear();
+    h.lred_ptr.assign(1, 0);
+    h.lred.clear();
+    h.lred_off.clear();
+    h.ltail.clear();
+    h.n_lpart = 0;
+    auto tgt = [](uint32_t op) { return (int)(op & 0xFFFFu); };
+    for (size_t l = 0; l + 1 < h.flev_ptr.size(); l++) {
+        const int rb = h.flev_ptr[l], re = h.flev_ptr[l + 1];
+        long long total = 0;
+        for (int r = rb; r < re; r++) {
+            const int i = h.frow[r];
+            total += h.fops_ptr[i + 1] - h.fops_ptr[i] + 2;
+        }
+        const int CH = std::max(16, (int)((total + NL - 1) / NL));
+        struct Job { std::vector<uint32_t> ops; int row, recip, ns, pbase; };
+        std::vector<Job> jobs;
+        int lpart = 0;
+        for (int r = rb; r < re; r++) {
+            const int i = h.frow[r];
+            const int recip = i < h.d ? 1 : 0;
+            std::vector<uint32_t> ops(h.fops.begin() + h.fops_ptr[i], h.fops.begin() + h.fops_ptr[i + 1]);
+            if (NL <= 32 || (int)ops.size() <= 2 * CH) { jobs.push_back({ops, i, recip, 0, 0}); continue; }
+            // pivot groups: a DIV and its updates
+            std::vector<std::pair<int, int>> groups;  // [begin, end) in ops
+            for (int q = 0; q < (int)ops.size(); q++) {
+                if ((ops[q] & CAMP_OP_DIV) || groups.empty()) groups.push_back({q, q + 1});
+                else groups.back().second = q + 1;
+            }
+            std::vector<std::vector<int>> chunks;  // op indices
+            std::unordered_map<int, std::vector<int>> writers;  // column -> chunks writing it
+            std::vector<int> cur;
+            int tail_from = (int)ops.size();
+            for (auto &g : groups) {
+                const int c = (int)chunks.size();
+                auto it = writers.find(tgt(ops[g.first]));
+                bool foreign = false;
+                if (it != writers.end())
+                    for (int w : it->second) foreign |= (w != c);
+                if (foreign) { tail_from = g.first; break; }
+                for (int q = g.first; q < g.second; q++) {
+                    cur.push_back(q);
+                    auto &v = writers[tgt(ops[q])];
+                    if (v.empty() || v.back() != c) v.push_back(c);
+                }
+                if ((int)cur.size() >= CH) { chunks.push_back(cur); cur.clear(); }
+            }
+            if (!cur.empty()) chunks.push_back(cur);
+            if (chunks.size() < 2) { jobs.push_back({ops, i, recip, 0, 0}); continue; }
+            std::unordered_map<int, int> tail_cols;
+            for (int q = tail_from; q < (int)ops.size(); q++) tail_cols[tgt(ops[q])] = 1;
+            std::vector<int> shared;
+            std::unordered_map<int, int> slot;
+            for (auto &g : groups)
+                for (int q = g.first; q < g.second && q < tail_from; q++) {
+                    const int t = tgt(ops[q]);
+                    if (slot.count(t)) continue;
+                    if (writers[t].size() >= 2 || tail_cols.count(t)) {
+                        slot[t] = (int)shared.size();
+                        shared.push_back(t);
+                    }
+                }
+            const int ns = (int)shared.size(), nch = (int)chunks.size();
+            if (ns > 0x7fff || nch > 0xffff) throw std::runtime_error("factor chunks do not fit their fields");
+            for (int c = 0; c < nch; c++) {
+                Job jb{{}, i, 0, ns, lpart + c * ns};
+                for (int q : chunks[c]) {
+                    uint32_t op = ops[q];
+                    if (!(op & CAMP_OP_DIV) && slot.count(tgt(op)))
+                        op = (op & 0xFFFF0000u) | 0x8000u | (uint32_t)slot[tgt(op)];
+                    jb.ops.push_back(op);
+                }
+                jobs.push_back(jb);
+            }
+            int4 rd;
+            rd.x = i | (recip << 16);
+            rd.y = (int)h.lred_off.size();
+            rd.z = ns | (nch << 16);
+            rd.w = lpart;
+            for (int t : shared) h.lred_off.push_back(t);
+            h.lred.push_back(rd.x); h.lred.push_back(rd.y); h.lred.push_back(rd.z); h.lred.push_back(rd.w);
+            // the tail's ops go after the level's jobs; until then x holds
+            // -1 - (the tail's first op within the row)
+            h.ltail.push_back(-1 - tail_from);
+            h.ltail.push_back((int)ops.size() - tail_from);
+            h.ltail_rows.push_back(i);
+            lpart += nch * ns;
+        }
+        h.n_lpart = std::max(h.n_lpart, lpart);
+        std::vector<int> idx(jobs.size());
+        for (size_t j = 0; j < jobs.size(); j++) idx[j] = (int)j;
+        balance_level(idx, 0, (int)idx.size(), NL, [&](int j) { return (int)jobs[j].ops.size() + 2; });
+        for (int j : idx) {
+            const Job &jb = jobs[j];
+            if (jb.ops.size() > 0xffff) throw std::runtime_error("factor job too long");
+            h.ljob.push_back((int)h.lops.size());
+            h.ljob.push_back((int)jb.ops.size() | (jb.ns << 16));
+            h.ljob.push_back(jb.row | (jb.recip << 16));
+            h.ljob.push_back(jb.pbase);
+            h.lops.insert(h.lops.end(), jb.ops.begin(), jb.ops.end());
+        }
+        h.ljob_ptr.push_back((int)h.ljob.size() / 4);
+        // the level's tails, stored after its jobs
+        for (size_t k = h.lred_ptr.back(); k < h.lred.size() / 4; k++) {
+            const int i = h.ltail_rows[k];
+            const int from = -1 - h.ltail[2 * k];
+            h.ltail[2 * k] = (int)h.lops.size();
+            h.lops.insert(h.lops.end(), h.fops.begin() + h.fops_ptr[i] + from, h.fops.begin() + h.fops_ptr[i + 1]);
+        }
+        h.lred_ptr.push_back((int)h.lred.size() / 4);
+    }
 }
 
 // ---- device tables -----------------------------------------------------------
@@ -487,26 +607,54 @@ static void build_tables(HostMech &h) {
         for (auto &e : fl[p]) { h.fk.push_back(e.first); h.fc.push_back(e.second); }
         h.fptr.push_back((int)h.fk.size());
     }
-    // longest-processing-time assignment of the per-position sums to 32 lanes
+    // the per-position sums over the lanes of one cell, longest processing
+    // time first; a sum longer than the lanes' mean load is cut into chunks
+    // whose partial sums a second pass adds in a fixed order
     {
-        std::vector<int> order(n);
-        for (int p = 0; p < n; p++) order[p] = p;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-            return h.fptr[a + 1] - h.fptr[a] > h.fptr[b + 1] - h.fptr[b];
-        });
-        std::vector<std::vector<int>> lanes(32);
-        std::vector<int> load(32, 0);
-        for (int p : order) {
+        const int NL = camp_cell_lanes(n);
+        long long total = 0;
+        for (int p = 0; p < n; p++) total += h.fptr[p + 1] - h.fptr[p] + 2;
+        // only block cells split (one-warp cells take no second pass)
+        const int CH = NL > 32 ? std::max(8, (int)((total + NL - 1) / NL)) : 1 << 30;
+        struct Job { int first, count, dst; };
+        std::vector<Job> jobs;
+        h.fsplit.clear();
+        h.n_fpart = 0;
+        for (int p = 0; p < n; p++) {
+            const int b = h.fptr[p], e = h.fptr[p + 1];
+            if (e - b <= CH) { jobs.push_back({b, e - b, p}); continue; }
+            const int nch = (e - b + CH - 1) / CH;
+            h.fsplit.push_back(p);
+            h.fsplit.push_back(h.n_fpart | (nch << 16));
+            for (int c = 0; c < nch; c++) {
+                const int cb = b + (int)((long long)c * (e - b) / nch), ce = b + (int)((long long)(c + 1) * (e - b) / nch);
+                jobs.push_back({cb, ce - cb, n + h.n_fpart + c});
+            }
+            h.n_fpart += nch;
+        }
+        std::vector<int> order(jobs.size());
+        for (size_t j = 0; j < jobs.size(); j++) order[j] = (int)j;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].count > jobs[b].count; });
+        std::vector<std::vector<int>> lanes(NL);
+        std::vector<long long> load(NL, 0);
+        for (int j : order) {
             int best = 0;
-            for (int l = 1; l < 32; l++)
+            for (int l = 1; l < NL; l++)
                 if (load[l] < load[best]) best = l;
-            lanes[best].push_back(p);
-            load[best] += h.fptr[p + 1] - h.fptr[p] + 2;  // entries plus the per-sum cost
+            lanes[best].push_back(j);
+            load[best] += jobs[j].count + 2;  // entries plus the per-sum cost
         }
         h.flane_ptr.assign(1, 0);
         h.flane_pos.clear();
+        h.fjob.clear();
         for (auto &v : lanes) {
-            for (int p : v) h.flane_pos.push_back(p);
+            for (int j : v) {
+                const Job &jb = jobs[j];
+                if (jb.dst > 0xffff || jb.count > 0xffff) throw std::runtime_error("forcing jobs do not fit 16-bit fields");
+                h.flane_pos.push_back(jb.dst);
+                h.fjob.push_back(jb.first);
+                h.fjob.push_back(jb.dst | (jb.count << 16));
+            }
             h.flane_ptr.push_back((int)h.flane_pos.size());
         }
     }
@@ -535,7 +683,6 @@ static void build_tables(HostMech &h) {
             if (h.lu_colidx[q] >= h.d) lu_off[q] = h.dbase + (i - h.d) * h.LD + (h.lu_colidx[q] - h.d);
     h.nlu = h.dbase + h.D * h.LD;
     if (h.nlu > 32767) throw std::runtime_error("LU storage too large for the packed tables (32767 values)");
-    if (h.nlu > 32767) throw std::runtime_error("LU storage exceeds 32767 entries");
     auto off = [&](int i, int j) {
         auto b = h.lu_colidx.begin() + h.lu_rowptr[i], e = h.lu_colidx.begin() + h.lu_rowptr[i + 1];
         auto it = std::lower_bound(b, e, j);
@@ -675,19 +822,58 @@ static void build_tables(HostMech &h) {
     // the factorisation's levels balanced by update count; the forward
     // substitution skips rows without L entries and balances by entry count
     for (size_t l = 0; l + 1 < h.flev_ptr.size(); l++)
-        balance_level(h.frow, h.flev_ptr[l], h.flev_ptr[l + 1],
+        balance_level(h.frow, h.flev_ptr[l], h.flev_ptr[l + 1], camp_cell_lanes(n),
                       [&](int i) { return h.fops_ptr[i + 1] - h.fops_ptr[i] + 1; });
-    h.slev_ptr.assign(1, 0);
-    h.srow.clear();
-    for (size_t l = 0; l + 1 < h.flev_ptr.size(); l++) {
-        for (int r = h.flev_ptr[l]; r < h.flev_ptr[l + 1]; r++) {
-            const int i = h.frow[r];
-            if (h.sl_ptr[i + 1] > h.sl_ptr[i]) h.srow.push_back(i);
+    build_factor_jobs(h);
+    // Forward substitution as lane jobs, level by level: a row longer than
+    // its level's mean load per lane is cut into chunks whose partial dot
+    // products a second pass subtracts in a fixed order.
+    {
+        const int NL = camp_cell_lanes(n);
+        h.slev_ptr.assign(1, 0);
+        h.sjob.clear();
+        h.ssplit_ptr.assign(1, 0);
+        h.ssplit.clear();
+        h.n_spart = 0;
+        struct Job { int first, count, dst; };
+        for (size_t l = 0; l + 1 < h.flev_ptr.size(); l++) {
+            std::vector<int> rows;
+            long long total = 0;
+            for (int r = h.flev_ptr[l]; r < h.flev_ptr[l + 1]; r++) {
+                const int i = h.frow[r];
+                if (h.sl_ptr[i + 1] > h.sl_ptr[i]) {
+                    rows.push_back(i);
+                    total += h.sl_ptr[i + 1] - h.sl_ptr[i] + 1;
+                }
+            }
+            if (rows.empty()) continue;
+            const int CH = NL > 32 ? std::max(16, (int)((total + NL - 1) / NL)) : 1 << 30;
+            std::vector<Job> jobs;
+            int np = 0;
+            for (int i : rows) {
+                const int b = h.sl_ptr[i], e = h.sl_ptr[i + 1];
+                if (e - b <= CH) { jobs.push_back({b, e - b, i}); continue; }
+                const int nch = (e - b + CH - 1) / CH;
+                h.ssplit.push_back(i);
+                h.ssplit.push_back(np | (nch << 16));
+                for (int c = 0; c < nch; c++) {
+                    const int cb = b + (int)((long long)c * (e - b) / nch), ce = b + (int)((long long)(c + 1) * (e - b) / nch);
+                    jobs.push_back({cb, ce - cb, n + np + c});
+                }
+                np += nch;
+            }
+            h.n_spart = std::max(h.n_spart, np);
+            std::vector<int> idx(jobs.size());
+            for (size_t j = 0; j < jobs.size(); j++) idx[j] = (int)j;
+            balance_level(idx, 0, (int)idx.size(), NL, [&](int j) { return jobs[j].count + 1; });
+            for (int j : idx) {
+                if (jobs[j].dst > 0xffff || jobs[j].count > 0xffff) throw std::runtime_error("substitution jobs do not fit 16-bit fields");
+                h.sjob.push_back(jobs[j].first);
+                h.sjob.push_back(jobs[j].dst | (jobs[j].count << 16));
+            }
+            h.slev_ptr.push_back((int)h.sjob.size() / 2);
+            h.ssplit_ptr.push_back((int)h.ssplit.size() / 2);
         }
-        if ((int)h.srow.size() == h.slev_ptr.back()) continue;
-        h.slev_ptr.push_back((int)h.srow.size());
-        const int b = h.slev_ptr[h.slev_ptr.size() - 2], e = h.slev_ptr.back();
-        balance_level(h.srow, b, e, [&](int i) { return h.sl_ptr[i + 1] - h.sl_ptr[i] + 1; });
     }
     std::vector<int> bl(n, 0);
     int maxb = -1;
@@ -706,7 +892,7 @@ static void build_tables(HostMech &h) {
         for (int i = 0; i < h.d; i++) if (bl[i] == l) h.brow.push_back(i);
         h.blev_ptr.push_back((int)h.brow.size());
         const int b = h.blev_ptr[h.blev_ptr.size() - 2], e = h.blev_ptr.back();
-        balance_level(h.brow, b, e, [&](int i) { return h.su_ptr[i + 1] - h.su_ptr[i] + 1; });
+        balance_level(h.brow, b, e, camp_cell_lanes(n), [&](int i) { return h.su_ptr[i + 1] - h.su_ptr[i] + 1; });
     }
 }
 
@@ -761,6 +947,7 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.n_env = h.n_env;
     dm.env_sec_base = h.env_sec_base;
     dm.npl32 = (h.n + 31) / 32;
+    dm.lanes = camp_cell_lanes(h.n);
     dm.rtype = pk.put(h.rtype);
     dm.rpar = pk.put(h.rpar);
     dm.rslot = pk.put(h.rslot);
@@ -792,10 +979,21 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.frow = pk.put(h.frow);
     dm.fops_ptr = pk.put(h.fops_ptr);
     dm.fops = pk.put(h.fops);
+    dm.ljob_ptr = pk.put(h.ljob_ptr);
+    dm.ljob = reinterpret_cast<const int4 *>(pk.put(h.ljob));
+    dm.lops = pk.put(h.lops);
+    dm.lred_ptr = pk.put(h.lred_ptr);
+    dm.lred = reinterpret_cast<const int4 *>(pk.put(h.lred));
+    dm.lred_off = pk.put(h.lred_off);
+    dm.ltail = reinterpret_cast<const int2 *>(pk.put(h.ltail));
     dm.sl_ptr = pk.put(h.sl_ptr);
     dm.n_slev = (int)h.slev_ptr.size() - 1;
     dm.slev_ptr = pk.put(h.slev_ptr);
-    dm.srow = pk.put(h.srow);
+    dm.sjob = reinterpret_cast<const int2 *>(pk.put(h.sjob));
+    dm.ssplit_ptr = pk.put(h.ssplit_ptr);
+    dm.ssplit = reinterpret_cast<const int2 *>(pk.put(h.ssplit));
+    // partials in doubles: the factor's are LU-precision values, at most 8 bytes
+    dm.n_part = std::max(std::max(h.n_fpart, h.n_spart), h.n_lpart);
     dm.sl_off = pk.put(h.sl_off);
     dm.sl_col = pk.put(h.sl_col);
     dm.n_blev = (int)h.blev_ptr.size() - 1;
@@ -810,6 +1008,8 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.fpk = pk.put(h.fpk);
     dm.fcoef = pk.put(h.fcoef);
     dm.fjob = reinterpret_cast<const int2 *>(pk.put(h.fjob));
+    dm.n_fsplit = (int)h.fsplit.size() / 2;
+    dm.fsplit = reinterpret_cast<const int2 *>(pk.put(h.fsplit));
     dm.jnz = reinterpret_cast<const int4 *>(pk.put(h.jnz));
     dm.jpack = reinterpret_cast<const int4 *>(pk.put(h.jpack));
     dm.sl_pack = pk.put(h.sl_pack);

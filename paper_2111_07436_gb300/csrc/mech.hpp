@@ -42,6 +42,8 @@ struct HostMech {
     std::vector<int> flane_ptr, flane_pos;
     std::vector<int> rpack, jnz, jpack, sl_pack, su_pack;  // int4 records as 4 ints
     std::vector<int> fpk, fjob;   // forcing gather entries and lane jobs (see DevMech)
+    std::vector<int> fsplit;      // split sums, 2 ints each (see DevMech)
+    int n_fpart = 0;
     std::vector<double> fcoef;
     std::vector<int> jl_ptr, jl_rec;
     std::vector<int> jptr, jdst, jdiag, jk, jo;
@@ -50,8 +52,14 @@ struct HostMech {
     int nlu = 0, d = 0, D = 0, LD = 0, dbase = 0;
     std::vector<int> flev_ptr, frow, fops_ptr;
     std::vector<uint32_t> fops;
+    // the factorisation as lane jobs (see DevMech)
+    std::vector<int> ljob_ptr, ljob, lred_ptr, lred, lred_off, ltail, ltail_rows;
+    std::vector<uint32_t> lops;
+    int n_lpart = 0;
     std::vector<int> sl_ptr, sl_off, sl_col;
-    std::vector<int> slev_ptr, srow;  // forward substitution: rows with L entries, by level
+    // forward substitution: lane jobs by level, split rows (see DevMech)
+    std::vector<int> slev_ptr, sjob, ssplit_ptr, ssplit;
+    int n_spart = 0;
     std::vector<int> blev_ptr, brow, su_ptr, su_off, su_col, udiag;
     long long factor_updates = 0;  // multiply-adds one device factorisation executes
     // algorithmic work of the method, from the symbolic structure
