@@ -107,11 +107,34 @@ def oracle_rate(wl, seconds, rank_seed=0):
     n = int(min(wl.n_cells, max(probe, seconds / max(per_cell, 1e-9))))
     idx = np.random.default_rng(rank_seed + 17).choice(wl.n_cells, n, replace=False)
     t = time.perf_counter()
-    _, st, _ = om.solve(y0[idx], env[idx], wl.dt, wl.rtol, wl.atol, threads=threads)
+    y_o, st, _ = om.solve(y0[idx], env[idx], wl.dt, wl.rtol, wl.atol, threads=threads)
     dt = time.perf_counter() - t
     return {"value": n * wl.n_outer / dt, "unit": "cell-steps/s", "cores": threads, "kind": "oracle",
             "sample": f"{n} of {wl.n_cells} cells (seeded random), {wl.n_outer} outer step(s), "
-                      f"{threads} threads, {dt:.1f} s", "ok_cells": int((st == 0).sum())}
+                      f"{threads} threads, {dt:.1f} s", "ok_cells": int((st == 0).sum()),
+            "_result": (idx, y_o, st)}
+
+
+def error_vs_oracle(y_gpu, sample, rtol, atol):
+    """GPU results against the oracle's on the sampled cells: relative error
+    over the species above atol in either (the parity rule's set), the same
+    over values above 100 atol, and the difference in units of the solver's
+    tolerance rtol |y| + atol over all species."""
+    import numpy as np
+    idx, y_o, st = sample
+    ok = st == 0
+    g, o = y_gpu[idx][ok], y_o[ok]
+    d = np.abs(g - o)
+    mask = np.maximum(np.abs(g), np.abs(o)) > atol
+    if not mask.any():
+        return None
+    rel = d[mask] / np.abs(o)[mask]
+    big = np.abs(o) > 100 * atol
+    tol = d / (rtol * np.abs(o) + atol)
+    return {"max_rel": float(rel.max()), "p99_rel": float(np.percentile(rel, 99)),
+            "median_rel": float(np.median(rel)), "values": int(rel.size),
+            "max_rel_above_100atol": float((d[big] / np.abs(o)[big]).max()) if big.any() else None,
+            "max_in_tol_units": float(tol.max()), "p99_in_tol_units": float(np.percentile(tol, 99))}
 
 
 # ----------------------------------------------------------------- main
@@ -138,9 +161,11 @@ def main():
         if rank != 0:
             return
         cpu = oracle_rate(wl, a.cpu_seconds)
+        cpu.pop("_result")
         steps_t = []
         for _ in range(a.warmup + a.steps):
             r = oracle_rate(wl, a.cpu_seconds / 2)
+            r.pop("_result")
             steps_t.append(r["value"])
         v = statistics.mean(steps_t[a.warmup:])
         cpu["value"] = v
@@ -221,6 +246,7 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(dev.index) as clk:
         times = run(variant, persistent, a.steps, a.warmup)
+    y_main = state.cpu().numpy()  # this form's result of the last timed step
     if dist:
         dist.barrier()
     _, t_max, value = replicas.aggregate(C * wl.n_outer * a.steps, sum(times) / 1e3, dist)
@@ -230,6 +256,7 @@ def main():
     plain = None
     if not a.no_plain and variant == camp.VARIANT_MIXED:
         pt = run(camp.VARIANT_FP64, False, max(1, a.steps // 2), 1)
+        y_plain = state.cpu().numpy()
         pms = sum(pt) / len(pt)
         plain = {"value": C * wl.n_outer / (pms / 1e3), "ms_per_step": pms, "form": "fp64 static grid"}
 
@@ -254,8 +281,15 @@ def main():
            "ok_cells": int((st_h == 0).sum())}
 
     cpu = None
+    err = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = oracle_rate(wl, a.cpu_seconds)
+        sample = cpu.pop("_result")
+        if wl.n_outer == 1:  # the oracle's sample covers one outer step
+            err = {"cells": int(len(sample[0])), "rule": "species above atol, relative to the FP64 oracle",
+                   a.variant: error_vs_oracle(y_main, sample, wl.rtol, wl.atol)}
+            if plain is not None:
+                err["fp64"] = error_vs_oracle(y_plain, sample, wl.rtol, wl.atol)
 
     if rank != 0:
         return
@@ -281,7 +315,8 @@ def main():
                     "per_s": {k: v * wl.n_outer * world / (ms / 1e3) for k, v in
                               (("bdf_steps", steps), ("newton_iters", newton), ("lu_setups", jac))}},
            "plain_fp64": plain, "mixed_over_plain": (value / world / plain["value"]) if plain else None,
-           "roofline": roof, "hbm_io_gbs": hbm, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary()}
+           "roofline": roof, "hbm_io_gbs": hbm, "e2e": e2e, "cpu_baseline": cpu,
+           "error_vs_oracle": err, "clocks": clk.summary()}
     print(json.dumps(out))
 
 

@@ -202,11 +202,11 @@ def test_atol_below_the_fp32_range(cuda, variant):
 
 
 @pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
-@pytest.mark.parametrize("n_particles,C", [(40, 96), (100, 12)])
+@pytest.mark.parametrize("n_particles,C", [(40, 96), (100, 12), (160, 6)])
 def test_particle_resolved_cells(form, n_particles, C):
     """The particle-resolved representation: one condensed-phase instance per
-    computational particle (298 and 718 species), integrated by a block of
-    64 or 128 threads per cell instead of one warp."""
+    computational particle (298, 718 and 1138 species), integrated by a block
+    of 64, 128 or 256 threads per cell instead of one warp."""
     mj = w.particle_resolved_mechanism(n_particles)
     text = json.dumps(mj)
     gm, om = camp.Mechanism(text), oracle.Mechanism(text)
