@@ -896,6 +896,102 @@ static void build_tables(HostMech &h) {
     }
 }
 
+// Bounds of every index the device tables hold, checked once per mechanism
+// on the host: the kernels index shared memory and the tables with these
+// values unchecked, so an out-of-range entry is a compiler bug caught here
+// (an exception naming the table) instead of a wrong access on the GPU.
+static void validate_tables(const HostMech &h) {
+    const int n = h.n, R = (int)h.procs.size(), nlu = h.nlu;
+    auto fail = [](const char *what) { throw std::runtime_error(std::string("internal table check failed: ") + what); };
+    auto in = [](long long v, long long lo, long long hi) { return v >= lo && v < hi; };
+    auto f16 = [](int v) { return v & 0xffff; };
+    auto h16 = [](int v) { return (int)((unsigned)v >> 16); };
+    const int NONE = 0xffff;
+    // permutation and rates
+    {
+        std::vector<int> seen(n, 0);
+        for (int p : h.perm) { if (!in(p, 0, n) || seen[p]++) fail("perm"); }
+        if ((int)h.perm.size() != n) fail("perm size");
+    }
+    for (int k = 0; k < R; k++) {
+        for (int c = 0; c < 6; c++) if (!in(h.rfac[6 * k + c], -1, n)) fail("rfac");
+        if (!in(h.rrev[k], -1, h.n_rev)) fail("rrev");
+        // fwd0 | fwd1, fwd2 | reverse-constant index, rev0 | rev1, rev2
+        for (int c = 0; c < 4; c++) {
+            const int w = h.rpack[4 * k + c];
+            const int lo = f16(w), hi = h16(w);
+            if (lo != NONE && !in(lo, 0, n)) fail("rpack");
+            if (c == 1 && hi != NONE && !in(hi, 0, h.n_rev)) fail("rpack");
+            if ((c == 0 || c == 2) && hi != NONE && !in(hi, 0, n)) fail("rpack");
+        }
+    }
+    // forcing gather
+    const int nf = (int)h.fk.size();
+    for (int q = 0; q < nf; q++)
+        if (!in(f16(h.fpk[q]), 0, R) || !in(h16(h.fpk[q]), 0, (int)h.fcoef.size())) fail("fpk");
+    const int nj = (int)h.fjob.size() / 2;
+    if (h.flane_ptr.front() != 0 || h.flane_ptr.back() != nj) fail("flane_ptr");
+    for (size_t l = 0; l + 1 < h.flane_ptr.size(); l++) if (h.flane_ptr[l] > h.flane_ptr[l + 1]) fail("flane_ptr order");
+    for (int i = 0; i < nj; i++) {
+        const int first = h.fjob[2 * i], dst = f16(h.fjob[2 * i + 1]), cnt = h16(h.fjob[2 * i + 1]);
+        if (!in(first, 0, nf + 1) || first + cnt > nf || !in(dst, 0, n + h.n_fpart)) fail("fjob");
+    }
+    for (size_t i = 0; i < h.fsplit.size() / 2; i++) {
+        const int pos = h.fsplit[2 * i], first = f16(h.fsplit[2 * i + 1]), cnt = h16(h.fsplit[2 * i + 1]);
+        if (!in(pos, 0, n) || first + cnt > h.n_fpart) fail("fsplit");
+    }
+    // Jacobian lists
+    const int nnzJ = (int)h.colidx.size();
+    for (size_t i = 0; i < h.jl_rec.size() / 4; i++) {
+        const int *r = &h.jl_rec[4 * i];
+        const int k = (int)(short)(r[1] & 0xffff), o1 = h16(r[1]), o2 = f16(r[3]), t = h16(r[3]);
+        if (!in(k, -h.n_rev, R) || (o1 != NONE && !in(o1, 0, n)) || (o2 != NONE && !in(o2, 0, n))) fail("jl_rec");
+        if (!in(r[2] & 0xffff, 0, nlu) || !in(t, 0, nnzJ)) fail("jl_rec target");
+    }
+    // LU: storage layout, factorisation jobs, substitution lists
+    if (h.dbase + h.D * h.LD > nlu || h.d + h.D != n) fail("dense block");
+    for (int i = 0; i < h.d; i++) if (!in(h.udiag[i], 0, nlu)) fail("udiag");
+    const int nops = (int)h.lops.size();
+    for (size_t j = 0; j < h.ljob.size() / 4; j++) {
+        const int *jb = &h.ljob[4 * j];
+        const int cnt = f16(jb[1]), ns = h16(jb[1]), row = f16(jb[2]);
+        if (jb[0] < 0 || jb[0] + cnt > nops || !in(row, 0, n) || (ns > 0 && jb[3] + ns > h.n_lpart))
+            fail("ljob");
+        for (int q = jb[0]; q < jb[0] + cnt; q++) {
+            const uint32_t op = h.lops[q];
+            const int t = (int)(op & 0xffffu), src = (int)((op >> 16) & 0x7fffu);
+            if (!in(src, 0, nlu)) fail("lops source");
+            if ((t & 0x8000) && !(op & CAMP_OP_DIV)) {
+                if (!in(jb[3] + (t & 0x7fff), 0, h.n_lpart) || (t & 0x7fff) >= ns) fail("lops partial");
+            } else if (!in(t, 0, nlu)) fail("lops target");
+        }
+    }
+    for (size_t k = 0; k < h.lred.size() / 4; k++) {
+        const int *rd = &h.lred[4 * k];
+        const int ns = f16(rd[2]), nch = h16(rd[2]);
+        if (!in(f16(rd[0]), 0, n) || rd[1] + ns > (int)h.lred_off.size() || rd[3] + ns * nch > h.n_lpart) fail("lred");
+        for (int s2 = 0; s2 < ns; s2++) if (!in(h.lred_off[rd[1] + s2], 0, nlu)) fail("lred_off");
+        if (h.ltail[2 * k] < 0 || h.ltail[2 * k] + h.ltail[2 * k + 1] > nops) fail("ltail");
+        for (int q = h.ltail[2 * k]; q < h.ltail[2 * k] + h.ltail[2 * k + 1]; q++)
+            if ((h.lops[q] & 0x8000u) && !(h.lops[q] & CAMP_OP_DIV)) fail("tail op with a partial target");
+    }
+    auto check_pack = [&](const std::vector<int> &pk, const char *what) {
+        for (int w : pk) if (!in(f16(w), 0, nlu) || !in(h16(w), 0, n)) fail(what);
+    };
+    check_pack(h.sl_pack, "sl_pack");
+    check_pack(h.su_pack, "su_pack");
+    const int nsl = (int)h.sl_pack.size();
+    for (size_t r = 0; r < h.sjob.size() / 2; r++) {
+        const int first = h.sjob[2 * r], dst = f16(h.sjob[2 * r + 1]), cnt = h16(h.sjob[2 * r + 1]);
+        if (first < 0 || first + cnt > nsl || !in(dst, 0, n + h.n_spart)) fail("sjob");
+    }
+    for (size_t k = 0; k < h.ssplit.size() / 2; k++)
+        if (!in(h.ssplit[2 * k], 0, n) || f16(h.ssplit[2 * k + 1]) + h16(h.ssplit[2 * k + 1]) > h.n_spart) fail("ssplit");
+    for (int i : h.brow) if (!in(i, 0, h.d)) fail("brow");
+    for (int i = 0; i < n; i++)
+        if (h.su_ptr[i] > h.su_ptr[i + 1] || h.sl_ptr[i] > h.sl_ptr[i + 1]) fail("substitution pointers");
+}
+
 HostMech compile_mechanism(const char *json, size_t len) {
     Value root = campjson::parse(json, len);
     HostMech h;
@@ -904,6 +1000,7 @@ HostMech compile_mechanism(const char *json, size_t len) {
     build_structure(h);
     build_tables(h);
     pack_records(h);
+    validate_tables(h);
     return h;
 }
 
