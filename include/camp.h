@@ -52,6 +52,7 @@ extern "C" {
 #define CAMP_E_UNSUPPORTED (-5) /* mechanism too large for the device kernels */
 #define CAMP_E_BUDGET (-6)      /* request larger than the server's memory budget */
 #define CAMP_E_TIMEOUT (-7)     /* bounded wait expired */
+#define CAMP_E_CANCELLED (-8)   /* request cancelled before it reached the GPU */
 
 /* ---- per-cell status ---------------------------------------------------- */
 #define CAMP_CELL_OK 0          /* integrated to dt */
@@ -351,6 +352,15 @@ int camp_server_wait(camp_server *s, uint64_t req_id, int32_t timeout_ms, camp_r
 
 /* Queue depth, chunks on the device and budget bytes in use. */
 int camp_server_stats(camp_server *s, int32_t *pending, int32_t *inflight, size_t *bytes_in_use);
+
+/* Withdraw a request that is still waiting for admission (a host model
+ * that has moved on, or is shutting down, no longer needs it): it finishes
+ * at once with rc CAMP_E_CANCELLED, its state and status arrays untouched,
+ * and is collected by poll/wait like any other.  Returns CAMP_OK; a request
+ * already on the GPU or finished cannot be withdrawn (CAMP_E_UNSUPPORTED; it
+ * completes normally); an unknown id gives CAMP_E_INVAL.  Not in the paper:
+ * part of the serving loop this library adds. */
+int camp_server_cancel(camp_server *s, uint64_t req_id);
 
 /* Finish every queued and in-flight chunk, then release the server. */
 int camp_server_destroy(camp_server *s);

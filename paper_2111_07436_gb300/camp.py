@@ -68,13 +68,16 @@ class RequestInfo(ctypes.Structure):
 
 
 E_TIMEOUT = -7
+E_CANCELLED = -8
+E_UNSUPPORTED = -5
 E_BUDGET = -6
 
 EXPORTS = ["camp_mech_load", "camp_mech_compile", "camp_mech_free", "camp_mech_info_get", "camp_mech_species_index",
            "camp_mech_structure", "camp_solve_opts_default", "camp_workspace_bytes", "camp_solve",
            "camp_solve_host", "camp_rate_constants", "camp_forcing", "camp_jacobian",
            "camp_lu_solve", "camp_last_error", "camp_server_create", "camp_server_submit",
-           "camp_server_poll", "camp_server_wait", "camp_server_stats", "camp_server_destroy",
+           "camp_server_poll", "camp_server_wait", "camp_server_stats", "camp_server_cancel",
+           "camp_server_destroy",
            "camp_solve_batch", "camp_autotune", "camp_probe_fma_rate", "camp_solve_host_static"]
 
 
@@ -113,6 +116,7 @@ def lib():
     L.camp_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32), ctypes.POINTER(RequestInfo)]
     L.camp_server_wait.argtypes = [vp, ctypes.c_uint64, i32, ctypes.POINTER(RequestInfo)]
     L.camp_server_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_size_t)]
+    L.camp_server_cancel.argtypes = [vp, ctypes.c_uint64]
     L.camp_server_destroy.argtypes = [vp]
     L.camp_solve_batch.argtypes = [ctypes.POINTER(Group), i32, dbl, dbl, ctypes.POINTER(SolveOpts), vp]
     L.camp_autotune.argtypes = [vp, i64, vp, vp, dbl, dbl, vp, i32, i32, ctypes.POINTER(i32),
@@ -358,6 +362,16 @@ class Server:
             return None
         self._keep.pop(rid, None)
         return info.as_dict()
+
+    def cancel(self, rid):
+        """Withdraw a request still waiting for admission: True if withdrawn
+        (it then finishes with rc E_CANCELLED), False if already on the GPU
+        or finished."""
+        rc = lib().camp_server_cancel(self._h, rid)
+        if rc == E_UNSUPPORTED:
+            return False
+        _check(rc)
+        return True
 
     def stats(self):
         p, i, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()

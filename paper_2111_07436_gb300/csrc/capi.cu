@@ -260,6 +260,7 @@ size_t camp_workspace_bytes(void) { return 256; }
 int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double *env, double dt,
                double rtol, const double *atol, int32_t atol_len, int32_t *status,
                const camp_solve_opts *opts, void *stream) {
+    CampRange range_("camp_solve");
     camp_mech *m = const_cast<camp_mech *>(mc);
     if (!m) return fail(CAMP_E_INVAL, "NULL mechanism");
     if (n_cells < 0) return fail(CAMP_E_INVAL, "n_cells < 0");
@@ -351,6 +352,7 @@ int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double
 int camp_solve_host(const camp_mech *mc, int64_t n_cells, double *state, const double *env,
                     double dt, double rtol, const double *atol, int32_t atol_len, int32_t *status,
                     const camp_solve_opts *opts, void *stream) {
+    CampRange range_("camp_solve_host");
     camp_mech *m = const_cast<camp_mech *>(mc);
     if (!m) return fail(CAMP_E_INVAL, "NULL mechanism");
     if (n_cells <= 0) return n_cells == 0 ? CAMP_OK : fail(CAMP_E_INVAL, "n_cells < 0");
@@ -404,6 +406,7 @@ int camp_solve_host(const camp_mech *mc, int64_t n_cells, double *state, const d
 
 int camp_solve_batch(const camp_group *groups, int32_t n_groups, double dt, double rtol,
                      const camp_solve_opts *opts, void *stream) {
+    CampRange range_("camp_solve_batch");
     if (!groups || n_groups < 0 || n_groups > CAMP_MAX_GROUPS) return fail(CAMP_E_INVAL, "bad group count");
     if (n_groups == 0) return CAMP_OK;
     // estimated work: cells x (per-cell f flops + LU solve flops), heaviest first
@@ -456,6 +459,7 @@ int camp_solve_batch(const camp_group *groups, int32_t n_groups, double dt, doub
 int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const double *env, double dt,
                   double rtol, const double *atol, int32_t atol_len, int32_t variant, int32_t *best_cpb,
                   int32_t *best_persistent, double *ms_best, void *stream) {
+    CampRange range_("camp_autotune");
     if (!m || n_cells <= 0 || !state || !env || !atol) return fail(CAMP_E_INVAL, "bad argument");
     if (variant != CAMP_VARIANT_MIXED && variant != CAMP_VARIANT_FP64) return fail(CAMP_E_INVAL, "unknown variant");
     if (int rc = check_device(m)) return rc;

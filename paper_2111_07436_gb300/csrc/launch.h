@@ -6,6 +6,17 @@
 
 #include "devmech.h"
 
+#include <nvtx3/nvToolsExt.h>
+
+// A named range on the profiler timeline for the life of a scope (NVTX;
+// free when no profiler is attached)
+struct CampRange {
+    explicit CampRange(const char *name) { nvtxRangePushA(name); }
+    ~CampRange() { nvtxRangePop(); }
+    CampRange(const CampRange &) = delete;
+    CampRange &operator=(const CampRange &) = delete;
+};
+
 struct SolveArgs {
     long long n_cells;
     double *state;

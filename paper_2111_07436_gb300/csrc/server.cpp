@@ -11,6 +11,7 @@
 // on the device for the server's life.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -21,6 +22,7 @@
 #include <vector>
 
 #include "camp.h"
+#include "launch.h"
 
 namespace {
 
@@ -75,6 +77,7 @@ struct camp_server {
     }
 
     void issue(Request *r) {
+        CampRange range_("camp_server: stage and launch a chunk");
         cudaStream_t s = streams[r->slot];
         const size_t bs = (size_t)r->n_cells * r->n * 8, be = (size_t)r->n_cells * r->n_env * 8;
         const size_t bst = (size_t)r->n_cells * 4;
@@ -264,6 +267,25 @@ int camp_server_wait(camp_server *s, uint64_t id, int32_t timeout_ms, camp_reque
             return CAMP_E_TIMEOUT;
     }
     return finish_locked(s, id, info);
+}
+
+int camp_server_cancel(camp_server *s, uint64_t id) {
+    if (!s) return CAMP_E_INVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->all.find(id);
+        if (it == s->all.end()) return CAMP_E_INVAL;
+        Request *r = it->second;
+        auto pos = std::find(s->pending.begin(), s->pending.end(), r);
+        if (pos == s->pending.end()) return CAMP_E_UNSUPPORTED;  // admitted or finished
+        s->pending.erase(pos);
+        r->info.rc = CAMP_E_CANCELLED;
+        r->info.t_admit = r->info.t_done = now_s() - s->t0;
+        r->finished = true;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_one();
+    return CAMP_OK;
 }
 
 int camp_server_stats(camp_server *s, int32_t *pending, int32_t *inflight, size_t *bytes_in_use) {

@@ -76,3 +76,23 @@ def test_budget_and_bounded_wait(mechs):
     assert ib["t_admit"] >= ia["t_done"] - 1e-3  # budget forced b to wait for a
     assert np.array_equal(a[0].numpy(), b[0].numpy())
     srv.close()
+
+
+def test_cancel_withdraws_only_pending_requests(mechs):
+    wl, gm = mechs[2]
+    srv = camp.Server(hbm_budget_bytes=4 << 30, max_inflight=1)
+    jobs = []
+    for i, C in enumerate((20000, 500, 500)):  # one slot: the last two wait behind the first
+        y, env = w.cells(wl.mech, C, seed=950 + i)
+        ty, te, ts = _pinned(y.copy()), _pinned(env), _pinned(np.full(C, -1, dtype=np.int32))
+        jobs.append((srv.submit(gm, ty, te, wl.dt, wl.rtol, wl.atol, ts), y, ty, ts))
+    assert srv.cancel(jobs[2][0])
+    info = srv.wait(jobs[2][0])
+    assert info["rc"] == camp.E_CANCELLED
+    assert np.array_equal(jobs[2][2].numpy(), jobs[2][1]) and (jobs[2][3].numpy() == -1).all()
+    for rid, y, ty, ts in jobs[:2]:
+        assert srv.wait(rid)["rc"] == 0
+        assert (ts.numpy() == 0).all()
+    with pytest.raises(camp.CampError):  # collected: no longer known
+        srv.cancel(jobs[0][0])
+    srv.close()
