@@ -439,32 +439,23 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
             return;
         }
     }
-    for (int t = lane; t < m.nnzJ; t += G) {
-        LT acc = (LT)0;
-        const int4 nz = __ldg(m.jnz + t);
-        for (int q = nz.x; q < nz.y; q++) {
-            LT v;
-            int k, oo;
-            if constexpr (sizeof(LT) == 4) {
-                const int4 je = __ldg(m.jpack + q);
-                k = je.y;
-                oo = je.z;
-                v = __int_as_float(je.x);
-            } else {
-                k = __ldg(m.jk + q);
-                oo = lo16(__ldg(m.jo + 2 * q)) | (lo16(__ldg(m.jo + 2 * q + 1)) << 16);
-                v = (LT)__ldg(m.jc + q);
+    if constexpr (sizeof(LT) == 8) {  // FP64: one non-zero per lane at a time
+        for (int t = lane; t < m.nnzJ; t += G) {
+            LT acc = (LT)0;
+            const int4 nz = __ldg(m.jnz + t);
+            for (int q = nz.x; q < nz.y; q++) {
+                const int k = __ldg(m.jk + q);
+                LT v = (LT)__ldg(m.jc + q) * (k >= 0 ? kfv[k] : krv[-k - 1]);
+                const int o1 = __ldg(m.jo + 2 * q), o2 = __ldg(m.jo + 2 * q + 1);
+                if (o1 >= 0) v *= yv[o1];
+                if (o2 >= 0) v *= yv[o2];
+                acc += v;
             }
-            v *= (k >= 0 ? kfv[k] : krv[-k - 1]);
-            const int o1 = lo16(oo), o2 = hi16(oo);
-            if (o1 != NONE16) v *= yv[o1];
-            if (o2 != NONE16) v *= yv[o2];
-            acc += v;
+            if (mode == 0)
+                c.lu[nz.z] = (nz.w ? (LT)1 : (LT)0) - g * acc;
+            else
+                out[t] = (double)acc;
         }
-        if (mode == 0)
-            c.lu[nz.z] = (nz.w ? (LT)1 : (LT)0) - g * acc;
-        else
-            out[t] = (double)acc;
     }
     gsync<G>(gm);
 }

@@ -48,7 +48,6 @@ struct DevMech {
     int R;            // process instances
     int n_env;
     int env_sec_base; // env index of section 0's radius
-    int npl32;        // ceil(n / 32)
     int lanes;        // lanes per cell the per-lane tables were built for
 
     // --- rate constants (process order) ---
@@ -57,61 +56,46 @@ struct DevMech {
     const int *rslot;     // [R] env slot (runtime types) or section (section types)
     const int *rnr;       // [R] total reactant multiplicity
     const int *rnp;       // [R] total product multiplicity (reversible types)
-
-    // --- rate terms r_k = kf prod(fwd) - kr prod(rev), positions, -1 = none ---
-    const int *rfac;      // [R][6]: 3 forward then 3 reverse
     int n_rev;            // reversible processes (the only ones with a kr)
     const int *rrev;      // [R] index into the cell's kr array, -1 if irreversible
 
-    // --- forcing gather, by position ---
-    const int *fptr;      // [n+1]
-    const int *fk;        // [nf] process index
-    const double *fc;     // [nf] net stoichiometric coefficient
-    // positions each of the 32 lanes sums, balanced by gather length
-    const int *flane_ptr; // [33]
-    const int *flane_pos; // [jobs] each job's destination (host reference)
-
-    // --- the same tables packed so one 16-byte load serves one record ---
-    // rate term k: x = fwd0 | fwd1 << 16, y = fwd2 | rv << 16,
-    //              z = rev0 | rev1 << 16, w = rev2  (16-bit fields, 0xffff = none)
+    // --- rate terms r_k = kf prod(fwd) - kr prod(rev), one 16-byte record each:
+    // x = fwd0 | fwd1 << 16, y = fwd2 | rv << 16, z = rev0 | rev1 << 16,
+    // w = rev2 (positions; 16-bit fields, 0xffff = none; rv = kr index)
     const int4 *rpack;    // [R]
-    // gather entry q: process | index into fcoef << 16
+
+    // --- forcing gather f_p = sum_q c_q r_k(q), as lane jobs ---
+    // entry q: process | index into fcoef << 16
     const int *fpk;       // [nf]
     const double *fcoef;  // the mechanism's distinct net coefficients
-    // lane job i: x = first entry, y = destination | entry count << 16; a
-    // destination d < n is the position's f, d >= n the partial sum d - n of
-    // a position whose sum was split into chunks
-    const int2 *fjob;     // lanes' jobs in flane_ptr ranges
-    int n_part;           // partial sums of split forcing sums and substitution
-                          // rows (FP64 scratch after the rate terms)
+    // lane l's jobs: flane_ptr[l] .. flane_ptr[l+1], balanced by entry count.
+    // Job: x = first entry, y = destination | entry count << 16; a destination
+    // d < n is the position's f, d >= n the partial sum d - n of a position
+    // whose sum was split into chunks (block cells only)
+    const int *flane_ptr; // [lanes+1]
+    const int2 *fjob;
+    int n_part;           // partial sums of split forcing sums, substitution
+                          // rows and factorisation rows (scratch after the
+                          // rate terms; counted in FP64 values)
     int n_fsplit;         // positions whose sums are split
     // split position i: x = position, y = first partial | chunk count << 16
     const int2 *fsplit;   // [n_fsplit]
-    // Jacobian non-zero t: x = first entry, y = end entry, z = LU offset, w = diagonal
-    const int4 *jnz;      // [nnzJ]
-    // Jacobian entry q: x = bits of the FP32 coefficient, y = constant index
-    // (k, or -(r+1) for a reverse constant), z = o1 | o2 << 16
-    const int4 *jpack;    // [nj]
-    // FP32 Jacobian assembly: per-lane flat entry lists (nonzeros spread
-    // over 32 lanes by entry count).  Record: x = bits of the FP32
-    // coefficient, y = k (signed 16 bits; -(r+1) for a reverse constant)
-    // | o1 << 16, z = LU offset | diag << 16 | last-entry-of-nonzero << 17,
-    // w = o2 | CSR index << 16
-    const int *jl_ptr;    // [33]
-    const int4 *jl_rec;   // [entries + empty non-zeros]
-    // substitution entries: off | col << 16
-    const int *sl_pack;   // [len(sl_off)]
-    const int *su_pack;   // [len(su_off)]
 
-    // --- Jacobian gather, by Jacobian non-zero ---
+    // --- Jacobian, assembled straight into I - gamma J ---
     int nnzJ;
-    const int *jptr;      // [nnzJ+1]
-    const int *jdst;      // [nnzJ] LU storage offset; the diagonal is flagged by jdiag
-    const int *jdiag;     // [nnzJ] 1 on the diagonal
-    const int *jk;        // [nj] process k (forward constant) or -(r+1), r = rrev[k] (reverse)
-    const int *jo;        // [nj][2] other factor positions, -1 = none
-    const double *jc;     // [nj] coefficient (net stoich x multiplicity, signed)
-    const float *jc32;    // [nj] the same coefficients in FP32 (mixed form)
+    // FP32: per-lane flat entry lists (nonzeros spread over the lanes by
+    // entry count).  Record: x = bits of the FP32 coefficient, y = k (signed
+    // 16 bits; -(r+1) for a reverse constant) | o1 << 16, z = LU offset |
+    // diag << 16 | last-entry-of-nonzero << 17, w = o2 | CSR index << 16
+    const int *jl_ptr;    // [lanes+1]
+    const int4 *jl_rec;   // [entries + empty non-zeros]
+    // FP64: by non-zero t: x = first entry, y = end entry, z = LU offset,
+    // w = diagonal; entry q: constant jk (k, or -(r+1) for a reverse constant),
+    // other factors jo (positions, -1 = none), coefficient jc
+    const int4 *jnz;      // [nnzJ]
+    const int *jk;        // [nj]
+    const int *jo;        // [nj][2]
+    const double *jc;     // [nj]
 
     // --- LU storage: sparse rows [0, nsp) then a dense trailing block ---
     int nlu;              // storage entries
@@ -120,20 +104,18 @@ struct DevMech {
     int LD;               // dense block row stride (odd, to spread shared-memory banks)
     int dbase;            // storage offset of the dense block
 
-    // factorisation of the sparse part, row by row (up-looking), by level
+    // factorisation of the sparse part: row-wise (up-looking) ops as lane
+    // jobs, by level.  Op: DIV flag | source << 16 | target (LU offsets; a
+    // division makes the multiplier, an update subtracts it times the
+    // source).  Job: x = first op in lops, y = op count | partial slots << 16,
+    // z = row | (1 << 16 if the job ends by taking the row's pivot
+    // reciprocal), w = partial base.  An update whose target has bit 15 set
+    // adds to partial w + (target & 0x7fff) instead of the LU value.  Per
+    // level, the rows cut into chunks then get a reduction (x = row |
+    // reciprocal flag << 16, y = first entry of lred_off, z = shared columns
+    // ns | chunks << 16, w = partial base; chunk c's slot s is w + c ns + s)
+    // and their tail ops (x = first op, y = count).
     int n_flev;
-    const int *flev_ptr;  // [n_flev+1] into frow
-    const int *frow;      // rows (positions)
-    const int *fops_ptr;  // [n+1]
-    const uint32_t *fops; // encoded DIV/UPD ops, row by row
-    // the same ops as lane jobs, by level (flev levels).  Job: x = first op in
-    // lops, y = op count | partial slots << 16, z = row | (1 << 16 if the job
-    // ends by taking the row's pivot reciprocal), w = partial base.  An update
-    // whose target has bit 15 set adds to partial w + (target & 0x7fff)
-    // instead of the LU value.  Per level, the rows cut into chunks then get
-    // a reduction (x = row | reciprocal flag << 16, y = first entry of
-    // lred_off, z = shared columns ns | chunks << 16, w = partial base; chunk
-    // c's slot s is w + c ns + s) and their tail ops (x = first op, y = count).
     const int *ljob_ptr;  // [n_flev+1] into ljob
     const int4 *ljob;
     const uint32_t *lops;
@@ -142,29 +124,28 @@ struct DevMech {
     const int *lred_off;  // LU offsets of the shared columns
     const int2 *ltail;
 
+    // substitution entries: LU offset | column << 16
+    const int *sl_pack;   // L entries of the sparse rows, row by row
+    const int *su_pack;   // U entries of the sparse rows, row by row
+
     // forward substitution of the sparse part: lane jobs by level (jobs
     // within a level ordered to balance the lanes) over the rows that have L
-    // entries.  Job: x = first entry, y = destination | entry count << 16; a
-    // destination d < n is row d, finished by the job, d >= n the partial
-    // dot product d - n of a row cut into chunks; the level's split rows
-    // (x = row, y = first partial | chunk count << 16) then subtract their
-    // partials in order.
+    // entries.  Job: x = first entry of sl_pack, y = destination | entry count
+    // << 16; a destination d < n is row d, finished by the job, d >= n the
+    // partial dot product d - n of a row cut into chunks; the level's split
+    // rows (x = row, y = first partial | chunk count << 16) then subtract
+    // their partials in order.
     int n_slev;
     const int *slev_ptr;  // [n_slev+1] into sjob
     const int2 *sjob;
     const int *ssplit_ptr; // [n_slev+1] into ssplit
     const int2 *ssplit;
-    const int *sl_ptr;    // [n+1]
-    const int *sl_off;    // storage offset of L(i,k)
-    const int *sl_col;    // k
 
     // backward substitution of the sparse rows (i < d), by level
     int n_blev;
     const int *blev_ptr;  // [n_blev+1] into brow
     const int *brow;
-    const int *su_ptr;    // [n+1]
-    const int *su_off;    // storage offset of U(i,j), j > i
-    const int *su_col;    // j
+    const int *su_ptr;    // [n+1] into su_pack
     const int *udiag;     // [n] storage offset of U(i,i) for sparse rows
 
     const int *perm;      // [n] position -> species (declaration order)

@@ -271,15 +271,6 @@ static void pack_records(HostMech &h) {
         h.jnz[(size_t)t * 4 + 2] = h.jdst[t];
         h.jnz[(size_t)t * 4 + 3] = h.jdiag[t];
     }
-    h.jpack.assign(h.jk.size() * 4, 0);
-    for (size_t q = 0; q < h.jk.size(); q++) {
-        float c = (float)h.jc[q];
-        int cb;
-        std::memcpy(&cb, &c, 4);
-        h.jpack[q * 4 + 0] = cb;
-        h.jpack[q * 4 + 1] = h.jk[q];
-        h.jpack[q * 4 + 2] = field16(h.jo[2 * q]) | (field16(h.jo[2 * q + 1]) << 16);
-    }
     // per-lane flat Jacobian entry lists, longest-processing-time over the lanes
     {
         const int NL = camp_cell_lanes(n);
@@ -745,7 +736,6 @@ static void build_tables(HostMech &h) {
             }
             h.jptr.push_back((int)h.jk.size());
         }
-    h.jc32.assign(h.jc.begin(), h.jc.end());
 
     // sparse factorisation ops, row by row; levels: sparse rows by level, then
     // every block row in one final level (they only need sparse pivots)
@@ -1043,39 +1033,25 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.R = (int)h.procs.size();
     dm.n_env = h.n_env;
     dm.env_sec_base = h.env_sec_base;
-    dm.npl32 = (h.n + 31) / 32;
     dm.lanes = camp_cell_lanes(h.n);
     dm.rtype = pk.put(h.rtype);
     dm.rpar = pk.put(h.rpar);
     dm.rslot = pk.put(h.rslot);
     dm.rnr = pk.put(h.rnr);
     dm.rnp = pk.put(h.rnp);
-    dm.rfac = pk.put(h.rfac);
     dm.n_rev = h.n_rev;
     dm.rrev = pk.put(h.rrev);
-    dm.fptr = pk.put(h.fptr);
-    dm.fk = pk.put(h.fk);
-    dm.fc = pk.put(h.fc);
     dm.flane_ptr = pk.put(h.flane_ptr);
-    dm.flane_pos = pk.put(h.flane_pos);
     dm.nnzJ = (int)h.colidx.size();
-    dm.jptr = pk.put(h.jptr);
-    dm.jdst = pk.put(h.jdst);
-    dm.jdiag = pk.put(h.jdiag);
     dm.jk = pk.put(h.jk);
     dm.jo = pk.put(h.jo);
     dm.jc = pk.put(h.jc);
-    dm.jc32 = pk.put(h.jc32);
     dm.nlu = h.nlu;
     dm.d = h.d;
     dm.D = h.D;
     dm.LD = h.LD;
     dm.dbase = h.dbase;
     dm.n_flev = (int)h.flev_ptr.size() - 1;
-    dm.flev_ptr = pk.put(h.flev_ptr);
-    dm.frow = pk.put(h.frow);
-    dm.fops_ptr = pk.put(h.fops_ptr);
-    dm.fops = pk.put(h.fops);
     dm.ljob_ptr = pk.put(h.ljob_ptr);
     dm.ljob = reinterpret_cast<const int4 *>(pk.put(h.ljob));
     dm.lops = pk.put(h.lops);
@@ -1083,7 +1059,6 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.lred = reinterpret_cast<const int4 *>(pk.put(h.lred));
     dm.lred_off = pk.put(h.lred_off);
     dm.ltail = reinterpret_cast<const int2 *>(pk.put(h.ltail));
-    dm.sl_ptr = pk.put(h.sl_ptr);
     dm.n_slev = (int)h.slev_ptr.size() - 1;
     dm.slev_ptr = pk.put(h.slev_ptr);
     dm.sjob = reinterpret_cast<const int2 *>(pk.put(h.sjob));
@@ -1091,14 +1066,10 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.ssplit = reinterpret_cast<const int2 *>(pk.put(h.ssplit));
     // partials in doubles: the factor's are LU-precision values, at most 8 bytes
     dm.n_part = std::max(std::max(h.n_fpart, h.n_spart), h.n_lpart);
-    dm.sl_off = pk.put(h.sl_off);
-    dm.sl_col = pk.put(h.sl_col);
     dm.n_blev = (int)h.blev_ptr.size() - 1;
     dm.blev_ptr = pk.put(h.blev_ptr);
     dm.brow = pk.put(h.brow);
     dm.su_ptr = pk.put(h.su_ptr);
-    dm.su_off = pk.put(h.su_off);
-    dm.su_col = pk.put(h.su_col);
     dm.udiag = pk.put(h.udiag);
     dm.perm = pk.put(h.perm);
     dm.rpack = reinterpret_cast<const int4 *>(pk.put(h.rpack));
@@ -1108,7 +1079,6 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.n_fsplit = (int)h.fsplit.size() / 2;
     dm.fsplit = reinterpret_cast<const int2 *>(pk.put(h.fsplit));
     dm.jnz = reinterpret_cast<const int4 *>(pk.put(h.jnz));
-    dm.jpack = reinterpret_cast<const int4 *>(pk.put(h.jpack));
     dm.sl_pack = pk.put(h.sl_pack);
     dm.jl_ptr = pk.put(h.jl_ptr);
     dm.jl_rec = reinterpret_cast<const int4 *>(pk.put(h.jl_rec));

@@ -40,7 +40,7 @@ struct HostMech {
     std::vector<int> fptr, fk;
     std::vector<double> fc;
     std::vector<int> flane_ptr, flane_pos;
-    std::vector<int> rpack, jnz, jpack, sl_pack, su_pack;  // int4 records as 4 ints
+    std::vector<int> rpack, jnz, sl_pack, su_pack;  // int4 records as 4 ints
     std::vector<int> fpk, fjob;   // forcing gather entries and lane jobs (see DevMech)
     std::vector<int> fsplit;      // split sums, 2 ints each (see DevMech)
     int n_fpart = 0;
@@ -48,7 +48,6 @@ struct HostMech {
     std::vector<int> jl_ptr, jl_rec;
     std::vector<int> jptr, jdst, jdiag, jk, jo;
     std::vector<double> jc;
-    std::vector<float> jc32;
     int nlu = 0, d = 0, D = 0, LD = 0, dbase = 0;
     std::vector<int> flev_ptr, frow, fops_ptr;
     std::vector<uint32_t> fops;
