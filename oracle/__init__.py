@@ -51,6 +51,9 @@ def lib():
         L.om_rate_constants.argtypes = [mp, _dp, _dp, _dp]
         L.om_forcing.argtypes = [mp, _dp, _dp, _dp, _dp]
         L.om_jacobian.argtypes = [mp, _dp, _dp, _dp, _dp]
+        L.om_forcing_env.argtypes = [mp, _dp, _dp, _dp, _dp, _dp]
+        L.om_jacobian_env.argtypes = [mp, _dp, _dp, _dp, _dp, _dp]
+        L.om_water.argtypes = [mp, _dp, _dp, _dp]
         L.om_lu_factor.argtypes = [ctypes.c_int, _dp, _ip]
         L.om_lu_factor.restype = ctypes.c_int
         L.om_lu_solve.argtypes = [ctypes.c_int, _dp, _ip, _dp]
@@ -129,15 +132,40 @@ class Mechanism:
         lib().om_rate_constants(self._ptr, _p(env), _p(kf), _p(kr))
         return kf, kr
 
-    def forcing(self, kf, kr, y):
+    @property
+    def has_water(self):
+        """True when a ZSR water parameter makes the sections' liquid volume a
+        function of the state (then forcing and jacobian need the cell's env)."""
+        return bool(self.m.electrolytes)
+
+    def _env_for(self, env):
+        if env is None:
+            if self.has_water:
+                raise ValueError("a mechanism with a water parameter needs the cell's env")
+            return np.zeros(max(1, self.n_env))
+        return _f64(env)
+
+    def forcing(self, kf, kr, y, env=None):
+        """f(y) from the rate constants (and, with a water parameter, the
+        cell's env for the liquid volume at y)."""
         f = np.zeros(self.n)
-        lib().om_forcing(self._ptr, _p(_f64(kf)), _p(_f64(kr)), _p(_f64(y)), _p(f))
+        lib().om_forcing_env(self._ptr, _p(self._env_for(env)), _p(_f64(kf)), _p(_f64(kr)),
+                             _p(_f64(y)), _p(f))
         return f
 
-    def jacobian(self, kf, kr, y):
+    def jacobian(self, kf, kr, y, env=None):
+        """df/dy, dense [n, n]; with a water parameter the chain-rule term of
+        Sect. 2.2.2 is included."""
         J = np.zeros((self.n, self.n))
-        lib().om_jacobian(self._ptr, _p(_f64(kf)), _p(_f64(kr)), _p(_f64(y)), _p(J))
+        lib().om_jacobian_env(self._ptr, _p(self._env_for(env)), _p(_f64(kf)), _p(_f64(kr)),
+                              _p(_f64(y)), _p(J))
         return J
+
+    def water(self, env, y):
+        """Liquid volume of every section at y [m^3 per m^3 air]."""
+        L = np.zeros(max(1, self.m.n_sections))
+        lib().om_water(self._ptr, _p(_f64(env)), _p(_f64(y)), _p(L))
+        return L[: self.m.n_sections]
 
     def _atol(self, atol):
         a = np.atleast_1d(_f64(atol))

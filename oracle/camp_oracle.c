@@ -15,6 +15,11 @@
  * (dy_i/dt)_k = nu_ik r_k (nu negative for reactants); the per-type physics
  * (Table 2) enters only through the pair (kf_k, kr_k).
  *
+ * Parameters (Sect. 2.2.2): a ZSR aerosol-water parameter makes the liquid
+ * volume L_b of each section a function of the state; the constants of the
+ * section processes then carry powers of 1/L_b(y), and the Jacobian gains
+ * the chain-rule term J_p P_y (om_jacobian_env).
+ *
  * State units: ppb-equivalent of air for every species (our reading; the
  * paper does not state solver units).  Constants: exact SI 2019 values.
  *
@@ -50,6 +55,8 @@ typedef struct {
     double p[10];           /* type parameters, see om_rate_constants */
 } om_rxn;
 
+#define OM_ZSR_NY 8         /* coefficients of one molality fit */
+
 typedef struct {
     int n_species;
     int n_rxn;
@@ -57,6 +64,14 @@ typedef struct {
     int n_sections;
     int env_section_base;   /* env index of section 0's radius */
     const om_rxn *rxn;
+    /* ZSR aerosol-water parameter (Sect. 2.2.2, Table 4, ZSRAerosolWater):
+     * with n_zsr > 0 the liquid volume of every section is a function of the
+     * state, computed from its electrolytes at the cell's relative humidity */
+    int rh_slot;              /* env index of the relative humidity (0..1), -1 if none */
+    int n_zsr;                /* electrolytes (0: no water parameter) */
+    const int *zsr_species;   /* [n_sections][n_zsr] species of electrolyte e in section b */
+    const double *zsr_Y;      /* [n_zsr][OM_ZSR_NY] molality fit, sqrt(m) = sum_j Y_j a_w^j */
+    const double *zsr_low;    /* [n_zsr] lowest water activity of the fit */
 } om_mech;
 
 /* ---- physical constants (SI 2019, exact) -------------------------------- */
@@ -118,6 +133,14 @@ static double mass_transfer(double rad, double Np, double alpha, double Dg, doub
     return Np * 4.0 * PI * rad * Dg * ffs;
 }
 
+/* Liquid volume of section b [m^3 per m^3 air] that enters the rate
+ * constants: the env value, or 1 when a water parameter makes it a function
+ * of the state.  In that case kf and kr are per unit volume and the powers of
+ * 1/L of water_powers() are applied wherever the state is known. */
+static double section_volume(const om_mech *m, const double *env, int b) {
+    return m->n_zsr > 0 ? 1.0 : env[m->env_section_base + 3 * b + 2];
+}
+
 void om_rate_constants(const om_mech *m, const double *env, double *kf, double *kr) {
     const double T = env[0], P = env[1];
     const double Mair = P / (KB * T) * 1e-6;   /* air number density, molec cm^-3 */
@@ -162,7 +185,7 @@ void om_rate_constants(const om_mech *m, const double *env, double *kf, double *
             int b = r->section;
             double rad = env[m->env_section_base + 3 * b];
             double Np = env[m->env_section_base + 3 * b + 1];
-            double L = env[m->env_section_base + 3 * b + 2];
+            double L = section_volume(m, env, b);
             if (!(L > 0.0 && Np > 0.0 && rad > 0.0)) break;
             double H = r->p[0] * exp(r->p[1] * (1.0 / T - 1.0 / 298.0));
             double Hcc = 1000.0 * H * RGAS * T;
@@ -181,7 +204,7 @@ void om_rate_constants(const om_mech *m, const double *env, double *kf, double *
             int b = r->section;
             double rad = env[m->env_section_base + 3 * b];
             double Np = env[m->env_section_base + 3 * b + 1];
-            double L = env[m->env_section_base + 3 * b + 2];
+            double L = section_volume(m, env, b);
             if (!(L > 0.0 && Np > 0.0 && rad > 0.0)) break;
             double lg = r->p[0] / T + r->p[1] + r->p[2] * T + r->p[3] * log(T);
             double p0 = 101325.0 * pow(10.0, lg);          /* Pa */
@@ -198,7 +221,7 @@ void om_rate_constants(const om_mech *m, const double *env, double *kf, double *
              * phi = 1e-9 P / (R T 1000 L) [M per ppb]; the rate in M s^-1 is
              * divided by phi to return to ppb s^-1. */
             int b = r->section;
-            double L = env[m->env_section_base + 3 * b + 2];
+            double L = section_volume(m, env, b);
             if (!(L > 0.0)) break;
             double Keq = r->p[0] * exp(r->p[1] * (1.0 / T - 1.0 / 298.0));
             double krev = r->p[2];
@@ -230,7 +253,7 @@ void om_rate_constants(const om_mech *m, const double *env, double *kf, double *
              * M s^-1 is k prod c with c = y phi, returned to ppb s^-1 by
              * dividing by phi, so kf = k phi^(nr - 1). */
             int b = r->section;
-            double L = env[m->env_section_base + 3 * b + 2];
+            double L = section_volume(m, env, b);
             if (!(L > 0.0)) break;
             double A = r->p[0], B = r->p[1], C = r->p[2], D = r->p[3], E = r->p[4];
             double kk = A * exp(C / T) * pow(T / D, B) * (1.0 + E * P);
@@ -314,6 +337,153 @@ void om_jacobian(const om_mech *m, const double *kf, const double *kr, const dou
 }
 
 /* ======================================================================== */
+/* ZSR aerosol water as a parameter (Sect. 2.2.2; Table 4, ZSRAerosolWater) */
+/* ======================================================================== */
+/* Powers of 1/L in kf (*la) and kr (*lb) of a section process when the
+ * liquid volume L is a parameter.  A molarity is y phi with phi proportional
+ * to 1/L, and a rate in M s^-1 returns to ppb s^-1 through one division by
+ * phi, so a side with f concentration factors carries L^-(f-1); the
+ * evaporation constant k_c / (H_cc L) of the phase-transfer types carries
+ * L^-1. */
+static void water_powers(const om_rxn *r, int *la, int *lb) {
+    int nr = 0, np = 0;
+    for (int i = 0; i < r->n_react; i++) nr += r->rstoich[i];
+    for (int i = 0; i < r->n_prod; i++) np += (int)r->yield[i];
+    *la = 0;
+    *lb = 0;
+    switch (r->type) {
+    case OM_HENRY:
+    case OM_SIMPOL: *lb = 1; break;
+    case OM_AQREV: *la = nr - 1; *lb = np - 1; break;
+    case OM_COND_ARRHENIUS: *la = nr - 1; break;
+    }
+}
+
+/* Molality [mol per kg water] of electrolyte e alone in water at water
+ * activity a_w, from a fit of the Jacobson et al. (1996) form
+ * sqrt(m) = sum_j Y_j a_w^j; below the fit's lowest activity a_w is held
+ * there. */
+static double zsr_molality(const om_mech *m, int e, double aw) {
+    if (aw < m->zsr_low[e]) aw = m->zsr_low[e];
+    double s = 0.0, p = 1.0;
+    for (int j = 0; j < OM_ZSR_NY; j++) {
+        s += m->zsr_Y[e * OM_ZSR_NY + j] * p;
+        p *= aw;
+    }
+    return s * s;
+}
+
+/* Liquid water volume per ppb of electrolyte e [m^3 per m^3 air per ppb]:
+ * the ZSR water W = sum_i 1000 M_i / (MW_i m_i(a_w)) (Table 4), in kg per
+ * m^3 of air with M_i in kg m^-3 and MW_i in g mol^-1, so that 1000 M_i /
+ * MW_i is the electrolyte's molar concentration, 1e-9 P / (R T) mol m^-3 per
+ * ppb; divided by the density of water, 1000 kg m^-3.  The water activity
+ * is the relative humidity.  An electrolyte whose fitted molality is not
+ * positive holds no water. */
+static double zsr_weight(const om_mech *m, const double *env, int e) {
+    const double T = env[0], P = env[1];
+    double mol = zsr_molality(m, e, env[m->rh_slot]);
+    if (!(mol > 0.0) || !isfinite(mol)) return 0.0;
+    return 1e-9 * P / (RGAS * T) / mol / 1000.0;
+}
+
+/* Liquid volume of every section at state y: the env value plus the ZSR
+ * water of the section's electrolytes. */
+void om_water(const om_mech *m, const double *env, const double *y, double *L) {
+    for (int b = 0; b < m->n_sections; b++) {
+        double v = env[m->env_section_base + 3 * b + 2];
+        for (int e = 0; e < m->n_zsr; e++)
+            v += zsr_weight(m, env, e) * y[m->zsr_species[b * m->n_zsr + e]];
+        L[b] = v;
+    }
+}
+
+/* kf, kr of om_rate_constants (per unit volume on the sections) with the
+ * powers of 1/L at the current liquid volumes applied */
+static void volume_constants(const om_mech *m, const double *kf, const double *kr,
+                             const double *L, double *kfe, double *kre) {
+    for (int k = 0; k < m->n_rxn; k++) {
+        const om_rxn *r = &m->rxn[k];
+        kfe[k] = kf[k];
+        kre[k] = kr[k];
+        if (r->section < 0) continue;
+        int la, lb;
+        water_powers(r, &la, &lb);
+        kfe[k] = kf[k] / ipow(L[r->section], la);
+        kre[k] = kr[k] / ipow(L[r->section], lb);
+    }
+}
+
+/* f(y) of a mechanism whose parameters are evaluated at y first (Sect.
+ * 2.2.2: the processes use the parameters' current values). */
+void om_forcing_env(const om_mech *m, const double *env, const double *kf, const double *kr,
+                    const double *y, double *f) {
+    if (m->n_zsr == 0) {
+        om_forcing(m, kf, kr, y, f);
+        return;
+    }
+    double *L = malloc(sizeof(double) * (size_t)(m->n_sections + 2 * m->n_rxn));
+    double *kfe = L + m->n_sections, *kre = kfe + m->n_rxn;
+    om_water(m, env, y, L);
+    volume_constants(m, kf, kr, L, kfe, kre);
+    om_forcing(m, kfe, kre, y, f);
+    free(L);
+}
+
+/* The solver's Jacobian by the chain rule of Sect. 2.2.2: the processes'
+ * partial derivatives with the parameters held at their values (J_y), plus
+ * the partial derivatives of the forcing with respect to the parameters
+ * (J_p, n x S) times those of the parameters with respect to the state
+ * (P_y, S x n):  J = J_y + J_p P_y.  For the liquid volume of section b,
+ * d r_k / d L_b = -(la F_k - lb B_k) / L_b with F_k and B_k the forward and
+ * reverse terms of r_k = F_k - B_k, and d L_b / d y_j is electrolyte j's
+ * water per ppb. */
+void om_jacobian_env(const om_mech *m, const double *env, const double *kf, const double *kr,
+                     const double *y, double *J) {
+    if (m->n_zsr == 0) {
+        om_jacobian(m, kf, kr, y, J);
+        return;
+    }
+    const int n = m->n_species, S = m->n_sections;
+    double *L = malloc(sizeof(double) * (size_t)(S + 2 * m->n_rxn));
+    double *kfe = L + S, *kre = kfe + m->n_rxn;
+    double *Jp = calloc((size_t)n * S, sizeof(double));
+    double *Py = calloc((size_t)S * n, sizeof(double));
+    om_water(m, env, y, L);
+    volume_constants(m, kf, kr, L, kfe, kre);
+    om_jacobian(m, kfe, kre, y, J);                        /* J_y */
+    for (int k = 0; k < m->n_rxn; k++) {                   /* J_p */
+        const om_rxn *r = &m->rxn[k];
+        if (r->section < 0) continue;
+        int la, lb;
+        water_powers(r, &la, &lb);
+        if (la == 0 && lb == 0) continue;
+        double F = kfe[k], B = 0.0;
+        for (int i = 0; i < r->n_react; i++) F *= ipow(y[r->react[i]], r->rstoich[i]);
+        if (kre[k] != 0.0) {
+            B = kre[k];
+            for (int i = 0; i < r->n_prod; i++) B *= ipow(y[r->prod[i]], (int)r->yield[i]);
+        }
+        const int b = r->section;
+        double dr = -(la * F - lb * B) / L[b];
+        for (int i = 0; i < r->n_react; i++) Jp[r->react[i] * S + b] -= r->rstoich[i] * dr;
+        for (int i = 0; i < r->n_prod; i++) Jp[r->prod[i] * S + b] += r->yield[i] * dr;
+    }
+    for (int b = 0; b < S; b++)                            /* P_y */
+        for (int e = 0; e < m->n_zsr; e++)
+            Py[b * n + m->zsr_species[b * m->n_zsr + e]] += zsr_weight(m, env, e);
+    for (int i = 0; i < n; i++)                            /* J += J_p P_y */
+        for (int b = 0; b < S; b++) {
+            double a = Jp[i * S + b];
+            if (a == 0.0) continue;
+            for (int j = 0; j < n; j++) J[i * n + j] += a * Py[b * n + j];
+        }
+    free(Py);
+    free(Jp);
+    free(L);
+}
+
+/* ======================================================================== */
 /* Dense LU with partial pivoting (textbook Doolittle, row swaps)           */
 /* ======================================================================== */
 /* Factor A (row-major n x n) in place; piv[k] = row swapped into k.  Returns 0
@@ -392,6 +562,7 @@ void om_bdf_coefficients(int q, double *l, double *ecoef) {
 typedef struct {
     const om_mech *m;
     int n;
+    const double *env;
     const double *kf, *kr;
     double *J, *LU, *tmp;
     int *piv;
@@ -399,7 +570,7 @@ typedef struct {
 } om_ctx;
 
 static void fval(om_ctx *c, const double *y, double *f) {
-    om_forcing(c->m, c->kf, c->kr, y, f);
+    om_forcing_env(c->m, c->env, c->kf, c->kr, y, f);
     c->nfe++;
 }
 
@@ -439,7 +610,7 @@ static void rescale(int n, int q, double *z, double eta) {
 /* Evaluate J at y, form M = I - gamma J and factor it.  Returns 0 on success. */
 static int setup(om_ctx *c, const double *y, double gamma) {
     int n = c->n;
-    om_jacobian(c->m, c->kf, c->kr, y, c->J);
+    om_jacobian_env(c->m, c->env, c->kf, c->kr, y, c->J);
     for (int i = 0; i < n * n; i++) c->LU[i] = -gamma * c->J[i];
     for (int i = 0; i < n; i++) c->LU[i * n + i] += 1.0;
     c->nje++;
@@ -524,7 +695,7 @@ static int integrate_cell(const om_mech *m, const double *env, double *y, double
     double *del = f + nn, *tmp = del + nn, *tmp2 = tmp + nn, *y1 = tmp2 + nn, *f1 = y1 + nn;
     double *J = f1 + nn, *LU = J + nn * nn, *kf = LU + nn * nn, *kr = kf + m->n_rxn;
 
-    om_ctx c = {m, n, kf, kr, J, LU, tmp, piv, 0, 0, 0, 0};
+    om_ctx c = {m, n, env, kf, kr, J, LU, tmp, piv, 0, 0, 0, 0};
     om_rate_constants(m, env, kf, kr);
     int status = OM_OK;
     int q = 1, qwait = 2, nst = 0, have_lu = 0, need_setup = 1, nst_lu = 0, ep_valid = 0;
@@ -725,7 +896,7 @@ double om_bdf_step(const om_mech *m, const double *env, const double *z_in, int 
     int *piv = calloc(nn, sizeof(int));
     double *w = buf, *ycur = w + nn, *f = ycur + nn, *del = f + nn, *tmp = del + nn;
     double *J = tmp + 3 * nn, *LU = J + nn * nn, *kf = LU + 2 * nn * nn, *kr = kf + m->n_rxn;
-    om_ctx c = {m, n, kf, kr, J, LU, tmp, piv, 0, 0, 0, 0};
+    om_ctx c = {m, n, env, kf, kr, J, LU, tmp, piv, 0, 0, 0, 0};
     om_rate_constants(m, env, kf, kr);
     memcpy(z_out, z_in, sizeof(double) * (q + 1) * nn);
     for (int i = 0; i < n; i++) w[i] = 1.0 / (rtol * fabs(z_in[i]) + atol[atol_len == 1 ? 0 : i]);

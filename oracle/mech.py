@@ -42,13 +42,21 @@ class OmRxn(ctypes.Structure):
                 ("p", ctypes.c_double * 10)]
 
 
+ZSR_NY = 8  # coefficients of one molality fit
+
+
 class OmMech(ctypes.Structure):
     _fields_ = [("n_species", ctypes.c_int),
                 ("n_rxn", ctypes.c_int),
                 ("n_env", ctypes.c_int),
                 ("n_sections", ctypes.c_int),
                 ("env_section_base", ctypes.c_int),
-                ("rxn", ctypes.POINTER(OmRxn))]
+                ("rxn", ctypes.POINTER(OmRxn)),
+                ("rh_slot", ctypes.c_int),
+                ("n_zsr", ctypes.c_int),
+                ("zsr_species", ctypes.POINTER(ctypes.c_int)),
+                ("zsr_Y", ctypes.POINTER(ctypes.c_double)),
+                ("zsr_low", ctypes.POINTER(ctypes.c_double))]
 
 
 @dataclass
@@ -75,6 +83,11 @@ class Mechanism:
     n_sections: int
     env_section_base: int
     raw: dict = field(repr=False, default=None)
+    # ZSR aerosol-water parameter (Sect. 2.2.2, Table 4): env slot of the
+    # relative humidity (-1: none) and per electrolyte (phase species name,
+    # fit coefficients Y_j of sqrt(m) = sum_j Y_j a_w^j, lowest a_w of the fit)
+    rh_slot: int = -1
+    electrolytes: list = field(default_factory=list)
 
     @property
     def n(self):
@@ -106,7 +119,22 @@ def parse(text) -> Mechanism:
     if len(index) != len(species):
         raise ValueError("duplicate species name")
     n_runtime = sum(1 for r in d["reactions"] if r["type"] in RUNTIME)
-    base = 2 + n_runtime
+    electrolytes = []
+    for par in d.get("parameters", []):
+        if par["type"] != "ZSR_AEROSOL_WATER":
+            raise ValueError(f"unknown parameter type {par['type']}")
+        if electrolytes or not nsec:
+            raise ValueError("one water parameter, on a mechanism with aerosol sections")
+        for e in par["electrolytes"]:
+            Y = [float(v) for v in e["Y"]]
+            if not 1 <= len(Y) <= ZSR_NY or e["species"] not in phase:
+                raise ValueError("bad electrolyte")
+            electrolytes.append((e["species"], Y + [0.0] * (ZSR_NY - len(Y)),
+                                 float(e.get("low_RH", 0.0))))
+        if not electrolytes:
+            raise ValueError("a water parameter needs electrolytes")
+    rh_slot = 2 + n_runtime if electrolytes else -1
+    base = 2 + n_runtime + (1 if electrolytes else 0)
     procs = []
     slot = 2
     for r in d["reactions"]:
@@ -164,7 +192,28 @@ def parse(text) -> Mechanism:
                                  env_slot=slot if t in RUNTIME else -1))
         if t in RUNTIME:
             slot += 1
-    return Mechanism(species, index, procs, base + 3 * nsec, nsec, base, d)
+    for p in procs:
+        if p.type in ("AQUEOUS_REVERSIBLE", "CONDENSED_ARRHENIUS") and not p.reactants:
+            raise ValueError("a condensed-phase reaction needs reactants")
+        if p.type == "AQUEOUS_REVERSIBLE" and not p.products:
+            raise ValueError("a reversible aqueous reaction needs products")
+    return Mechanism(species, index, procs, base + 3 * nsec, nsec, base, d, rh_slot, electrolytes)
+
+
+def water_powers(p: Process):
+    """Powers of 1/L in (kf, kr) of a section process when the liquid volume is
+    a parameter: a side with f concentration factors carries L^-(f-1) (molarity
+    y phi, phi ~ 1/L, one division by phi back to ppb s^-1); the evaporation
+    constant of the phase-transfer types carries L^-1."""
+    nr = sum(s for _, s in p.reactants)
+    np_ = sum(int(y) for _, y in p.products)
+    if p.type in ("HL_PHASE_TRANSFER", "SIMPOL_PHASE_TRANSFER"):
+        return 0, 1
+    if p.type == "AQUEOUS_REVERSIBLE":
+        return nr - 1, np_ - 1
+    if p.type == "CONDENSED_ARRHENIUS":
+        return nr - 1, 0
+    return 0, 0
 
 
 def to_ctypes(m: Mechanism):
@@ -187,6 +236,19 @@ def to_ctypes(m: Mechanism):
         r.section = p.section
         for i, v in enumerate(p.params):
             r.p[i] = v
+    ne = len(m.electrolytes)
+    sp = (ctypes.c_int * max(1, m.n_sections * ne))()
+    Y = (ctypes.c_double * max(1, ne * ZSR_NY))()
+    low = (ctypes.c_double * max(1, ne))()
+    for e, (name, coef, lo) in enumerate(m.electrolytes):
+        for b in range(m.n_sections):
+            sp[b * ne + e] = m.index[f"bin{b}.{name}"]
+        for j, v in enumerate(coef):
+            Y[e * ZSR_NY + j] = v
+        low[e] = lo
     cm = OmMech(m.n, len(m.processes), m.n_env, m.n_sections, m.env_section_base,
-                ctypes.cast(arr, ctypes.POINTER(OmRxn)))
-    return cm, arr
+                ctypes.cast(arr, ctypes.POINTER(OmRxn)), m.rh_slot, ne,
+                ctypes.cast(sp, ctypes.POINTER(ctypes.c_int)),
+                ctypes.cast(Y, ctypes.POINTER(ctypes.c_double)),
+                ctypes.cast(low, ctypes.POINTER(ctypes.c_double)))
+    return cm, (arr, sp, Y, low)

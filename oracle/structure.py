@@ -6,7 +6,10 @@ integer work that the product's mechanism compiler does once per mechanism
 
   pattern   every (i, j) with d f_i / d y_j possibly non-zero, plus the
             diagonal: the rows R_k u P_k times the species D_k that appear in
-            r_k (D_k = R_k, or R_k u P_k for reversible processes)
+            r_k (D_k = R_k, or R_k u P_k for reversible processes); with a
+            ZSR water parameter (Sect. 2.2.2) also the rows R_k u P_k of every
+            section process whose constants carry a power of 1/L, times the
+            electrolytes of its section (the chain-rule term J_p P_y)
   rxn_map   for each process k, each j in D_k, each i in R_k u P_k (all in
             declaration order, reactants before products, each species once):
             the CSR position of (i, j)
@@ -20,7 +23,7 @@ integer work that the product's mechanism compiler does once per mechanism
 """
 from __future__ import annotations
 
-from .mech import Mechanism
+from .mech import Mechanism, water_powers
 
 
 def _ordered_unique(seq):
@@ -49,6 +52,11 @@ def pattern(m: Mechanism):
         for j in dependence(p):
             for i in rows_of(p):
                 s.add((i, j))
+        if m.electrolytes and p.section >= 0 and any(water_powers(p)):
+            for name, _, _ in m.electrolytes:
+                j = m.index[f"bin{p.section}.{name}"]
+                for i in rows_of(p):
+                    s.add((i, j))
     return s
 
 

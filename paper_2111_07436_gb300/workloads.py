@@ -47,11 +47,23 @@ Reaction types and their fields (units follow Table 2 of the paper):
                        Dg, MW, c_tot [M] (condensed-phase total molarity,
                        default that of water)               (one per section)
 
+Parameters (optional; Sect. 2.2.2 and Table 4 of the paper):
+    "parameters": [{"type": "ZSR_AEROSOL_WATER",
+                    "electrolytes": [{"species": phase species name,
+                                      "Y": [Y_0, ..., Y_k] (k < 8),
+                                      "low_RH": lowest water activity of
+                                                the fit (default 0)}, ...]}]
+    The water of every section by the ZSR rule, W = sum_i 1000 M_i /
+    (MW_i m_i(a_w)), with molality fits sqrt(m_i) = sum_j Y_j a_w^j
+    (Jacobson et al. 1996 form) at a_w = relative humidity.  The section's
+    liquid volume becomes L_b = L_env,b + W_b(y) / 1000 kg m^-3.
+
 Per-cell environment vector (the solver reads only this; "value" fields are
 the defaults a host model would copy in):
     [T (K), P (Pa), one entry per PHOTOLYSIS / EMISSION / FIRST_ORDER_LOSS
-     reaction in declaration order, then per section b: r_b (m),
-     N_b (m^-3), L_b (m^3 water per m^3 air)]
+     reaction in declaration order, RH (0..1; only with a water parameter),
+     then per section b: r_b (m), N_b (m^-3), L_b (m^3 water per m^3 air;
+     with a water parameter the part its electrolytes do not hold)]
 
 State: every species, gas and aqueous, in ppb-equivalent of air (mole ratio
 x 1e9).  Species order: gas species in declaration order, then for section
@@ -351,6 +363,37 @@ def particle_resolved_mechanism(n_particles=128, seed=106):
     return mech
 
 
+def water_mechanism(seed=107, n_sections=8):
+    """The 232-species multiphase mechanism with its aerosol water as a
+    parameter (Sect. 2.2.2; Table 4, ZSRAerosolWater): one more phase species,
+    an inert salt (the sections' dry particle volume, per cell), and a ZSR
+    water parameter over two electrolytes -- the
+    salt and the aqueous species that the first Henry's-law transfer feeds,
+    so that the water, and with it every section rate that depends on the
+    liquid volume, follows the state.  72 gas + 8 x 21 phase species = 240.
+    The paper prints no molality fits, so each electrolyte gets a synthetic
+    fit of the Jacobson et al. (1996) form sqrt(m) = Y0 + Y1 a_w + Y2 a_w^2:
+    molality log-uniform 4..12 mol/kg at a_w = 0.5 and 0.5..2 at 0.95,
+    joined linearly in sqrt(m) plus a small curvature, held below
+    a_w = 0.5."""
+    rng = np.random.default_rng(seed)
+    mech = multiphase_mechanism()
+    mech["phases"]["aqueous"].append({"name": "SALT", "atoms": 1})
+    hl = [r for r in mech["reactions"] if r["type"] == "HL_PHASE_TRANSFER"]
+    electrolytes = []
+    for name in ("SALT", hl[0]["aqueous"]):
+        s05 = math.sqrt(float(_logu(rng, 4.0, 12.0)))
+        s95 = math.sqrt(float(_logu(rng, 0.5, 2.0)))
+        kappa = float(rng.uniform(-0.5, 0.5))
+        slope = (s95 - s05) / 0.45
+        # s05 + slope (a - 0.5) + kappa (a - 0.5)(a - 0.95), expanded in a
+        Y = [s05 - 0.5 * slope + kappa * 0.475, slope - 1.45 * kappa, kappa]
+        electrolytes.append({"species": name, "Y": Y, "low_RH": 0.5})
+    mech["parameters"] = [{"type": "ZSR_AEROSOL_WATER", "electrolytes": electrolytes}]
+    mech["name"] = f"multiphase-water-{len(mech['species']) + n_sections * 21}"
+    return mech
+
+
 # --------------------------------------------------------------------------
 # layout helpers (interface description only)
 # --------------------------------------------------------------------------
@@ -381,6 +424,8 @@ def layout(mech) -> Layout:
             env.append(f"{r['type'].lower()}[{i}]")
             defaults.append(float(r["value"]))
             kinds.append(r["type"])
+    if mech.get("parameters"):
+        env.append("RH")
     for b in range(nsec):
         env += [f"bin{b}.r", f"bin{b}.N", f"bin{b}.L"]
     return Layout(species, np.array(atoms, dtype=np.int64), env, defaults, kinds, nsec)
@@ -431,6 +476,10 @@ def cells(mech, n_cells, seed, T=None, P=None, sza=True, night_fraction=None,
     for k, (d, kind) in enumerate(zip(lay.runtime_defaults, lay.runtime_kind)):
         env[:, 2 + k] = d * (mu if kind == "PHOTOLYSIS" else 1.0)
     base = 2 + len(lay.runtime_defaults)
+    water = bool(mech.get("parameters"))
+    if water:  # relative humidity, and the electrolytes that hold the water
+        env[:, base] = rng.uniform(0.5, 0.95, n_cells)
+        base += 1
     if lay.n_sections and mech["aerosol"].get("representation") == "particles":
         P = lay.n_sections
         r = np.clip(np.exp(rng.normal(math.log(1e-7), math.log(1.8), (n_cells, P))), 5e-9, 1e-5)
@@ -447,6 +496,19 @@ def cells(mech, n_cells, seed, T=None, P=None, sza=True, night_fraction=None,
             share = share / share.sum(axis=1, keepdims=True)
             L = np.where(cloudy[:, None], lwc[:, None] * share, 0.0)
         r = np.broadcast_to(r[None, :], (n_cells, lay.n_sections))
+    if water:
+        # all section water comes from the electrolytes: L_env = 0.  Each
+        # section's dry particles, N 4/3 pi r^3 per m^3 of air, are salt of
+        # 13400 mol m^-3 (1770 kg m^-3 at 0.132 kg mol^-1, ammonium-sulphate
+        # like); the other electrolytes start at 1% of the salt
+        L = np.zeros_like(L)
+        idx = {s: i for i, s in enumerate(lay.species)}
+        air = env[:, 1] / (8.314462618 * env[:, 0])  # mol air per m^3
+        for b in range(lay.n_sections):
+            salt = N[:, b] * (4.0 / 3.0) * math.pi * r[:, b] ** 3 * 13400.0 / air * 1e9
+            for e in mech["parameters"][0]["electrolytes"]:
+                name = f"bin{b}.{e['species']}"
+                y[:, idx[name]] = salt if e["species"] == "SALT" else 0.01 * salt
     if lay.n_sections:
         for b in range(lay.n_sections):
             env[:, base + 3 * b] = r[:, b]
@@ -512,7 +574,8 @@ def serving_requests(n_requests=2000, seed=205, gas_share=0.7, cells_lo=256, cel
 
 def workload(k: int) -> Workload:
     """k = 1..3: the single-mechanism workloads (sizes in the docstrings);
-    k = 6: the particle-resolved workload."""
+    k = 6: the particle-resolved workload; k = 7: the water-parameter
+    workload."""
     if k == 1:
         return Workload("small-gas 1 cell, 60 x 60 s", small_gas_mechanism(), 1, 60.0, 60,
                         1e-4, 1e-5, 201, dict(T=298.0, P=101300.0, sza=False))
@@ -525,4 +588,7 @@ def workload(k: int) -> Workload:
     if k == 6:  # the particle-resolved shape (a row beyond the five configurations)
         return Workload("particle-resolved 128 particles (914 species) 2048 cells, 180 s",
                         particle_resolved_mechanism(128), 2048, 180.0, 1, 1e-4, 1e-5, 206, {})
+    if k == 7:  # aerosol water as a parameter of the state
+        return Workload("multiphase-water-240 (ZSR water parameter) 4096 cells, 300 s",
+                        water_mechanism(), 4096, 300.0, 1, 1e-4, 1e-5, 207, {})
     raise ValueError(k)

@@ -2,13 +2,19 @@
 import json
 
 
-def mech(species, reactions, phase=None, sections=0, atoms=None):
+def mech(species, reactions, phase=None, sections=0, atoms=None, water=None):
+    """water: [(phase species, [Y_0, ...], low_RH), ...] -> a ZSR aerosol-water
+    parameter over those electrolytes."""
     d = {"name": "test",
          "species": [{"name": s, "atoms": (atoms or {}).get(s, 1)} for s in species],
          "reactions": reactions}
     if phase is not None:
         d["phases"] = {"aqueous": [{"name": p, "atoms": 1} for p in phase]}
         d["aerosol"] = {"phase": "aqueous", "sections": sections}
+    if water:
+        d["parameters"] = [{"type": "ZSR_AEROSOL_WATER",
+                            "electrolytes": [{"species": e, "Y": list(Y), "low_RH": lo}
+                                             for e, Y, lo in water]}]
     return json.dumps(d)
 
 
@@ -66,3 +72,4 @@ def simpol(gas, aq, B, alpha=0.5, Dg=1e-5, MW=0.05, c_tot=None):
     if c_tot is not None:
         d["c_tot"] = c_tot
     return d
+
