@@ -25,7 +25,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOADS = {"small": 1, "gas72": 2, "multiphase232": 3, "uneven": 4, "serving": 5, "particles": 6}
+WORKLOADS = {"small": 1, "gas72": 2, "multiphase232": 3, "uneven": 4, "serving": 5, "particles": 6,
+             "water": 7}
 FP64_PEAK_NOMINAL_GFLOPS = 1250.0  # GB300 dense FP64, nominal
 
 

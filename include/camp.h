@@ -25,9 +25,13 @@
  *       env    [n_cells][n_env]      T (K), P (Pa), one entry per
  *                                   PHOTOLYSIS (s^-1) / EMISSION (ppb s^-1)
  *                                   / FIRST_ORDER_LOSS (s^-1) process in
- *                                   declaration order, then per section:
- *                                   radius (m), number (m^-3), water volume
- *                                   fraction (m^3 m^-3);
+ *                                   declaration order, the relative
+ *                                   humidity (0..1; only with a
+ *                                   ZSR_AEROSOL_WATER parameter), then per
+ *                                   section: radius (m), number (m^-3),
+ *                                   water volume fraction (m^3 m^-3; with
+ *                                   a water parameter the part not held by
+ *                                   its electrolytes);
  *       status [n_cells]             per-cell status (CAMP_CELL_*).
  *   - Calls taking a `stream` are asynchronous on that cudaStream_t (NULL =
  *     legacy default stream); they validate arguments on the host and return
@@ -103,6 +107,13 @@ typedef struct {
  * CONDENSED_ARRHENIUS (one instance per aerosol section, or per
  * computational particle in the particle-resolved representation,
  * SingleParticle of Sect. 2.2.3, Table 6).
+ * Parameters (Sect. 2.2.2, Table 4): ZSR_AEROSOL_WATER, the water of each
+ * section from its electrolytes by the ZSR mixing rule
+ * W = sum_i 1000 M_i / (MW_i m_i(a_w)) with Jacobson-form molality fits
+ * sqrt(m_i) = sum_j Y_j a_w^j at a_w = RH.  The section's liquid volume is
+ * then L_b(y) = L_env,b + W_b(y) / (1000 kg m^-3), a function of the state:
+ * the section processes' constants carry powers of 1/L_b(y), and df/dy
+ * includes the chain-rule term (df/dL_b)(dL_b/dy).
  * Limits: at most 2048 species (up to 256 a cell runs on one warp, beyond
  * that on a block of 64, 128 or 256 threads), 32767 stored LU values, and a
  * per-cell working set that fits one SM's shared memory; larger mechanisms
@@ -132,7 +143,9 @@ int camp_mech_species_index(const camp_mech *m, const char *name);
  *   rowptr [n+1], colidx [nnz_jac]: CSR pattern of df/dy in declaration
  *       order, columns sorted: the diagonal plus, for every process k, the
  *       rows R_k u P_k times the species D_k its rate depends on
- *       (D_k = R_k, or R_k u P_k for reversible processes);
+ *       (D_k = R_k, or R_k u P_k for reversible processes); with a water
+ *       parameter also, for every section process whose constants carry a
+ *       power of 1/L_b, the rows R_k u P_k times the electrolytes of b;
  *   rxn_map [rxn_map_len]: for every process k, every j in D_k, every i in
  *       R_k u P_k (declaration order, reactants first, each species once):
  *       the CSR position of (i, j);
@@ -285,7 +298,9 @@ int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const doub
 /* ---- single steps of the method, for testing ----------------------------- */
 /* Rate constants (paper Table 2) in ppb units: device env [n_cells][n_env]
  * -> kf, kr device [n_cells][n_rxn] (process order).  The rate of process k
- * is kf_k prod_{reactants} y^s - kr_k prod_{products} y^nu. */
+ * is kf_k prod_{reactants} y^s - kr_k prod_{products} y^nu.  With a water
+ * parameter the section processes' constants are per unit liquid volume
+ * (the powers of 1/L_b(y) are applied at each state). */
 int camp_rate_constants(const camp_mech *m, int64_t n_cells, const double *env, double *kf,
                         double *kr, void *stream);
 
@@ -296,7 +311,8 @@ int camp_forcing(const camp_mech *m, int64_t n_cells, const double *state, const
 
 /* Jacobian df_i/dy_j = sum_k (df_i/dy_j)_k (paper Sect. 2.4.2) at the CSR
  * non-zeros of camp_mech_structure: device jac [n_cells][nnz_jac], values
- * computed in the variant's assembly precision. */
+ * computed in the variant's assembly precision (the chain-rule term of a
+ * water parameter, Sect. 2.2.2, in FP64). */
 int camp_jacobian(const camp_mech *m, int64_t n_cells, const double *state, const double *env,
                   double *jac, int32_t variant, void *stream);
 

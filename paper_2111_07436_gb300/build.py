@@ -1,7 +1,8 @@
 """Build libcamp.so in-tree with nvcc for sm_103a.
 
-The translation units compile in parallel (the two LU precisions are separate
-units); objects go to _build/, the library to libcamp.so beside this file.
+The translation units compile in parallel (the two LU precisions, and their
+builds for mechanisms with a water parameter, are separate units); objects go
+to _build/, the library to libcamp.so beside this file.
 """
 from __future__ import annotations
 
@@ -14,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcamp.so")
-SOURCES = ["capi.cu", "solve_f32.cu", "solve_f64.cu", "mech.cpp", "server.cpp", "probe.cu", "static_scratch.cu"]
+SOURCES = ["capi.cu", "solve_f32.cu", "solve_f64.cu", "solve_f32w.cu", "solve_f64w.cu", "mech.cpp",
+           "server.cpp", "probe.cu", "static_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -42,18 +42,22 @@ constexpr double PI_D = 3.14159265358979323846;
 
 // ---- shared-memory layout of one cell --------------------------------------
 struct CellSmem {
-    int ys, rs, kf, kr, x, lu, bytes;
+    int ys, rs, kf, kr, pw, x, lu, bytes;
 };
 __host__ __device__ inline int align16(int b) { return (b + 15) & ~15; }
 // rs holds the R rate terms, then n_part partial sums (of split forcing sums
 // inside an f evaluation, of split substitution rows inside a solve)
-__host__ __device__ inline CellSmem cell_smem(int n, int R, int n_rev, int nlu, int lu_elem, int n_part) {
+// pw holds the water parameter's per-cell values (n_pw doubles, none
+// without one)
+__host__ __device__ inline CellSmem cell_smem(int n, int R, int n_rev, int nlu, int lu_elem, int n_part,
+                                              int n_pw) {
     CellSmem c;
     int o = 0;
     c.ys = o; o = align16(o + 8 * n);
     c.rs = o; o = align16(o + 8 * (R + n_part));
     c.kf = o; o = align16(o + 8 * R);
     c.kr = o; o = align16(o + 8 * n_rev);
+    c.pw = o; o = align16(o + 8 * n_pw);
     // the substitution vector shares the rate-term scratch when it fits:
     // the rate terms live only inside one f evaluation, the vector only
     // inside one Newton solve, and the Jacobian assembly keeps its FP32
@@ -71,14 +75,15 @@ __host__ __device__ inline CellSmem cell_smem(int n, int R, int n_rev, int nlu, 
 
 template <typename LT>
 struct CellPtr {
-    double *ys, *rs, *kf, *kr;
+    double *ys, *rs, *kf, *kr, *pw;
     LT *x, *lu;
     __device__ CellPtr(char *base, const DevMech &m) {
-        CellSmem c = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part);
+        CellSmem c = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw);
         ys = (double *)(base + c.ys);
         rs = (double *)(base + c.rs);
         kf = (double *)(base + c.kf);
         kr = (double *)(base + c.kr);
+        pw = (double *)(base + c.pw);
         x = (LT *)(base + c.x);
         lu = (LT *)(base + c.lu);
     }
@@ -149,6 +154,13 @@ __device__ __forceinline__ double condensation(double rad, double Np, double alp
     return Np * 4.0 * PI_D * rad * Dg * ffs;
 }
 
+// Liquid volume of section b in the rate constants: the env value, or 1 when
+// the water parameter makes it a function of the state (the constants are
+// then per unit volume and the powers of 1/L are applied at each state)
+__device__ __forceinline__ double section_volume(const DevMech &m, const double *__restrict__ env, int b) {
+    return m.n_wsec > 0 ? 1.0 : env[m.env_sec_base + 3 * b + 2];
+}
+
 __device__ inline void rate_constant(const DevMech &m, int k, const double *__restrict__ env,
                                      double &kf, double &kr) {
     const double T = env[0], P = env[1];
@@ -201,7 +213,7 @@ __device__ inline void rate_constant(const DevMech &m, int k, const double *__re
         const int b = __ldg(m.rslot + k);
         const double rad = env[m.env_sec_base + 3 * b];
         const double Np = env[m.env_sec_base + 3 * b + 1];
-        const double L = env[m.env_sec_base + 3 * b + 2];
+        const double L = section_volume(m, env, b);
         if (!(L > 0.0 && Np > 0.0 && rad > 0.0)) break;
         double H, kb;
         if (__ldg(m.rtype + k) == CAMP_P_HENRY) {
@@ -220,7 +232,7 @@ __device__ inline void rate_constant(const DevMech &m, int k, const double *__re
         // K_eq = A exp(C (1/T - 1/298)); rates in M/s, molarity = y * phi,
         // phi = 1e-9 P / (R T 1000 L) M per ppb
         const int b = __ldg(m.rslot + k);
-        const double L = env[m.env_sec_base + 3 * b + 2];
+        const double L = section_volume(m, env, b);
         if (!(L > 0.0)) break;
         double Keq = __ldg(par) * exp(__ldg(par + 1) * (1.0 / T - 1.0 / 298.0));
         double krev = __ldg(par + 2);
@@ -233,7 +245,7 @@ __device__ inline void rate_constant(const DevMech &m, int k, const double *__re
         // Arrhenius in the section's condensed phase, M^(1-nr) s^-1:
         // kf = k phi^(nr - 1) in ppb units
         const int b = __ldg(m.rslot + k);
-        const double L = env[m.env_sec_base + 3 * b + 2];
+        const double L = section_volume(m, env, b);
         if (!(L > 0.0)) break;
         double kk = __ldg(par) * exp(__ldg(par + 2) / T) * pow(T / __ldg(par + 3), __ldg(par + 1)) *
                     (1.0 + __ldg(par + 4) * P);
@@ -301,13 +313,141 @@ __device__ __forceinline__ double gather_entry(const DevMech &m, int q, const do
     return __ldg(m.fcoef + hi16(g)) * rs[lo16(g)];
 }
 
+// ---- the water parameter (Sect. 2.2.2; Table 4, ZSRAerosolWater) ----------
+// Per-cell scratch c.pw: kf0, kr0 and d r / d L of each parameterised
+// process, then the electrolyte weights, L_env and 1 / L of each section, then
+// the g sums d f_i / d L_b.
+__device__ __forceinline__ double *pw_dl(const DevMech &m, double *pw) { return pw + 2 * m.n_pp; }
+__device__ __forceinline__ double *pw_wt(const DevMech &m, double *pw) { return pw + 3 * m.n_pp; }
+__device__ __forceinline__ double *pw_lenv(const DevMech &m, double *pw) { return pw_wt(m, pw) + m.n_el; }
+__device__ __forceinline__ double *pw_invl(const DevMech &m, double *pw) { return pw_lenv(m, pw) + m.n_wsec; }
+__device__ __forceinline__ double *pw_g(const DevMech &m, double *pw) { return pw_invl(m, pw) + m.n_wsec; }
+
+// Water per ppb of electrolyte e [m^3 per m^3 air]: 1e-9 P / (R T) mol m^-3
+// per ppb over the molality m_e(a_w) of its binary solution (ZSR:
+// W = sum_i 1000 M_i / (MW_i m_i(a_w)) kg m^-3), over the density of water.
+// The molality fit is sqrt(m) = sum_j Y_j a_w^j with a_w = RH, held at the
+// fit's lowest activity below it; a fit that gives no positive molality
+// holds no water.
+__device__ inline double zsr_weight(const DevMech &m, int e, const double *__restrict__ env) {
+    const double T = env[0], P = env[1];
+    double aw = env[m.rh_slot];
+    const double lo = __ldg(m.zsr_low + e);
+    if (aw < lo) aw = lo;
+    double s = 0.0, p = 1.0;
+    for (int j = 0; j < CAMP_ZSR_NY; j++) {
+        s += __ldg(m.zsr_Y + CAMP_ZSR_NY * e + j) * p;
+        p *= aw;
+    }
+    const double mol = s * s;
+    if (!(mol > 0.0) || !finite_bits(mol)) return 0.0;
+    return 1e-9 * P / (RG * T) / mol / 1000.0;
+}
+
+// After the rate constants: keep each parameterised process's per-volume
+// constants, the electrolyte weights and the sections' env volumes.
+template <int G>
+__device__ __forceinline__ void water_setup(const DevMech &m, double *pw, const double *kf, const double *kr,
+                                         const double *__restrict__ env, int lane, unsigned gm) {
+    for (int j = lane; j < m.n_pp; j += G) {
+        const int4 r = __ldg(m.pp + j);
+        pw[j] = kf[r.x];
+        pw[m.n_pp + j] = r.w >= 0 ? kr[r.w] : 0.0;
+    }
+    double *wt = pw_wt(m, pw), *lenv = pw_lenv(m, pw);
+    for (int e = lane; e < m.n_el; e += G) wt[e] = zsr_weight(m, e, env);
+    for (int b = lane; b < m.n_wsec; b += G) lenv[b] = env[m.env_sec_base + 3 * b + 2];
+    gsync<G>(gm);
+}
+
+// The parameter at the state in ys: L_b = L_env,b + sum_e w_e y_e, then the
+// constants kf = kf0 L^-la, kr = kr0 L^-lb of every parameterised process.
+template <int G>
+__device__ __forceinline__ void water_update(const DevMech &m, double *pw, double *kf, double *kr,
+                                          const double *ys, int lane, unsigned gm) {
+    const double *wt = pw_wt(m, pw), *lenv = pw_lenv(m, pw);
+    double *invl = pw_invl(m, pw);
+    for (int b = lane; b < m.n_wsec; b += G) {
+        double v = lenv[b];
+        const int q1 = __ldg(m.pw_ptr + b + 1);
+        for (int q = __ldg(m.pw_ptr + b); q < q1; q++) {
+            const int w = __ldg(m.pw + q);
+            v += wt[hi16(w)] * ys[lo16(w)];
+        }
+        invl[b] = 1.0 / v;
+    }
+    gsync<G>(gm);
+    for (int j = lane; j < m.n_pp; j += G) {
+        const int4 r = __ldg(m.pp + j);
+        const double il = invl[r.y];
+        kf[r.x] = pw[j] * ipowd(il, r.z & 0xff);
+        if (r.w >= 0) kr[r.w] = pw[m.n_pp + j] * ipowd(il, r.z >> 8);
+    }
+    gsync<G>(gm);
+}
+
+// Before a Jacobian assembly at ys: the parameter and constants at ys, then
+// d r_j / d L_b = -(la F_j - lb B_j) / L_b of each parameterised process
+// (F, B its forward and reverse terms) and the sums g = d f_i / d L_b.
+template <int G>
+__device__ __forceinline__ void water_jacobian_prep(const DevMech &m, double *pw, double *kf, double *kr,
+                                                 const double *ys, int lane, unsigned gm) {
+    water_update<G>(m, pw, kf, kr, ys, lane, gm);
+    double *dl = pw_dl(m, pw), *g = pw_g(m, pw);
+    const double *invl = pw_invl(m, pw);
+    for (int j = lane; j < m.n_pp; j += G) {
+        const int4 r = __ldg(m.pp + j);
+        const int4 rp = __ldg(m.rpack + r.x);
+        const int a0 = lo16(rp.x), a1 = hi16(rp.x), a2 = lo16(rp.y);
+        double F = kf[r.x];
+        if (a0 != NONE16) F *= ys[a0];
+        if (a1 != NONE16) F *= ys[a1];
+        if (a2 != NONE16) F *= ys[a2];
+        double B = 0.0;
+        if (r.w >= 0) {
+            const int b0 = lo16(rp.z), b1 = hi16(rp.z), b2 = lo16(rp.w);
+            B = kr[r.w];
+            if (b0 != NONE16) B *= ys[b0];
+            if (b1 != NONE16) B *= ys[b1];
+            if (b2 != NONE16) B *= ys[b2];
+        }
+        dl[j] = -((double)(r.z & 0xff) * F - (double)(r.z >> 8) * B) * invl[r.y];
+    }
+    gsync<G>(gm);
+    for (int i = lane; i < m.n_g; i += G) {
+        double acc = 0.0;
+        const int q1 = __ldg(m.g_ptr + i + 1);
+        for (int q = __ldg(m.g_ptr + i); q < q1; q++) acc += __ldg(m.g_coef + q) * dl[__ldg(m.g_ent + q)];
+        g[i] = acc;
+    }
+    gsync<G>(gm);
+}
+
+// The chain-rule term J_p P_y of Sect. 2.2.2 after the direct assembly:
+// J_ie += g_(i,b) w_e for each electrolyte e of section b.  Each entry is a
+// distinct (row, electrolyte) pair, so lanes need no atomics.
+template <int G, typename LT>
+__device__ __forceinline__ void water_chain(const DevMech &m, double *pw, LT *lu, double gamma, int lane,
+                                         int mode, double *out) {
+    const double *wt = pw_wt(m, pw), *g = pw_g(m, pw);
+    for (int i = lane; i < m.n_ch; i += G) {
+        const int4 r = __ldg(m.ch + i);
+        const double v = g[r.y] * wt[r.z];
+        if (mode == 0)
+            lu[r.x] -= to_lu<LT>(gamma * v);
+        else
+            out[r.w] += v;
+    }
+}
+
 // y in c.ys (written by the caller, who also made it visible to the group)
 // -> f (own positions).  The per-position sums are spread over the cell's
 // lanes by the compiler's balanced assignment (long sums in chunks) and
 // handed back through shared memory (reusing ys).
-template <int G, int NPL, typename LT>
+template <int G, int NPL, typename LT, bool W>
 __device__ __forceinline__ void eval_f_ys(const DevMech &m, const CellPtr<LT> &c, double (&f)[NPL],
                                           int lane, unsigned gm) {
+    if constexpr (W) water_update<G>(m, c.pw, c.kf, c.kr, c.ys, lane, gm);
     for (int k = lane; k < m.R; k += G) c.rs[k] = rate_term(m, k, c.ys, c.kf[k], c.kr);
     gsync<G>(gm);
     double *fs = c.ys;  // y is no longer needed
@@ -346,7 +486,7 @@ __device__ __forceinline__ void eval_f_ys(const DevMech &m, const CellPtr<LT> &c
 }
 
 // y (own positions, registers) -> f (own positions)
-template <int G, int NPL, typename LT>
+template <int G, int NPL, typename LT, bool W>
 __device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, const double (&y)[NPL],
                                        double (&f)[NPL], int lane, unsigned gm) {
 #pragma unroll
@@ -355,11 +495,11 @@ __device__ __forceinline__ void eval_f(const DevMech &m, const CellPtr<LT> &c, c
         if (p < m.n) c.ys[p] = y[s];
     }
     gsync<G>(gm);
-    eval_f_ys<G, NPL, LT>(m, c, f, lane, gm);
+    eval_f_ys<G, NPL, LT, W>(m, c, f, lane, gm);
 }
 
 // f at y = a + b u (own positions), without a register copy of y
-template <int G, int NPL, typename LT>
+template <int G, int NPL, typename LT, bool W>
 __device__ __forceinline__ void eval_f_at(const DevMech &m, const CellPtr<LT> &c, const double (&a)[NPL],
                                           double b, const double (&u)[NPL], double (&f)[NPL], int lane,
                                           unsigned gm) {
@@ -369,7 +509,7 @@ __device__ __forceinline__ void eval_f_at(const DevMech &m, const CellPtr<LT> &c
         if (p < m.n) c.ys[p] = a[s] + b * u[s];
     }
     gsync<G>(gm);
-    eval_f_ys<G, NPL, LT>(m, c, f, lane, gm);
+    eval_f_ys<G, NPL, LT, W>(m, c, f, lane, gm);
 }
 
 // ---- Jacobian gather: J (or M = I - gamma J) at ys into LU storage -----------
@@ -378,9 +518,10 @@ __device__ __forceinline__ void eval_f_at(const DevMech &m, const CellPtr<LT> &c
 // In FP32 the rate constants and y are converted once into scratch that is
 // free at this point (the rate array and the substitution vector), so the
 // per-entry gather does no FP64/FP32 conversion.
-template <int G, typename LT>
+template <int G, typename LT, bool W>
 __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c, double gamma,
                                          int lane, unsigned gm, int mode, double *out) {
+    if constexpr (W) water_jacobian_prep<G>(m, c.pw, c.kf, c.kr, c.ys, lane, gm);
     const LT *kfv, *krv, *yv;
     if constexpr (sizeof(LT) == 4) {
         LT *kf32 = (LT *)c.rs, *kr32 = kf32 + m.R, *y32 = (LT *)c.ys;
@@ -435,8 +576,6 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
                     acc = (LT)0;
                 }
             }
-            gsync<G>(gm);
-            return;
         }
     }
     if constexpr (sizeof(LT) == 8) {  // FP64: one non-zero per lane at a time
@@ -458,6 +597,10 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
         }
     }
     gsync<G>(gm);
+    if constexpr (W) {
+        water_chain<G, LT>(m, c.pw, c.lu, gamma, lane, mode, out);
+        gsync<G>(gm);
+    }
 }
 
 template <typename LT> __device__ __forceinline__ LT tiny_pivot();
@@ -925,7 +1068,7 @@ struct CellStats {
 // the state is written back only on success.  step_io (null: cold start):
 // warm start, in: a value > 0 replaces the initial-step estimate; out: the
 // step held before the final cut to dt, 0 on failure.
-template <int G, int NPL, typename LT>
+template <int G, int NPL, typename LT, bool W>
 __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__restrict__ y_cell,
                               const double *__restrict__ env_cell, double dt, double rtol,
                               const double *__restrict__ atol, int atol_len, int max_steps,
@@ -965,6 +1108,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
         if (rv >= 0) c.kr[rv] = b;
     }
     gsync<G>(gm);
+    if constexpr (W) water_setup<G>(m, c.pw, c.kf, c.kr, env_cell, lane, gm);
 
     // atol is re-read (an L1 hit) rather than held in registers
     auto set_weights = [&]() {
@@ -985,7 +1129,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
 
     const double T = dt, hmin = hmin_frac * dt;
     set_weights();
-    eval_f<G, NPL, LT>(m, c, z[0], f, lane, gm);
+    eval_f<G, NPL, LT, W>(m, c, z[0], f, lane, gm);
     if (any_nonfinite(f)) return fail_early(ST_NONFINITE);
 
     // initial step: the carried one, else Hairer, Norsett & Wanner's
@@ -997,7 +1141,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
         double d0 = wrms<G, NPL>(m, z[0], w, gm), d1 = wrms<G, NPL>(m, f, w, gm);
         double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
         if (h0 > T) h0 = T;
-        eval_f_at<G, NPL, LT>(m, c, z[0], h0, f, e, lane, gm);
+        eval_f_at<G, NPL, LT, W>(m, c, z[0], h0, f, e, lane, gm);
 #pragma unroll
         for (int s = 0; s < NPL; s++) ep[s] = e[s] - f[s];  // ep is free until the first step ends
         double d2 = wrms<G, NPL>(m, ep, w, gm) / h0;
@@ -1053,7 +1197,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                     if (p < n) c.ys[p] = z[0][s];
                 }
                 gsync<G>(gm);
-                assemble<G, LT>(m, c, gamma, lane, gm, 0, nullptr);
+                assemble<G, LT, W>(m, c, gamma, lane, gm, 0, nullptr);
                 lu_fail = !factor<G, LT>(m, c, lane, gm);
                 st.jac++;
                 gamma_lu = gamma;
@@ -1071,7 +1215,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                 for (int s = 0; s < NPL; s++) e[s] = 0.0;
                 const LT scale = (gamma != gamma_lu) ? (LT)2 / ((LT)1 + to_lu<LT>(gamma * rgamma_lu)) : (LT)1;
                 for (int it = 0; it < NEWTON_MAXIT; it++) {
-                    eval_f_at<G, NPL, LT>(m, c, z[0], 1.0, e, f, lane, gm);
+                    eval_f_at<G, NPL, LT, W>(m, c, z[0], 1.0, e, f, lane, gm);
                     st.newton++;
                     if (any_nonfinite(f)) break;
 #pragma unroll
@@ -1129,7 +1273,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                     h *= 0.1;
                     if (h < hmin) { status = ST_ERRTEST; break; }
                     q = 1;
-                    eval_f<G, NPL, LT>(m, c, z[0], f, lane, gm);
+                    eval_f<G, NPL, LT, W>(m, c, z[0], f, lane, gm);
 #pragma unroll
                     for (int s = 0; s < NPL; s++) z[1][s] = h * f[s];
                 } else {

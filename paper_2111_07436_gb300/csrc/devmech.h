@@ -27,6 +27,7 @@ enum {
 };
 
 #define CAMP_NPAR 10  // rate parameters per process
+#define CAMP_ZSR_NY 8 // coefficients of one electrolyte's molality fit
 
 // Lanes that integrate one cell of an n-species mechanism: one warp up to
 // 256 species, else one block of 64, 128 or 256 threads (up to 8 species a
@@ -149,6 +150,35 @@ struct DevMech {
     const int *udiag;     // [n] storage offset of U(i,i) for sparse rows
 
     const int *perm;      // [n] position -> species (declaration order)
+
+    // --- ZSR aerosol water as a parameter (Sect. 2.2.2): with n_wsec > 0 the
+    // liquid volume of section b is L_b(y) = L_env,b + sum_e w_e y_e over its
+    // electrolytes, w_e = 1e-9 P / (R T) / (1000 m_e(a_w)) with the molality
+    // fit sqrt(m_e) = sum_j Y_j a_w^j at a_w = RH (held at the fit's lowest
+    // activity below it).  Section processes then get per-unit-volume
+    // constants kf0, kr0 and the kernels apply kf0 L^-la, kr0 L^-lb at every
+    // state; the Jacobian adds the chain-rule term J_p P_y.
+    int n_wsec;           // sections with a water parameter (0: none)
+    int n_el;             // electrolytes
+    int rh_slot;          // env index of the relative humidity
+    const double *zsr_Y;  // [n_el][CAMP_ZSR_NY]
+    const double *zsr_low;// [n_el]
+    const int *pw_ptr;    // [n_wsec+1] into pw
+    const int *pw;        // electrolyte entries: position | electrolyte << 16
+    int n_pp;             // processes carrying powers of 1/L
+    // x = process, y = section, z = la | lb << 8, w = kr index (-1: none)
+    const int4 *pp;       // [n_pp]
+    // d f_i / d L_b for each (row, section) pair g: sum over entries of
+    // coefficient * d r_j / d L_b of parameterised process j
+    int n_g;
+    const int *g_ptr;     // [n_g+1] into g_ent, g_coef
+    const int *g_ent;     // parameterised process index
+    const double *g_coef; // net stoichiometric coefficient
+    // chain-rule entries J_ij += g_(i,b) w_e: x = LU offset of (i, e),
+    // y = g index, z = electrolyte, w = species-CSR non-zero
+    int n_ch;
+    const int4 *ch;
+    int n_pw;             // per-cell FP64 scratch of the parameter (0: none)
 
     // BDF coefficients: l-vector of prod_{i=1..q}(1 + x/i), local-error
     // constants 1/((q+1) l_1(q)), factorials

@@ -1,6 +1,8 @@
 // Kernels of the batched solve and of its per-step test entry points,
 // templated on the LU precision LT (float: mixed form, double: plain form),
-// the lanes per cell G and the register slots per lane NPL.
+// the lanes per cell G and the register slots per lane NPL; W selects the
+// build with the water parameter's per-state work (mechanisms whose section
+// constants carry powers of 1/L(y)), so that no other mechanism pays for it.
 #pragma once
 #include "cellsolve.cuh"
 #include "launch.h"
@@ -24,13 +26,13 @@ __device__ __forceinline__ unsigned group_mask() {
 // registers and shared memory together (168 a lane fits 12 cells per SM;
 // 224 fits 9); the FP64 form and block cells may take the architectural
 // maximum.
-template <int G, int NPL, typename LT>
+template <int G, int NPL, typename LT, bool W>
 __global__ void __maxnreg__((sizeof(LT) == 8 || G > 32) ? 255 : (NPL >= 6 ? 224 : 168))
     k_solve(DevMech m, SolveArgs a) {
     extern __shared__ __align__(16) char smem[];
     const int group = threadIdx.x / G, lane = threadIdx.x % G;
     const unsigned gm = group_mask<G>();
-    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part);
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw);
     CellPtr<LT> c(smem + group * L.bytes, m);
     long long cell = a.queue ? 0 : (long long)blockIdx.x * a.cpb + group;
     for (;;) {
@@ -49,7 +51,7 @@ __global__ void __maxnreg__((sizeof(LT) == 8 || G > 32) ? 255 : (NPL >= 6 ? 224 
         }
         if (cell >= a.n_cells) break;
         CellStats st;
-        int s = integrate_cell<G, NPL, LT>(m, c, a.state + cell * m.n, a.env + cell * m.n_env, a.dt,
+        int s = integrate_cell<G, NPL, LT, W>(m, c, a.state + cell * m.n, a.env + cell * m.n_env, a.dt,
                                            a.rtol, a.atol, a.atol_len, a.max_steps, a.hmin_frac,
                                            a.step ? a.step + cell : nullptr, lane, gm, st);
         if (lane == 0) {
@@ -82,7 +84,7 @@ __global__ void k_rates(DevMech m, long long n_cells, const double *env, double 
     }
 }
 
-template <int G, int NPL, typename LT>
+template <int G, int NPL, typename LT, bool W>
 __device__ __forceinline__ void load_cell(const DevMech &m, const CellPtr<LT> &c, const double *y,
                                           const double *env, double (&yr)[NPL], int lane, unsigned gm) {
     for (int k = lane; k < m.R; k += G) {
@@ -99,10 +101,11 @@ __device__ __forceinline__ void load_cell(const DevMech &m, const CellPtr<LT> &c
         if (p < m.n) c.ys[p] = yr[s];
     }
     gsync<G>(gm);
+    if constexpr (W) water_setup<G>(m, c.pw, c.kf, c.kr, env, lane, gm);
 }
 
 // f(y) of every cell, [cell][n] in declaration order.
-template <int G, int NPL, typename LT>
+template <int G, int NPL, typename LT, bool W>
 __global__ void k_forcing(DevMech m, long long n_cells, const double *state, const double *env,
                           double *f_out) {
     extern __shared__ __align__(16) char smem[];
@@ -110,11 +113,11 @@ __global__ void k_forcing(DevMech m, long long n_cells, const double *state, con
     const unsigned gm = group_mask<G>();
     const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
     if (cell >= n_cells) return;
-    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part);
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw);
     CellPtr<LT> c(smem + group * L.bytes, m);
     double y[NPL], f[NPL];
-    load_cell<G, NPL, LT>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
-    eval_f<G, NPL, LT>(m, c, y, f, lane, gm);
+    load_cell<G, NPL, LT, W>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
+    eval_f<G, NPL, LT, W>(m, c, y, f, lane, gm);
 #pragma unroll
     for (int s = 0; s < NPL; s++) {
         int p = lane + G * s;
@@ -124,7 +127,7 @@ __global__ void k_forcing(DevMech m, long long n_cells, const double *state, con
 
 // Jacobian values of every cell, [cell][nnzJ] in species-CSR order, computed
 // in precision LT (the assembly precision of the corresponding solve form).
-template <int G, int NPL, typename LT>
+template <int G, int NPL, typename LT, bool W>
 __global__ void k_jacobian(DevMech m, long long n_cells, const double *state, const double *env,
                            double *jac) {
     extern __shared__ __align__(16) char smem[];
@@ -132,17 +135,17 @@ __global__ void k_jacobian(DevMech m, long long n_cells, const double *state, co
     const unsigned gm = group_mask<G>();
     const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
     if (cell >= n_cells) return;
-    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part);
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw);
     CellPtr<LT> c(smem + group * L.bytes, m);
     double y[NPL];
-    load_cell<G, NPL, LT>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
-    assemble<G, LT>(m, c, 0.0, lane, gm, 1, jac + cell * (long long)m.nnzJ);
+    load_cell<G, NPL, LT, W>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
+    assemble<G, LT, W>(m, c, 0.0, lane, gm, 1, jac + cell * (long long)m.nnzJ);
 }
 
 // Solve (I - gamma J(y)) x = b for every cell with the device LU in
 // precision LT; b and x [cell][n] in declaration order; status 4 on a
 // tiny pivot (x then left unwritten).
-template <int G, int NPL, typename LT>
+template <int G, int NPL, typename LT, bool W>
 __global__ void k_lu_solve(DevMech m, long long n_cells, const double *state, const double *env,
                            double gamma, const double *b, double *x, int *status) {
     extern __shared__ __align__(16) char smem[];
@@ -150,11 +153,11 @@ __global__ void k_lu_solve(DevMech m, long long n_cells, const double *state, co
     const unsigned gm = group_mask<G>();
     const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
     if (cell >= n_cells) return;
-    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part);
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw);
     CellPtr<LT> c(smem + group * L.bytes, m);
     double y[NPL];
-    load_cell<G, NPL, LT>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
-    assemble<G, LT>(m, c, gamma, lane, gm, 0, nullptr);
+    load_cell<G, NPL, LT, W>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
+    assemble<G, LT, W>(m, c, gamma, lane, gm, 0, nullptr);
     bool ok = factor<G, LT>(m, c, lane, gm);
     if (lane == 0) status[cell] = ok ? 0 : ST_SINGULAR;
     if (!ok) return;

@@ -1,6 +1,12 @@
 // Launchers for one LU precision; included by solve_f32.cu and solve_f64.cu
-// with CAMP_LT (float / double) and CAMP_SUFFIX (f32 / f64) defined.
+// with CAMP_LT (float / double) and CAMP_SUFFIX (f32 / f64) defined, and by
+// solve_f32w.cu / solve_f64w.cu with CAMP_WATER 1 as well (the builds for
+// mechanisms with a water parameter, suffix f32w / f64w).
 #include "kernels.cuh"
+
+#ifndef CAMP_WATER
+#define CAMP_WATER 0
+#endif
 
 #define CAMP_CAT2(a, b) a##_##b
 #define CAMP_CAT(a, b) CAMP_CAT2(a, b)
@@ -8,6 +14,7 @@
 
 namespace {
 using LT = CAMP_LT;
+constexpr bool W = CAMP_WATER != 0;
 
 // Raise a kernel's dynamic shared-memory limit once to the maximum (the
 // block's 227 KB less the kernel's own static shared memory), so that
@@ -33,7 +40,7 @@ cudaError_t allow_smem(K kern) {
 
 template <int G, int NPL>
 cudaError_t launch_solve_npl(const DevMech &m, const SolveArgs &a, int grid, cudaStream_t s) {
-    auto kern = campdev::k_solve<G, NPL, LT>;
+    auto kern = campdev::k_solve<G, NPL, LT, W>;
     int smem = camp_cell_smem_bytes(m, (int)sizeof(LT)) * a.cpb;
     cudaError_t e = allow_smem<G * 16 + NPL>(kern);
     if (e != cudaSuccess) return e;
@@ -43,7 +50,7 @@ cudaError_t launch_solve_npl(const DevMech &m, const SolveArgs &a, int grid, cud
 
 template <int G, int NPL>
 cudaError_t occupancy_npl(const DevMech &m, int cpb, int *blocks) {
-    auto kern = campdev::k_solve<G, NPL, LT>;
+    auto kern = campdev::k_solve<G, NPL, LT, W>;
     int smem = camp_cell_smem_bytes(m, (int)sizeof(LT)) * cpb;
     cudaError_t e = allow_smem<G * 16 + NPL>(kern);
     if (e != cudaSuccess) return e;
@@ -53,7 +60,7 @@ cudaError_t occupancy_npl(const DevMech &m, int cpb, int *blocks) {
 template <int G, int NPL>
 cudaError_t launch_jac_npl(const DevMech &m, long long n_cells, const double *state,
                            const double *env, double *jac, cudaStream_t s) {
-    auto kern = campdev::k_jacobian<G, NPL, LT>;
+    auto kern = campdev::k_jacobian<G, NPL, LT, W>;
     int smem = camp_cell_smem_bytes(m, (int)sizeof(LT));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -65,7 +72,7 @@ template <int G, int NPL>
 cudaError_t launch_lu_npl(const DevMech &m, long long n_cells, const double *state,
                           const double *env, double gamma, const double *b, double *x, int *status,
                           cudaStream_t s) {
-    auto kern = campdev::k_lu_solve<G, NPL, LT>;
+    auto kern = campdev::k_lu_solve<G, NPL, LT, W>;
     int smem = camp_cell_smem_bytes(m, (int)sizeof(LT));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -74,7 +81,19 @@ cudaError_t launch_lu_npl(const DevMech &m, long long n_cells, const double *sta
 }
 }  // namespace
 
-// one case per instantiated cell shape (lanes per cell, register slots per lane)
+// one case per instantiated cell shape (lanes per cell, register slots per
+// lane).  The water builds hold the 8-slot shapes only: a one-warp cell of
+// fewer species runs with slots to spare.
+#if CAMP_WATER
+#define CAMP_DISPATCH_SHAPE(shape)                                \
+    switch ((shape) > 0 && (shape) < CAMP_SHAPE_BLOCK ? 8 : (shape)) { \
+    case 8: return CALL(32, 8);                                   \
+    case CAMP_SHAPE_BLOCK + 2: return CALL(64, 8);                \
+    case CAMP_SHAPE_BLOCK + 4: return CALL(128, 8);               \
+    case CAMP_SHAPE_BLOCK + 8: return CALL(256, 8);               \
+    default: return cudaErrorInvalidValue;                        \
+    }
+#else
 #define CAMP_DISPATCH_SHAPE(shape)                   \
     switch (shape) {                                 \
     case 1: return CALL(32, 1);                      \
@@ -88,6 +107,7 @@ cudaError_t launch_lu_npl(const DevMech &m, long long n_cells, const double *sta
     case CAMP_SHAPE_BLOCK + 8: return CALL(256, 8);  \
     default: return cudaErrorInvalidValue;           \
     }
+#endif
 
 cudaError_t CAMP_FN(camp_launch_solve)(const DevMech &m, const SolveArgs &a, int grid, cudaStream_t s) {
 #define CALL(G_, N) launch_solve_npl<G_, N>(m, a, grid, s)

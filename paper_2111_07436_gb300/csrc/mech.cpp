@@ -10,6 +10,7 @@
 #include "mech.hpp"
 
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstring>
 #include <stdexcept>
@@ -108,7 +109,33 @@ static void read_processes(const Value &root, HostMech &h) {
     if (rx.kind != Value::Array) throw std::runtime_error("'reactions' must be an array");
     int n_runtime = 0;
     for (auto &r : rx.arr) n_runtime += is_runtime(type_code(r.string("type")));
-    h.env_sec_base = 2 + n_runtime;
+    // parameters (Sect. 2.2.2): a ZSR aerosol-water parameter of the phase,
+    // one instance per section
+    if (const Value *pars = root.find("parameters")) {
+        if (pars->kind != Value::Array) throw std::runtime_error("'parameters' must be an array");
+        for (auto &par : pars->arr) {
+            if (par.string("type") != "ZSR_AEROSOL_WATER")
+                throw std::runtime_error("unknown parameter type '" + par.string("type") + "'");
+            if (!h.el_phase.empty() || h.n_sections == 0)
+                throw std::runtime_error("one water parameter, on a mechanism with aerosol sections");
+            const Value &els = par.at("electrolytes");
+            if (els.kind != Value::Array || els.arr.empty())
+                throw std::runtime_error("a water parameter needs electrolytes");
+            for (auto &e : els.arr) {
+                auto it = std::find(phase.begin(), phase.end(), e.string("species"));
+                if (it == phase.end()) throw std::runtime_error("electrolyte '" + e.string("species") + "' is not a phase species");
+                h.el_phase.push_back((int)(it - phase.begin()));
+                const Value &Y = e.at("Y");
+                if (Y.kind != Value::Array || Y.arr.empty() || Y.arr.size() > CAMP_ZSR_NY)
+                    throw std::runtime_error("an electrolyte's 'Y' must hold 1 to 8 numbers");
+                for (int j = 0; j < CAMP_ZSR_NY; j++) h.zsr_Y.push_back(j < (int)Y.arr.size() ? Y.arr[j].num : 0.0);
+                h.zsr_low.push_back(e.number_or("low_RH", 0.0));
+            }
+        }
+    }
+    const bool water = !h.el_phase.empty();
+    h.rh_slot = water ? 2 + n_runtime : -1;
+    h.env_sec_base = 2 + n_runtime + (water ? 1 : 0);
     h.n_env = h.env_sec_base + 3 * h.n_sections;
 
     int slot = 2;
@@ -200,7 +227,26 @@ static void read_processes(const Value &root, HostMech &h) {
             for (auto &e : p.prod) np += (int)e.second;
             if (np > CAMP_MAXFAC) throw std::runtime_error("more than 3 product factors in a reversible process");
         }
+        if ((p.type == CAMP_P_AQREV || p.type == CAMP_P_COND_ARRHENIUS) && nr == 0)
+            throw std::runtime_error("a condensed-phase reaction needs reactants");
+        if (p.type == CAMP_P_AQREV && np == 0)
+            throw std::runtime_error("a reversible aqueous reaction needs products");
+        // with a water parameter: powers of 1/L in kf and kr.  A molarity is
+        // y phi, phi ~ 1/L, and one division by phi returns a rate in M s^-1
+        // to ppb s^-1, so a side with f concentration factors carries
+        // L^-(f-1); the evaporation constant k_c / (H_cc L) carries L^-1
+        if (water && is_sectioned(p.type)) {
+            if (p.type == CAMP_P_HENRY || p.type == CAMP_P_SIMPOL) p.lb = 1;
+            if (p.type == CAMP_P_AQREV) { p.la = nr - 1; p.lb = np - 1; }
+            if (p.type == CAMP_P_COND_ARRHENIUS) p.la = nr - 1;
+        }
     }
+}
+
+// species index of electrolyte e in section b
+static int electrolyte_species(const HostMech &h, int b, int e) {
+    const int n_phase = (h.n - h.n_gas) / h.n_sections;
+    return h.n_gas + b * n_phase + h.el_phase[e];
 }
 
 // ---- integer structure -----------------------------------------------------
@@ -323,6 +369,12 @@ static void build_structure(HostMech &h) {
     for (auto &p : h.procs)
         for (int j : dependence(p))
             for (int i : touched(p)) pat[(size_t)i * n + j] = 1;
+    // chain rule through the water parameter (Sect. 2.2.2): a process whose
+    // constants carry a power of 1/L_b reaches every electrolyte of section b
+    for (auto &p : h.procs)
+        if (p.la || p.lb)
+            for (size_t e = 0; e < h.el_phase.size(); e++)
+                for (int i : touched(p)) pat[(size_t)i * n + electrolyte_species(h, p.slot, (int)e)] = 1;
     h.rowptr.assign(1, 0);
     h.colidx.clear();
     for (int i = 0; i < n; i++) {
@@ -737,6 +789,67 @@ static void build_tables(HostMech &h) {
             h.jptr.push_back((int)h.jk.size());
         }
 
+    // the water parameter: electrolyte lists per section, the processes that
+    // carry powers of 1/L, d f_i / d L_b sums and the chain-rule entries
+    h.pw_ptr.clear(); h.pw.clear(); h.pp.clear(); h.g_ptr.clear(); h.g_ent.clear();
+    h.g_coef.clear(); h.ch.clear();
+    h.n_pw = 0;
+    if (!h.el_phase.empty()) {
+        const int S = h.n_sections, n_el = (int)h.el_phase.size();
+        h.pw_ptr.assign(1, 0);
+        for (int b = 0; b < S; b++) {
+            for (int e = 0; e < n_el; e++) h.pw.push_back(ip[electrolyte_species(h, b, e)] | (e << 16));
+            h.pw_ptr.push_back((int)h.pw.size());
+        }
+        std::map<std::pair<int, int>, int> gidx;  // (species, section) -> g
+        std::vector<std::pair<int, int>> grow;    // g -> (species, section)
+        std::vector<std::vector<std::pair<int, double>>> gl;
+        for (int k = 0; k < R; k++) {
+            const Process &p = h.procs[k];
+            if (!p.la && !p.lb) continue;
+            const int j = (int)h.pp.size() / 4;
+            h.pp.push_back(k);
+            h.pp.push_back(p.slot);
+            h.pp.push_back(p.la | (p.lb << 8));
+            h.pp.push_back(h.rrev[k]);
+            for (int i : touched(p)) {
+                const double nu = net_coef(p, i);
+                if (nu == 0.0) continue;
+                auto key = std::make_pair(i, p.slot);
+                auto it = gidx.find(key);
+                int g;
+                if (it == gidx.end()) {
+                    g = (int)grow.size();
+                    gidx.emplace(key, g);
+                    grow.push_back(key);
+                    gl.emplace_back();
+                } else {
+                    g = it->second;
+                }
+                gl[g].emplace_back(j, nu);
+            }
+        }
+        h.g_ptr.assign(1, 0);
+        for (auto &v : gl) {
+            for (auto &e : v) { h.g_ent.push_back(e.first); h.g_coef.push_back(e.second); }
+            h.g_ptr.push_back((int)h.g_ent.size());
+        }
+        for (int g = 0; g < (int)grow.size(); g++) {
+            const int i = grow[g].first, b = grow[g].second;
+            for (int e = 0; e < n_el; e++) {
+                const int col = electrolyte_species(h, b, e);
+                h.ch.push_back(off(ip[i], ip[col]));
+                h.ch.push_back(g);
+                h.ch.push_back(e);
+                h.ch.push_back(csr_pos(i, col));
+            }
+        }
+        const int n_pp = (int)h.pp.size() / 4;
+        // per cell: kf0, kr0 and d r / d L per parameterised process, the
+        // weights, L_env and 1 / L per section, and the g sums
+        h.n_pw = 3 * n_pp + n_el + 2 * S + (int)grow.size();
+    }
+
     // sparse factorisation ops, row by row; levels: sparse rows by level, then
     // every block row in one final level (they only need sparse pivots)
     h.fops_ptr.assign(1, 0);
@@ -768,6 +881,16 @@ static void build_tables(HostMech &h) {
     h.flops_jacobian = 2LL * (long long)h.colidx.size();
     for (size_t e = 0; e < h.jk.size(); e++)
         h.flops_jacobian += 2 + (h.jo[2 * e] >= 0) + (h.jo[2 * e + 1] >= 0);
+    if (!h.el_phase.empty()) {
+        // the water parameter per state: a multiply-add per electrolyte and a
+        // reciprocal per section, then the powers of 1/L of each process;
+        // per assembly also d r / d L, the g sums and the chain-rule entries
+        long long upd = 2LL * (long long)h.pw.size() + h.n_sections;
+        for (auto &p : h.procs) upd += p.la + p.lb + ((p.la || p.lb) && p.lb ? 1 : 0);
+        h.flops_forcing += upd;
+        h.flops_jacobian += upd + 10LL * (long long)(h.pp.size() / 4) + 2LL * (long long)h.g_ent.size() +
+                            3LL * (long long)(h.ch.size() / 4);
+    }
     h.flops_factor = 0;
     {
         std::vector<int> lower(n, 0), upper(n, 0);
@@ -978,6 +1101,25 @@ static void validate_tables(const HostMech &h) {
     for (size_t k = 0; k < h.ssplit.size() / 2; k++)
         if (!in(h.ssplit[2 * k], 0, n) || f16(h.ssplit[2 * k + 1]) + h16(h.ssplit[2 * k + 1]) > h.n_spart) fail("ssplit");
     for (int i : h.brow) if (!in(i, 0, h.d)) fail("brow");
+    // water parameter
+    if (!h.el_phase.empty()) {
+        const int S = h.n_sections, n_el = (int)h.el_phase.size(), n_pp = (int)h.pp.size() / 4;
+        const int n_g = (int)h.g_ptr.size() - 1;
+        if ((int)h.pw_ptr.size() != S + 1 || h.pw_ptr.back() != (int)h.pw.size()) fail("pw_ptr");
+        for (int w : h.pw) if (!in(f16(w), 0, n) || !in(h16(w), 0, n_el)) fail("pw");
+        for (int j = 0; j < n_pp; j++) {
+            const int *r = &h.pp[4 * j];
+            if (!in(r[0], 0, R) || !in(r[1], 0, S) || !in(r[3], -1, h.n_rev)) fail("pp");
+            if ((r[2] & 0xff) > CAMP_MAXFAC || (r[2] >> 8) > CAMP_MAXFAC) fail("pp powers");
+        }
+        if (h.g_ptr.front() != 0 || h.g_ptr.back() != (int)h.g_ent.size()) fail("g_ptr");
+        for (int j : h.g_ent) if (!in(j, 0, n_pp)) fail("g_ent");
+        for (size_t c = 0; c < h.ch.size() / 4; c++) {
+            const int *r = &h.ch[4 * c];
+            if (!in(r[0], 0, nlu) || !in(r[1], 0, n_g) || !in(r[2], 0, n_el) || !in(r[3], 0, nnzJ)) fail("ch");
+        }
+        if (!in(h.rh_slot, 2, h.env_sec_base)) fail("rh_slot");
+    }
     for (int i = 0; i < n; i++)
         if (h.su_ptr[i] > h.su_ptr[i + 1] || h.sl_ptr[i] > h.sl_ptr[i + 1]) fail("substitution pointers");
 }
@@ -1083,6 +1225,22 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.jl_ptr = pk.put(h.jl_ptr);
     dm.jl_rec = reinterpret_cast<const int4 *>(pk.put(h.jl_rec));
     dm.su_pack = pk.put(h.su_pack);
+    dm.n_wsec = h.el_phase.empty() ? 0 : h.n_sections;
+    dm.n_el = (int)h.el_phase.size();
+    dm.rh_slot = h.rh_slot;
+    dm.zsr_Y = pk.put(h.zsr_Y);
+    dm.zsr_low = pk.put(h.zsr_low);
+    dm.pw_ptr = pk.put(h.pw_ptr);
+    dm.pw = pk.put(h.pw);
+    dm.n_pp = (int)h.pp.size() / 4;
+    dm.pp = reinterpret_cast<const int4 *>(pk.put(h.pp));
+    dm.n_g = h.g_ptr.empty() ? 0 : (int)h.g_ptr.size() - 1;
+    dm.g_ptr = pk.put(h.g_ptr);
+    dm.g_ent = pk.put(h.g_ent);
+    dm.g_coef = pk.put(h.g_coef);
+    dm.n_ch = (int)h.ch.size() / 4;
+    dm.ch = reinterpret_cast<const int4 *>(pk.put(h.ch));
+    dm.n_pw = h.n_pw;
     bdf_coefficients(dm);
     return pk.img;
 }

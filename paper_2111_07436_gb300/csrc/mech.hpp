@@ -17,6 +17,7 @@ struct Process {
     std::vector<std::pair<int, double>> prod;  // (species, yield), distinct
     double par[CAMP_NPAR] = {};
     int slot = -1;                             // env slot or section
+    int la = 0, lb = 0;                        // powers of 1/L in kf, kr (water parameter)
     bool reversible() const {
         return type == CAMP_P_HENRY || type == CAMP_P_AQREV || type == CAMP_P_SIMPOL;
     }
@@ -28,6 +29,13 @@ struct HostMech {
     std::vector<std::string> species;
     int n = 0, n_gas = 0, n_env = 0, n_sections = 0, env_sec_base = 0;
     std::vector<Process> procs;
+    // ZSR aerosol-water parameter (none when el_phase is empty)
+    int rh_slot = -1;
+    std::vector<int> el_phase;                 // phase-species index per electrolyte
+    std::vector<double> zsr_Y, zsr_low;        // [n_el][CAMP_ZSR_NY], [n_el]
+    std::vector<int> pw_ptr, pw, pp, g_ptr, g_ent, ch;
+    std::vector<double> g_coef;
+    int n_pw = 0;
 
     // integer structure (species numbering except the LU, which is permuted)
     std::vector<int> rowptr, colidx, rxn_map, perm, iperm;

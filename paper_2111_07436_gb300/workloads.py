@@ -373,17 +373,18 @@ def water_mechanism(seed=107, n_sections=8):
     liquid volume, follows the state.  72 gas + 8 x 21 phase species = 240.
     The paper prints no molality fits, so each electrolyte gets a synthetic
     fit of the Jacobson et al. (1996) form sqrt(m) = Y0 + Y1 a_w + Y2 a_w^2:
-    molality log-uniform 4..12 mol/kg at a_w = 0.5 and 0.5..2 at 0.95,
-    joined linearly in sqrt(m) plus a small curvature, held below
-    a_w = 0.5."""
+    molality log-uniform 4..12 mol/kg at a_w = 0.5 and 0.5..2 at 0.95 for
+    the salt, ten times that for the fed species (it holds a tenth of the
+    salt's water per mole), joined linearly in sqrt(m) plus a small
+    curvature, held below a_w = 0.5."""
     rng = np.random.default_rng(seed)
     mech = multiphase_mechanism()
     mech["phases"]["aqueous"].append({"name": "SALT", "atoms": 1})
     hl = [r for r in mech["reactions"] if r["type"] == "HL_PHASE_TRANSFER"]
     electrolytes = []
-    for name in ("SALT", hl[0]["aqueous"]):
-        s05 = math.sqrt(float(_logu(rng, 4.0, 12.0)))
-        s95 = math.sqrt(float(_logu(rng, 0.5, 2.0)))
+    for name, scale in (("SALT", 1.0), (hl[0]["aqueous"], 10.0)):
+        s05 = math.sqrt(scale * float(_logu(rng, 4.0, 12.0)))
+        s95 = math.sqrt(scale * float(_logu(rng, 0.5, 2.0)))
         kappa = float(rng.uniform(-0.5, 0.5))
         slope = (s95 - s05) / 0.45
         # s05 + slope (a - 0.5) + kappa (a - 0.5)(a - 0.95), expanded in a

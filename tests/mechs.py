@@ -73,3 +73,18 @@ def simpol(gas, aq, B, alpha=0.5, Dg=1e-5, MW=0.05, c_tot=None):
         d["c_tot"] = c_tot
     return d
 
+
+
+def water_chain_mechanism(Y1=(3.1, -2.2, -0.3), Y2=(2.4, -1.1)):
+    """Every section process type over two sections with a ZSR water
+    parameter whose electrolytes take part in them (an inert salt S, the
+    dissociation product C and the condensation product E)."""
+    return mech(["G1", "G2"], [
+        henry("G1", "A", H298=2e3 / 101325.0, C_H=1000.0, alpha=0.2),
+        simpol("G2", "B", (2.5e3, -9.0, 0.0, 0.0)),
+        aqrev({"A": 1}, {"C": 1, "D": 1}, A=3e-2, kr=5.0),        # L^-1 on kr
+        aqrev({"B": 2}, {"E": 1}, A=4.0, kr=0.3),                 # L^-1 on kf
+        condensed_arrhenius({"A": 1, "C": 1}, {"E": 1}, A=2e2),   # L^-1 on kf
+        condensed_arrhenius({"D": 1}, {"B": 1}, A=0.1),           # first order: no L
+    ], phase=["A", "B", "C", "D", "E", "S"], sections=2,
+        water=[("S", Y1, 0.0), ("C", Y2, 0.3), ("E", (2.0, -0.5, -0.5), 0.2)])

@@ -251,3 +251,53 @@ def test_random_tiny_mechanisms(form, name):
     assert ok.mean() > 0.9 and (st[ok] == 0).all()
     assert np.array_equal(yg[st != 0], y0[st != 0])
     parity.check(om, y0[ok], env[ok], 300.0, 1e-4, 1e-5, yg[ok], yo[ok])
+
+
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+def test_water_parameter_workload(form):
+    """Aerosol water as a parameter of the state (Sect. 2.2.2): the
+    240-species workload whose section water is held by a salt and by the
+    species that Henry's-law uptake feeds.  The full workload in one launch;
+    a seeded sample of cells re-solved by the oracle."""
+    wl = w.workload(7)
+    gm, om = camp.Mechanism(wl.json()), oracle.Mechanism(wl.json())
+    y0, env = wl.inputs()
+    yg, st = _gpu_solve(gm, y0, env, wl.dt, wl.rtol, wl.atol, *form)
+    assert (st == 0).all()
+    idx = np.sort(np.random.default_rng(7).choice(wl.n_cells, 48, replace=False))
+    yo, sto, _ = om.solve(y0[idx], env[idx], wl.dt, wl.rtol, wl.atol)
+    assert (sto == 0).all()
+    parity.check(om, y0[idx], env[idx], wl.dt, wl.rtol, wl.atol, yg[idx], yo)
+    # the water follows the state
+    dL = [np.max(np.abs(om.water(env[c], yg[c]) / om.water(env[c], y0[c]) - 1)) for c in idx]
+    assert max(dL) > 1e-4
+
+
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+def test_water_parameter_every_section_type(form):
+    """Henry's law, SIMPOL, aqueous equilibria and condensed-phase reactions
+    in sections whose water comes from three electrolytes, two of which the
+    reactions make or consume (the chain-rule Jacobian of every kind)."""
+    from tests import mechs as M
+    text = M.water_chain_mechanism()
+    gm, om = camp.Mechanism(text), oracle.Mechanism(text)
+    C = 77
+    rng = np.random.default_rng(81)
+    y0 = rng.uniform(0.2, 5.0, (C, om.n))
+    env = np.zeros((C, om.n_env))
+    env[:, 0] = rng.uniform(260.0, 310.0, C)
+    env[:, 1] = rng.uniform(5e4, 1.013e5, C)
+    env[:, om.m.rh_slot] = rng.uniform(0.3, 0.97, C)
+    base = om.m.env_section_base
+    env[:, base:base + 3] = np.column_stack([np.full(C, 2e-7), np.full(C, 1e9), np.zeros(C)])
+    env[:, base + 3:base + 6] = np.column_stack([np.full(C, 1e-6), np.full(C, 1e8),
+                                                 10 ** rng.uniform(-13, -11, C)])
+    yg, st = _gpu_solve(gm, y0, env, 120.0, 1e-4, 1e-5, *form)
+    yo, sto, _ = om.solve(y0, env, 120.0, 1e-4, 1e-5)
+    # the first steps of these far-from-equilibrium cells are violent: the
+    # oracle's controller gives up on one of them at rtol 1e-4 (it solves at
+    # 1e-6); a cell may then fail on the GPU too, with its state unchanged
+    ok = sto == 0
+    assert ok.mean() > 0.95 and (st[ok] == 0).all()
+    assert np.array_equal(yg[st != 0], y0[st != 0])
+    parity.check(om, y0[ok], env[ok], 120.0, 1e-4, 1e-5, yg[ok], yo[ok])

@@ -84,21 +84,8 @@ def test_binary_solution_limit_and_zsr_additivity():
     assert m0.water(env_w(m0, T, P, 1.0, [(*SEC, 5e-12)]), np.array([0.0, 4.0]))[0] == 5e-12
 
 
-def _chain_mechanism():
-    """Every section process type, with electrolytes that take part in them."""
-    return M.mech(["G1", "G2"], [
-        M.henry("G1", "A", H298=2e3 / 101325.0, C_H=1000.0, alpha=0.2),
-        M.simpol("G2", "B", (2.5e3, -9.0, 0.0, 0.0)),
-        M.aqrev({"A": 1}, {"C": 1, "D": 1}, A=3e-2, kr=5.0),        # L^-1 on kr
-        M.aqrev({"B": 2}, {"E": 1}, A=4.0, kr=0.3),                 # L^-1 on kf
-        M.condensed_arrhenius({"A": 1, "C": 1}, {"E": 1}, A=2e2),   # L^-1 on kf
-        M.condensed_arrhenius({"D": 1}, {"B": 1}, A=0.1),           # first order: no L
-    ], phase=["A", "B", "C", "D", "E", "S"], sections=2,
-        water=[("S", Y1, 0.0), ("C", Y2, 0.3), ("E", (2.0, -0.5, -0.5), 0.2)])
-
-
 def test_chain_rule_jacobian_matches_central_differences():
-    m = oracle.Mechanism(_chain_mechanism())
+    m = oracle.Mechanism(M.water_chain_mechanism(Y1, Y2))
     i = {s: k for k, s in enumerate(m.m.species)}
     rng = np.random.default_rng(11)
     for trial in range(3):

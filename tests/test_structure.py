@@ -29,6 +29,12 @@ def _mechs():
     out["variety"] = w.process_variety_mechanism()
     out["particles40"] = w.particle_resolved_mechanism(40)
     out["variety_1sec"] = w.process_variety_mechanism(seed=9, n_sections=1)
+    out["water"] = w.water_mechanism()
+    tw = json.loads(json.dumps(out["tiny_aq"]))  # a water parameter over two phase species
+    tw["parameters"] = [{"type": "ZSR_AEROSOL_WATER",
+                         "electrolytes": [{"species": "a3", "Y": [3.0, -2.0]},
+                                          {"species": "a1", "Y": [2.5, -1.0, -0.5], "low_RH": 0.4}]}]
+    out["tiny_aq_water"] = tw
     return out
 
 
@@ -46,7 +52,7 @@ def test_pattern_is_the_numeric_jacobian_support(name):
     if mj.get("aerosol"):
         env[0, m.m.env_section_base + 2::3] = 1e-7         # every section holds water
     kf, kr = m.rate_constants(env[0])
-    J = m.jacobian(kf, kr, y)
+    J = m.jacobian(kf, kr, y, env[0])
     nz = {(i, j) for i, j in zip(*np.nonzero(J))}
     assert nz <= pat
     off = {(i, j) for (i, j) in pat if i != j}
