@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 from tests import mechs as M
+from tests.golden.load import isoprene_soa_table9
 
 # published constants (CODATA 2018)
 LOSCHMIDT_CM3 = 2.686780111e19        # molec cm^-3 at 273.15 K, 101.325 kPa
@@ -207,15 +208,19 @@ def test_condensed_second_order_decay_in_molarity():
     assert y[2] == pytest.approx((5.0 - y[1]) / 2, rel=1e-10)
 
 
-# SIMPOL.1 parameters of isoprene products (Table 9): B1 [K], B2, B3 [1/K], B4
-SOA_B = (3.81e3, -21.3, 0.0, 0.0)
+# SIMPOL.1 parameters of the isoprene products (Table 9, tests/golden):
+# B1 [K], B2, B3 [1/K], B4; the box model's environment (Sect. 4.1)
+TABLE9 = isoprene_soa_table9()
+SOA_B = TABLE9["partition"]["soa1"][2]
+SOA2_B = TABLE9["partition"]["soa2"][2]
+BOX_T, BOX_P = TABLE9["environment"]["T"], TABLE9["environment"]["P"]
 
 
 def test_simpol_partition_follows_raoults_law():
     # Reading: ideal solution of fixed molarity c_tot, so at equilibrium
     # y_g P = (c_a / c_tot) p0, i.e. y_a / y_g = c_tot R T L / p0 with the
     # SIMPOL.1 vapour pressure log10 p0 [atm] = B1/T + B2 + B3 T + B4 ln T
-    T, P, L, c_tot = 290.0, 1e5, 4e-12, 7.0
+    T, P, L, c_tot = BOX_T, BOX_P, 4e-12, 7.0
     mt = dict(alpha=0.1, Dg=1e-5, MW=0.15)
     m = oracle.Mechanism(M.mech(["G"], [
         M.simpol("G", "a", SOA_B, c_tot=c_tot, **mt),
@@ -223,6 +228,7 @@ def test_simpol_partition_follows_raoults_law():
         M.simpol("G", "a", (0.0, 0.0, 0.01, 0.0), c_tot=c_tot, **mt),
         M.simpol("G", "a", (0.0, 0.0, 0.0, 0.5), c_tot=c_tot, **mt),
         M.simpol("G", "a", SOA_B, **mt),
+        M.simpol("G", "a", SOA2_B, c_tot=c_tot, **mt),
     ], phase=["a"], sections=1))
     kf, kr = m.rate_constants(env_of(m, T, P, sections=[(2e-7, 1e9, L)]))
     p0 = 10.0 ** (SOA_B[0] / T + SOA_B[1])
@@ -232,10 +238,14 @@ def test_simpol_partition_follows_raoults_law():
     assert kf[3] / kr[3] == pytest.approx(c_tot * R_LATM * T * L / T ** (0.5 * math.log(10.0)), rel=1e-8)
     # the default solvent is water, 55.5 mol per litre
     assert (kf[4] / kr[4]) / (kf[0] / kr[0]) == pytest.approx(1000.0 / 18.015 / c_tot, rel=1e-12)
+    # Table 9's two products share B1 and differ by 0.4 in B2: ISOP-P1's
+    # vapour pressure is 10^-0.4 of ISOP-P2's at any T, so it partitions
+    # 10^0.4 = 2.51 times more strongly into the same particles
+    assert (kf[0] / kr[0]) / (kf[5] / kr[5]) == pytest.approx(10.0 ** (SOA2_B[1] - SOA_B[1]), rel=1e-12)
 
 
 def test_simpol_two_compartment_relaxation():
-    T, P, L = 290.0, 1e5, 4e-12
+    T, P, L = BOX_T, BOX_P, 4e-12
     m = oracle.Mechanism(M.mech(["G"], [M.simpol("G", "a", SOA_B, alpha=0.1, c_tot=7.0)],
                                 phase=["a"], sections=1))
     env = env_of(m, T, P, sections=[(2e-7, 1e9, L)])

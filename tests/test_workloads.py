@@ -102,3 +102,37 @@ def test_particle_resolved_inputs():
     assert np.allclose(N, N[:, :1]) and ((N.sum(axis=1) >= 1e8) & (N.sum(axis=1) <= 1e10)).all()
     np.testing.assert_allclose(L, N * 4.0 / 3.0 * np.pi * r ** 3)
     assert (y[:, 18:] == 0).all()
+
+
+def test_process_variety_isoprene_chemistry_is_table9():
+    """The isoprene oxidation and SOA partitioning of the process-variety
+    mechanism carry the paper's printed values (Table 9, tests/golden)."""
+    from tests.golden.load import isoprene_soa_table9
+    t9 = isoprene_soa_table9()
+    mj = w.process_variety_mechanism()
+    name = {"ISOP-P1": "ISOPP1", "ISOP-P2": "ISOPP2"}
+    gas = [r for r in mj["reactions"] if r["type"] == "ARRHENIUS" and "ISOP" in r["reactants"]]
+    assert len(gas) == len(t9["gas"])
+    for reactants, products, A, C in t9["gas"].values():
+        r = next(r for r in gas if r["reactants"] == reactants)
+        assert r["products"] == {name[k]: v for k, v in products.items()}
+        assert (r["A"], r["C"], r["B"], r["E"]) == (A, C, 0.0, 0.0)
+    simpol = {r["gas"]: r for r in mj["reactions"] if r["type"] == "SIMPOL_PHASE_TRANSFER"}
+    for g, aero, B in t9["partition"].values():
+        assert simpol[name[g]]["aqueous"] == aero
+        assert tuple(simpol[name[g]]["B"]) == B
+
+
+def test_water_mechanism_inputs():
+    mj = w.water_mechanism()
+    lay = w.layout(mj)
+    assert len(lay.species) == 240 and "RH" in lay.env
+    y, env = w.cells(mj, 64, seed=5)
+    rh = env[:, lay.env.index("RH")]
+    assert ((rh >= 0.5) & (rh <= 0.95)).all()
+    base = lay.env.index("bin0.r")
+    assert (env[:, base + 2::3] == 0.0).all()          # all water from the electrolytes
+    salt = y[:, [lay.species.index(f"bin{b}.SALT") for b in range(8)]]
+    r, N = env[:, base::3], env[:, base + 1::3]
+    assert np.allclose(salt / (N * r ** 3), salt[0, 0] / (N[0, 0] * r[0, 0] ** 3) *
+                       (env[0, 1] / env[0, 0]) / (env[:, 1:2] / env[:, 0:1]), rtol=1e-12)
