@@ -490,6 +490,61 @@ static void balance_level(std::vector<int> &rows, int b, int e, int G, Cost cost
 // columns that several chunks (or the rest of the row) write go to chunk
 // partial sums.  One lane then adds the partials in order and finishes the
 // row's remaining pivots (the tail).
+// How one long row splits for a chunk length CH: chunks of op indices (at
+// pivot boundaries, none writing a column another chunk's pivot reads), the
+// first op of the tail, and the shared columns (written by several chunks
+// or by the tail), each of which takes one partial slot per chunk.
+struct RowSplit {
+    std::vector<std::vector<int>> chunks;
+    int tail_from = 0;
+    std::vector<int> shared;
+    std::unordered_map<int, int> slot;
+};
+static RowSplit split_row(const std::vector<uint32_t> &ops, int CH) {
+    auto tgt = [](uint32_t op) { return (int)(op & 0xFFFFu); };
+    RowSplit rs;
+    std::vector<std::pair<int, int>> groups;  // [begin, end) in ops: a DIV and its updates
+    for (int q = 0; q < (int)ops.size(); q++) {
+        if ((ops[q] & CAMP_OP_DIV) || groups.empty()) groups.push_back({q, q + 1});
+        else groups.back().second = q + 1;
+    }
+    std::unordered_map<int, std::vector<int>> writers;  // column -> chunks writing it
+    std::vector<int> cur;
+    rs.tail_from = (int)ops.size();
+    for (auto &g : groups) {
+        const int c = (int)rs.chunks.size();
+        auto it = writers.find(tgt(ops[g.first]));
+        bool foreign = false;
+        if (it != writers.end())
+            for (int w : it->second) foreign |= (w != c);
+        if (foreign) { rs.tail_from = g.first; break; }
+        for (int q = g.first; q < g.second; q++) {
+            cur.push_back(q);
+            auto &v = writers[tgt(ops[q])];
+            if (v.empty() || v.back() != c) v.push_back(c);
+        }
+        if ((int)cur.size() >= CH) { rs.chunks.push_back(cur); cur.clear(); }
+    }
+    if (!cur.empty()) rs.chunks.push_back(cur);
+    if (rs.chunks.size() < 2) return rs;
+    std::unordered_map<int, int> tail_cols;
+    for (int q = rs.tail_from; q < (int)ops.size(); q++) tail_cols[tgt(ops[q])] = 1;
+    for (auto &g : groups)
+        for (int q = g.first; q < g.second && q < rs.tail_from; q++) {
+            const int t = tgt(ops[q]);
+            if (rs.slot.count(t)) continue;
+            if (writers[t].size() >= 2 || tail_cols.count(t)) {
+                rs.slot[t] = (int)rs.shared.size();
+                rs.shared.push_back(t);
+            }
+        }
+    return rs;
+}
+
+// Partial slots one level may use (FP64 values of per-cell shared memory):
+// a longer chunk length is taken when the level's splits would need more.
+static const long long kLevelPartials = 2048;
+
 static void build_factor_jobs(HostMech &h) {
     const int NL = camp_cell_lanes(h.n);
     h.ljob_ptr.assign(1, 0);
@@ -501,69 +556,52 @@ static void build_factor_jobs(HostMech &h) {
     h.ltail.clear();
     h.n_lpart = 0;
     auto tgt = [](uint32_t op) { return (int)(op & 0xFFFFu); };
+    auto row_ops = [&](int i) {
+        return std::vector<uint32_t>(h.fops.begin() + h.fops_ptr[i], h.fops.begin() + h.fops_ptr[i + 1]);
+    };
     for (size_t l = 0; l + 1 < h.flev_ptr.size(); l++) {
         const int rb = h.flev_ptr[l], re = h.flev_ptr[l + 1];
-        long long total = 0;
+        long long total = 0, longest = 0;
         for (int r = rb; r < re; r++) {
             const int i = h.frow[r];
             total += h.fops_ptr[i + 1] - h.fops_ptr[i] + 2;
+            longest = std::max<long long>(longest, h.fops_ptr[i + 1] - h.fops_ptr[i]);
         }
-        const int CH = std::max(16, (int)((total + NL - 1) / NL));
+        // chunk length: the level's mean load per lane, at least 16 ops, and
+        // long enough that the level's partial slots stay within budget
+        int CH = std::max(16, (int)((total + NL - 1) / NL));
+        if (NL > 32) {
+            for (;;) {
+                long long need = 0;
+                for (int r = rb; r < re; r++) {
+                    const std::vector<uint32_t> ops = row_ops(h.frow[r]);
+                    if ((int)ops.size() <= 2 * CH) continue;
+                    const RowSplit rs = split_row(ops, CH);
+                    if (rs.chunks.size() >= 2) need += (long long)rs.chunks.size() * (long long)rs.shared.size();
+                }
+                if (need <= kLevelPartials || CH >= longest) break;
+                CH *= 2;
+            }
+        }
         struct Job { std::vector<uint32_t> ops; int row, recip, ns, pbase; };
         std::vector<Job> jobs;
         int lpart = 0;
         for (int r = rb; r < re; r++) {
             const int i = h.frow[r];
             const int recip = i < h.d ? 1 : 0;
-            std::vector<uint32_t> ops(h.fops.begin() + h.fops_ptr[i], h.fops.begin() + h.fops_ptr[i + 1]);
+            std::vector<uint32_t> ops = row_ops(i);
             if (NL <= 32 || (int)ops.size() <= 2 * CH) { jobs.push_back({ops, i, recip, 0, 0}); continue; }
-            // pivot groups: a DIV and its updates
-            std::vector<std::pair<int, int>> groups;  // [begin, end) in ops
-            for (int q = 0; q < (int)ops.size(); q++) {
-                if ((ops[q] & CAMP_OP_DIV) || groups.empty()) groups.push_back({q, q + 1});
-                else groups.back().second = q + 1;
-            }
-            std::vector<std::vector<int>> chunks;  // op indices
-            std::unordered_map<int, std::vector<int>> writers;  // column -> chunks writing it
-            std::vector<int> cur;
-            int tail_from = (int)ops.size();
-            for (auto &g : groups) {
-                const int c = (int)chunks.size();
-                auto it = writers.find(tgt(ops[g.first]));
-                bool foreign = false;
-                if (it != writers.end())
-                    for (int w : it->second) foreign |= (w != c);
-                if (foreign) { tail_from = g.first; break; }
-                for (int q = g.first; q < g.second; q++) {
-                    cur.push_back(q);
-                    auto &v = writers[tgt(ops[q])];
-                    if (v.empty() || v.back() != c) v.push_back(c);
-                }
-                if ((int)cur.size() >= CH) { chunks.push_back(cur); cur.clear(); }
-            }
-            if (!cur.empty()) chunks.push_back(cur);
-            if (chunks.size() < 2) { jobs.push_back({ops, i, recip, 0, 0}); continue; }
-            std::unordered_map<int, int> tail_cols;
-            for (int q = tail_from; q < (int)ops.size(); q++) tail_cols[tgt(ops[q])] = 1;
-            std::vector<int> shared;
-            std::unordered_map<int, int> slot;
-            for (auto &g : groups)
-                for (int q = g.first; q < g.second && q < tail_from; q++) {
-                    const int t = tgt(ops[q]);
-                    if (slot.count(t)) continue;
-                    if (writers[t].size() >= 2 || tail_cols.count(t)) {
-                        slot[t] = (int)shared.size();
-                        shared.push_back(t);
-                    }
-                }
-            const int ns = (int)shared.size(), nch = (int)chunks.size();
+            const RowSplit rs = split_row(ops, CH);
+            if (rs.chunks.size() < 2) { jobs.push_back({ops, i, recip, 0, 0}); continue; }
+            const int ns = (int)rs.shared.size(), nch = (int)rs.chunks.size();
             if (ns > 0x7fff || nch > 0xffff) throw std::runtime_error("factor chunks do not fit their fields");
             for (int c = 0; c < nch; c++) {
                 Job jb{{}, i, 0, ns, lpart + c * ns};
-                for (int q : chunks[c]) {
+                for (int q : rs.chunks[c]) {
                     uint32_t op = ops[q];
-                    if (!(op & CAMP_OP_DIV) && slot.count(tgt(op)))
-                        op = (op & 0xFFFF0000u) | 0x8000u | (uint32_t)slot[tgt(op)];
+                    auto it = rs.slot.find(tgt(op));
+                    if (!(op & CAMP_OP_DIV) && it != rs.slot.end())
+                        op = (op & 0xFFFF0000u) | 0x8000u | (uint32_t)it->second;
                     jb.ops.push_back(op);
                 }
                 jobs.push_back(jb);
@@ -573,12 +611,12 @@ static void build_factor_jobs(HostMech &h) {
             rd.y = (int)h.lred_off.size();
             rd.z = ns | (nch << 16);
             rd.w = lpart;
-            for (int t : shared) h.lred_off.push_back(t);
+            for (int t : rs.shared) h.lred_off.push_back(t);
             h.lred.push_back(rd.x); h.lred.push_back(rd.y); h.lred.push_back(rd.z); h.lred.push_back(rd.w);
             // the tail's ops go after the level's jobs; until then x holds
             // -1 - (the tail's first op within the row)
-            h.ltail.push_back(-1 - tail_from);
-            h.ltail.push_back((int)ops.size() - tail_from);
+            h.ltail.push_back(-1 - rs.tail_from);
+            h.ltail.push_back((int)ops.size() - rs.tail_from);
             h.ltail_rows.push_back(i);
             lpart += nch * ns;
         }

@@ -88,3 +88,16 @@ def water_chain_mechanism(Y1=(3.1, -2.2, -0.3), Y2=(2.4, -1.1)):
         condensed_arrhenius({"D": 1}, {"B": 1}, A=0.1),           # first order: no L
     ], phase=["A", "B", "C", "D", "E", "S"], sections=2,
         water=[("S", Y1, 0.0), ("C", Y2, 0.3), ("E", (2.0, -0.5, -0.5), 0.2)])
+
+
+def water_particles_mechanism(n_particles):
+    """The particle-resolved mechanism with an inert salt in every particle
+    and a ZSR water parameter over the salt and the sulphate that the
+    particles' H2O2 + HSO3 chemistry makes (made-up molality fits)."""
+    from paper_2111_07436_gb300 import workloads as w
+    mj = w.particle_resolved_mechanism(n_particles)
+    mj["phases"]["aqueous"].append({"name": "SALT", "atoms": 1})
+    mj["parameters"] = [{"type": "ZSR_AEROSOL_WATER", "electrolytes": [
+        {"species": "SALT", "Y": [3.3, -2.6, 0.1], "low_RH": 0.45},
+        {"species": "SULF", "Y": [6.0, -4.5], "low_RH": 0.45}]}]
+    return mj

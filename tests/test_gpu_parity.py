@@ -301,3 +301,20 @@ def test_water_parameter_every_section_type(form):
     assert ok.mean() > 0.95 and (st[ok] == 0).all()
     assert np.array_equal(yg[st != 0], y0[st != 0])
     parity.check(om, y0[ok], env[ok], 120.0, 1e-4, 1e-5, yg[ok], yo[ok])
+
+
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+@pytest.mark.parametrize("n_particles,C", [(40, 48), (100, 8), (160, 4)])
+def test_water_parameter_on_block_cells(form, n_particles, C):
+    """The water builds of the block shapes (64, 128 and 256 threads per
+    cell: 338, 818 and 1298 species): particles whose water is held by a
+    salt and by the sulphate their chemistry makes."""
+    from tests import mechs as M
+    mj = M.water_particles_mechanism(n_particles)
+    text = json.dumps(mj)
+    gm, om = camp.Mechanism(text), oracle.Mechanism(text)
+    y0, env = w.cells(mj, C, seed=73)
+    yg, st = _gpu_solve(gm, y0, env, 180.0, 1e-4, 1e-5, *form)
+    yo, sto, _ = om.solve(y0, env, 180.0, 1e-4, 1e-5)
+    assert (st == 0).all() and (sto == 0).all()
+    parity.check(om, y0, env, 180.0, 1e-4, 1e-5, yg, yo)

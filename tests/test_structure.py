@@ -35,6 +35,8 @@ def _mechs():
                          "electrolytes": [{"species": "a3", "Y": [3.0, -2.0]},
                                           {"species": "a1", "Y": [2.5, -1.0, -0.5], "low_RH": 0.4}]}]
     out["tiny_aq_water"] = tw
+    from tests import mechs as M
+    out["water_particles40"] = M.water_particles_mechanism(40)
     return out
 
 
