@@ -90,6 +90,9 @@ typedef struct {
     int64_t flops_jacobian; /* one assembly of I - gamma J */
     int64_t flops_factor;   /* one sparse LU factorisation */
     int64_t flops_solve;    /* one forward + backward substitution */
+    int32_t env_rh;         /* env index of the relative humidity, -1 without
+                               a ZSR_AEROSOL_WATER parameter */
+    int32_t n_electrolytes; /* electrolytes of the water parameter (0: none) */
 } camp_mech_info;
 
 /*

@@ -35,7 +35,8 @@ class MechInfo(ctypes.Structure):
                 ("lu_storage", ctypes.c_int32), ("smem_per_cell_mixed", ctypes.c_int32),
                 ("smem_per_cell_fp64", ctypes.c_int32), ("factor_updates", ctypes.c_int64),
                 ("flops_forcing", ctypes.c_int64), ("flops_jacobian", ctypes.c_int64),
-                ("flops_factor", ctypes.c_int64), ("flops_solve", ctypes.c_int64)]
+                ("flops_factor", ctypes.c_int64), ("flops_solve", ctypes.c_int64),
+                ("env_rh", ctypes.c_int32), ("n_electrolytes", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

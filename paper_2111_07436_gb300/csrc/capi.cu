@@ -223,6 +223,8 @@ int camp_mech_info_get(const camp_mech *m, camp_mech_info *o) {
     o->flops_jacobian = h.flops_jacobian;
     o->flops_factor = h.flops_factor;
     o->flops_solve = h.flops_solve;
+    o->env_rh = h.rh_slot;
+    o->n_electrolytes = (int32_t)h.el_phase.size();
     return CAMP_OK;
 }
 

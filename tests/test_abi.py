@@ -1,6 +1,7 @@
 """The C ABI library builds, loads and exports every declared entry point
 (no GPU: nothing here launches a kernel)."""
 import ctypes
+import json
 import os
 import re
 
@@ -58,3 +59,13 @@ def test_info_reports_the_dense_block():
     assert inf.n_species == 72 and inf.n_rxn == 186 and inf.n_env == 48
     assert 0 < inf.dense_block <= 72 and inf.nnz_lu >= inf.nnz_jac
     assert inf.smem_per_cell_fp64 > inf.smem_per_cell_mixed
+    assert inf.env_rh == -1 and inf.n_electrolytes == 0
+
+
+def test_info_reports_the_water_parameter():
+    from paper_2111_07436_gb300 import workloads as w
+    mj = w.water_mechanism()
+    inf = camp.Mechanism(json.dumps(mj), device=False).info
+    lay = w.layout(mj)
+    assert inf.n_electrolytes == 2 and inf.env_rh == lay.env.index("RH")
+    assert inf.n_env == len(lay.env)
