@@ -28,6 +28,13 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {"small": 1, "gas72": 2, "multiphase232": 3, "uneven": 4, "serving": 5, "particles": 6,
              "water": 7}
 FP64_PEAK_NOMINAL_GFLOPS = 1250.0  # GB300 dense FP64, nominal
+# DRAM bytes (read + write) per cell of one mixed-form k_solve launch, from
+# one ncu capture of the same kernel on a smaller launch of the same
+# workload (gas-72: 4096 cells, 4.18 MB; particles: 512 cells, 5.91 MB;
+# water: 2048 cells, 5.95 MB): the inputs only, so traffic scales with the
+# cells.  To be taken again whenever the kernel changes.
+DRAM_BYTES_PER_CELL = {"gas72": 4.180480e6 / 4096, "particles": 5.905152e6 / 512,
+                       "water": 5.947136e6 / 2048}
 
 
 def args():
@@ -301,7 +308,9 @@ def main():
             "peak": peak64, "peak_source": "measured FP64 FMA chains on this GPU (camp_probe_fma_rate)",
             "peak_nominal": FP64_PEAK_NOMINAL_GFLOPS, "peak_fp32_measured": peak32,
             "frac": achieved / peak64, "frac_of_nominal": achieved / FP64_PEAK_NOMINAL_GFLOPS,
-            "traffic": None,
+            "traffic": (DRAM_BYTES_PER_CELL[a.workload] * C
+                        if variant == camp.VARIANT_MIXED and a.workload in DRAM_BYTES_PER_CELL else None),
+            "traffic_unit": "bytes per launch (ncu dram read + write, scaled by cells)",
             "kernel": "k_solve", "fp64_flops_per_launch": fp64, "lu_flops_per_launch": lu,
             "lu_dtype": "f32" if variant == camp.VARIANT_MIXED else "f64"}
     hbm = (y0.nbytes * 2 + env.nbytes + C * 4) / (ms / 1e3) / 1e9
