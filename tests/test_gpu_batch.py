@@ -160,3 +160,26 @@ def test_full_size_uneven_batch_sampled(cuda):
         assert (so == 0).all()
         for y_gpu, _ in (mixed[gi], plain[gi]):
             parity.check(om, g["y0"][idx], g["env_np"][idx], 180.0, 1e-4, 1e-5, y_gpu[idx], yo)
+
+
+def test_batch_with_a_water_parameter_mechanism(cuda):
+    """A water-parameter mechanism (its own kernel build) beside a gas-only
+    one in one batched call: each group equals its lone solve bit for bit."""
+    import torch
+    gas, water = w.large_gas_mechanism(), w.water_mechanism()
+    groups = []
+    for mj, C, seed in ((gas, 700, 51), (water, 300, 52)):
+        y, env = w.cells(mj, C, seed=seed)
+        groups.append({"mech": camp.Mechanism(json.dumps(mj)), "y0": y,
+                       "env": torch.tensor(env, device=cuda),
+                       "atol": torch.full((1,), 1e-5, dtype=torch.float64, device=cuda),
+                       "workspace": camp.workspace(cuda)})
+    _reset(groups)
+    camp.solve_batch(_args(groups), 180.0, 1e-4)
+    torch.cuda.synchronize()
+    for g in groups:
+        ty = torch.tensor(g["y0"], device="cuda")
+        st = g["mech"].solve(ty, g["env"], 180.0, 1e-4, 1e-5, persistent=True)
+        torch.cuda.synchronize()
+        assert (st.cpu().numpy() == 0).all() and (g["status"].cpu().numpy() == 0).all()
+        assert np.array_equal(ty.cpu().numpy(), g["state"].cpu().numpy())
