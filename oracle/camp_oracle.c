@@ -399,7 +399,9 @@ void om_water(const om_mech *m, const double *env, const double *y, double *L) {
 }
 
 /* kf, kr of om_rate_constants (per unit volume on the sections) with the
- * powers of 1/L at the current liquid volumes applied */
+ * powers of 1/L at the current liquid volumes applied.  A section whose
+ * water is not positive takes no part, as a section with no water in env
+ * does (its processes' constants are 0). */
 static void volume_constants(const om_mech *m, const double *kf, const double *kr,
                              const double *L, double *kfe, double *kre) {
     for (int k = 0; k < m->n_rxn; k++) {
@@ -407,6 +409,10 @@ static void volume_constants(const om_mech *m, const double *kf, const double *k
         kfe[k] = kf[k];
         kre[k] = kr[k];
         if (r->section < 0) continue;
+        if (!(L[r->section] > 0.0)) {
+            kfe[k] = kre[k] = 0.0;
+            continue;
+        }
         int la, lb;
         water_powers(r, &la, &lb);
         kfe[k] = kf[k] / ipow(L[r->section], la);
@@ -465,6 +471,7 @@ void om_jacobian_env(const om_mech *m, const double *env, const double *kf, cons
             for (int i = 0; i < r->n_prod; i++) B *= ipow(y[r->prod[i]], (int)r->yield[i]);
         }
         const int b = r->section;
+        if (!(L[b] > 0.0)) continue;   /* a dry section takes no part */
         double dr = -(la * F - lb * B) / L[b];
         for (int i = 0; i < r->n_react; i++) Jp[r->react[i] * S + b] -= r->rstoich[i] * dr;
         for (int i = 0; i < r->n_prod; i++) Jp[r->prod[i] * S + b] += r->yield[i] * dr;

@@ -361,7 +361,9 @@ __device__ __forceinline__ void water_setup(const DevMech &m, double *pw, const 
 }
 
 // The parameter at the state in ys: L_b = L_env,b + sum_e w_e y_e, then the
-// constants kf = kf0 L^-la, kr = kr0 L^-lb of every parameterised process.
+// constants kf = kf0 L^-la, kr = kr0 L^-lb of every section process.  A
+// section whose water is not positive takes no part, as one with no water
+// in env does: 1/L is stored as 0 and its processes' constants as 0.
 template <int G>
 __device__ __forceinline__ void water_update(const DevMech &m, double *pw, double *kf, double *kr,
                                           const double *ys, int lane, unsigned gm) {
@@ -374,14 +376,15 @@ __device__ __forceinline__ void water_update(const DevMech &m, double *pw, doubl
             const int w = __ldg(m.pw + q);
             v += wt[hi16(w)] * ys[lo16(w)];
         }
-        invl[b] = 1.0 / v;
+        invl[b] = v > 0.0 ? 1.0 / v : 0.0;
     }
     gsync<G>(gm);
     for (int j = lane; j < m.n_pp; j += G) {
         const int4 r = __ldg(m.pp + j);
         const double il = invl[r.y];
-        kf[r.x] = pw[j] * ipowd(il, r.z & 0xff);
-        if (r.w >= 0) kr[r.w] = pw[m.n_pp + j] * ipowd(il, r.z >> 8);
+        const bool wet = il > 0.0;
+        kf[r.x] = wet ? pw[j] * ipowd(il, r.z & 0xff) : 0.0;
+        if (r.w >= 0) kr[r.w] = wet ? pw[m.n_pp + j] * ipowd(il, r.z >> 8) : 0.0;
     }
     gsync<G>(gm);
 }

@@ -165,8 +165,10 @@ struct DevMech {
     const double *zsr_low;// [n_el]
     const int *pw_ptr;    // [n_wsec+1] into pw
     const int *pw;        // electrolyte entries: position | electrolyte << 16
-    int n_pp;             // processes carrying powers of 1/L
-    // x = process, y = section, z = la | lb << 8, w = kr index (-1: none)
+    int n_pp;             // section processes, rescaled at every state
+    // x = process, y = section, z = la | lb << 8 (powers of 1/L in kf, kr),
+    // w = kr index (-1: none); a section whose water is not positive takes
+    // no part (its processes' constants are 0)
     const int4 *pp;       // [n_pp]
     // d f_i / d L_b for each (row, section) pair g: sum over entries of
     // coefficient * d r_j / d L_b of parameterised process j

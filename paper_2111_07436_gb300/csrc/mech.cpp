@@ -842,14 +842,18 @@ static void build_tables(HostMech &h) {
         std::map<std::pair<int, int>, int> gidx;  // (species, section) -> g
         std::vector<std::pair<int, int>> grow;    // g -> (species, section)
         std::vector<std::vector<std::pair<int, double>>> gl;
+        // every section process is rescaled at each state (a section whose
+        // water is not positive switches its processes off); only those with
+        // powers of 1/L enter the chain rule
         for (int k = 0; k < R; k++) {
             const Process &p = h.procs[k];
-            if (!p.la && !p.lb) continue;
+            if (!is_sectioned(p.type)) continue;
             const int j = (int)h.pp.size() / 4;
             h.pp.push_back(k);
             h.pp.push_back(p.slot);
             h.pp.push_back(p.la | (p.lb << 8));
             h.pp.push_back(h.rrev[k]);
+            if (!p.la && !p.lb) continue;
             for (int i : touched(p)) {
                 const double nu = net_coef(p, i);
                 if (nu == 0.0) continue;

@@ -318,3 +318,24 @@ def test_water_parameter_on_block_cells(form, n_particles, C):
     yo, sto, _ = om.solve(y0, env, 180.0, 1e-4, 1e-5)
     assert (st == 0).all() and (sto == 0).all()
     parity.check(om, y0, env, 180.0, 1e-4, 1e-5, yg, yo)
+
+
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+def test_water_parameter_dry_sections(form):
+    """Sections whose electrolytes hold no water take no part (the reading
+    used for a section with no water in env); here every other cell has two
+    such sections."""
+    wl = w.workload(7)
+    gm, om = camp.Mechanism(wl.json()), oracle.Mechanism(wl.json())
+    y0, env = wl.inputs(96)
+    lay = w.layout(wl.mech)
+    for b in (0, 3):
+        for e in wl.mech["parameters"][0]["electrolytes"]:
+            y0[::2, lay.species.index(f"bin{b}.{e['species']}")] = 0.0
+    assert om.water(env[0], y0[0])[0] == 0.0
+    yg, st = _gpu_solve(gm, y0, env, wl.dt, wl.rtol, wl.atol, *form)
+    yo, sto, _ = om.solve(y0, env, wl.dt, wl.rtol, wl.atol)
+    assert (st == 0).all() and (sto == 0).all()
+    parity.check(om, y0, env, wl.dt, wl.rtol, wl.atol, yg, yo)
+    dry = [lay.species.index(s) for s in lay.species if s.startswith("bin0.")]
+    assert np.array_equal(yg[::2][:, dry], y0[::2][:, dry])

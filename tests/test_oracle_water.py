@@ -192,3 +192,24 @@ def test_inert_water_equals_the_same_volume_given_in_env():
     yp, sp, _ = om_p.solve(y, env_p, 60.0, 1e-9, 1e-12, threads=2)
     assert (sw == 0).all() and (sp == 0).all()
     np.testing.assert_allclose(yw, yp, rtol=1e-6, atol=1e-9)
+
+
+def test_a_section_without_water_takes_no_part():
+    """Reading: like a section with no water in env, a section whose
+    electrolytes hold no water (and L_env = 0) takes no part; the cell still
+    solves, equal to the same cell with that section's particles removed."""
+    T, P = STP
+    m = oracle.Mechanism(M.mech(["G"], [
+        M.henry("G", "A", H298=3e3 / 101325.0, alpha=0.2),
+        M.aqrev({"A": 1}, {"B": 1, "C": 1}, A=1e-3, kr=10.0),
+        M.condensed_arrhenius({"B": 1}, {"C": 1}, A=0.05),
+    ], phase=["S", "A", "B", "C"], sections=2, water=[("S", Y1, 0.0)]))
+    y0 = np.array([10.0, 2.0, 0.0, 0.5, 0.0, 0.0, 0.3, 0.2, 0.1])  # section 1: no salt
+    dry = env_w(m, T, P, 0.8, [(1e-6, 1e8, 0.0), (1e-6, 1e8, 0.0)])
+    gone = env_w(m, T, P, 0.8, [(1e-6, 1e8, 0.0), (1e-6, 0.0, 0.0)])  # no particles
+    assert m.water(dry, y0)[1] == 0.0
+    y1, s1, _ = m.integrate(y0, dry, 300.0, 1e-10, 1e-14)
+    y2, s2, _ = m.integrate(y0, gone, 300.0, 1e-10, 1e-14)
+    assert s1 == 0 and s2 == 0
+    np.testing.assert_allclose(y1, y2, rtol=1e-9, atol=1e-14)
+    assert (y1[5:] == y0[5:]).all() and y1[2] != y0[2]   # section 1 frozen, section 0 active
