@@ -96,3 +96,24 @@ def test_cancel_withdraws_only_pending_requests(mechs):
     with pytest.raises(camp.CampError):  # collected: no longer known
         srv.cancel(jobs[0][0])
     srv.close()
+
+
+def test_water_parameter_chunks_equal_lone_solves(mechs):
+    """Chunks of a water-parameter mechanism (its own kernel build) served
+    beside gas chunks give the lone solves' results bit for bit."""
+    wlw = w.workload(7)
+    gmw = camp.Mechanism(wlw.json())
+    srv = camp.Server(hbm_budget_bytes=2 << 30, max_inflight=4)
+    jobs = []
+    for i, (wl, gm, C) in enumerate([(wlw, gmw, 300), (mechs[2][0], mechs[2][1], 900),
+                                     (wlw, gmw, 77), (mechs[2][0], mechs[2][1], 40)]):
+        y, env = w.cells(wl.mech, C, seed=950 + i)
+        ty, te, ts = _pinned(y.copy()), _pinned(env), _pinned(np.zeros(C, dtype=np.int32))
+        rid = srv.submit(gm, ty, te, 300.0, wl.rtol, wl.atol, ts)
+        jobs.append((rid, gm, y, env, wl, ty, ts))
+    for rid, gm, y, env, wl, ty, ts in jobs:
+        assert srv.wait(rid)["rc"] == 0
+        ya, sa = _alone(gm, y, env, 300.0, wl.rtol, wl.atol)
+        assert np.array_equal(ty.numpy(), ya) and np.array_equal(ts.numpy(), sa)
+        assert (sa == 0).all()
+    srv.close()

@@ -75,3 +75,24 @@ def test_host_entry_point_and_failed_cells(gas):
     assert st_h[5] == 5 and step_h[5] == 0.0
     ok = np.arange(len(y0)) != 5
     assert (st_h[ok] == 0).all() and (step_h[ok] > 0).all()
+
+
+def test_water_parameter_warm_start(cuda):
+    """Warm start on the water build: three consecutive calls against the
+    oracle's warm start."""
+    import torch
+    wl = w.workload(7)
+    gm, om = camp.Mechanism(wl.json()), oracle.Mechanism(wl.json())
+    y0, env = wl.inputs(129)
+    ty, te = torch.tensor(y0, device="cuda"), torch.tensor(env, device="cuda")
+    step_g = torch.zeros(len(y0), dtype=torch.float64, device="cuda")
+    step_o = np.zeros(len(y0))
+    yo = y0.copy()
+    for call in range(3):
+        y_before = yo.copy()
+        st = gm.solve(ty, te, wl.dt, wl.rtol, wl.atol, step=step_g)
+        torch.cuda.synchronize()
+        yo, so, _ = om.solve(yo, env, wl.dt, wl.rtol, wl.atol, step=step_o)
+        assert (st.cpu().numpy() == 0).all() and (so == 0).all()
+        parity.check(om, y_before, env, wl.dt, wl.rtol, wl.atol, ty.cpu().numpy(), yo)
+        assert (step_g.cpu().numpy() > 0).all()

@@ -34,7 +34,7 @@ def _static_call(gm, y, env, dt, rtol, atol, variant):
     return rc, status
 
 
-@pytest.mark.parametrize("k,C", [(2, 3000), (3, 1000)])
+@pytest.mark.parametrize("k,C", [(2, 3000), (3, 1000), (7, 500)])
 @pytest.mark.parametrize("variant", [camp.VARIANT_MIXED, camp.VARIANT_FP64])
 def test_matches_the_allocating_entry_point_on_two_calls_in_a_row(cuda, k, C, variant):
     wl = w.workload(k)
