@@ -86,7 +86,7 @@ int camp_pick_shape(int n) {
 int camp_group_size(int n) { return camp_cell_lanes(n); }
 
 int camp_cell_smem_bytes(const DevMech &m, int lu_elem) {
-    return campdev::cell_smem(m.n, m.R, m.n_rev, m.nlu, lu_elem, m.n_part, m.n_pw).bytes;
+    return campdev::cell_smem(m.n, m.R, m.n_rev, m.nlu, lu_elem, m.n_part, m.n_pw, m.n_pw64).bytes;
 }
 
 cudaError_t camp_launch_rates(const DevMech &m, long long n_cells, const double *env, double *kf,
@@ -98,7 +98,7 @@ cudaError_t camp_launch_rates(const DevMech &m, long long n_cells, const double 
 
 cudaError_t camp_launch_forcing(const DevMech &m, long long n_cells, const double *state,
                                 const double *env, double *f, cudaStream_t s) {
-    if (m.n_pp > 0) {  // the water build: 8-slot shapes only
+    if (m.n_wsec > 0) {  // the water build: 8-slot shapes only
         switch (camp_pick_shape(m.n) < CAMP_SHAPE_BLOCK ? 8 : camp_pick_shape(m.n)) {
         case 8: return forcing_npl<32, 8, true>(m, n_cells, state, env, f, s);
         case CAMP_SHAPE_BLOCK + 2: return forcing_npl<64, 8, true>(m, n_cells, state, env, f, s);
@@ -296,7 +296,7 @@ int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double
                                                            : (o.variant == CAMP_VARIANT_MIXED ? 1 : 0);
     auto occupancy = [&](int cpb_, int *per_sm) -> cudaError_t {
         if (m->occ[o.variant][cpb_] == 0) {
-            const bool w = m->dm.n_pp > 0;
+            const bool w = m->dm.n_wsec > 0;
             cudaError_t e = f32 ? (w ? camp_occupancy_f32w(m->dm, cpb_, per_sm) : camp_occupancy_f32(m->dm, cpb_, per_sm))
                                 : (w ? camp_occupancy_f64w(m->dm, cpb_, per_sm) : camp_occupancy_f64(m->dm, cpb_, per_sm));
             if (e != cudaSuccess) return e;
@@ -358,7 +358,7 @@ int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double
         grid = (n_cells + cpb - 1) / cpb;
         if (grid > 0x7fffffffLL) return fail(CAMP_E_INVAL, "too many cells for one launch");
     }
-    if (m->dm.n_pp > 0)
+    if (m->dm.n_wsec > 0)
         CUDA_TRY(f32 ? camp_launch_solve_f32w(m->dm, a, (int)grid, s) : camp_launch_solve_f64w(m->dm, a, (int)grid, s));
     else
         CUDA_TRY(f32 ? camp_launch_solve_f32(m->dm, a, (int)grid, s) : camp_launch_solve_f64(m->dm, a, (int)grid, s));
@@ -552,7 +552,7 @@ int camp_jacobian(const camp_mech *m, int64_t n_cells, const double *state, cons
     if (n_cells > 0x7fffffffLL) return fail(CAMP_E_INVAL, "too many cells");
     if (int rc = check_device(m)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    if (m->dm.n_pp > 0)
+    if (m->dm.n_wsec > 0)
         CUDA_TRY(variant == CAMP_VARIANT_MIXED ? camp_launch_jacobian_f32w(m->dm, n_cells, state, env, jac, s)
                                                : camp_launch_jacobian_f64w(m->dm, n_cells, state, env, jac, s));
     else
@@ -571,7 +571,7 @@ int camp_lu_solve(const camp_mech *m, int64_t n_cells, const double *state, cons
     if (n_cells > 0x7fffffffLL) return fail(CAMP_E_INVAL, "too many cells");
     if (int rc = check_device(m)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    if (m->dm.n_pp > 0)
+    if (m->dm.n_wsec > 0)
         CUDA_TRY(variant == CAMP_VARIANT_MIXED
                      ? camp_launch_lu_solve_f32w(m->dm, n_cells, state, env, gamma, b, x, status, s)
                      : camp_launch_lu_solve_f64w(m->dm, n_cells, state, env, gamma, b, x, status, s));

@@ -47,17 +47,17 @@ struct CellSmem {
 __host__ __device__ inline int align16(int b) { return (b + 15) & ~15; }
 // rs holds the R rate terms, then n_part partial sums (of split forcing sums
 // inside an f evaluation, of split substitution rows inside a solve)
-// pw holds the water parameter's per-cell values (n_pw doubles, none
-// without one)
+// pw holds the water parameter's per-cell values (n_pw doubles, and n_pw64
+// more in the FP64 form; none without one)
 __host__ __device__ inline CellSmem cell_smem(int n, int R, int n_rev, int nlu, int lu_elem, int n_part,
-                                              int n_pw) {
+                                              int n_pw, int n_pw64) {
     CellSmem c;
     int o = 0;
     c.ys = o; o = align16(o + 8 * n);
     c.rs = o; o = align16(o + 8 * (R + n_part));
     c.kf = o; o = align16(o + 8 * R);
     c.kr = o; o = align16(o + 8 * n_rev);
-    c.pw = o; o = align16(o + 8 * n_pw);
+    c.pw = o; o = align16(o + 8 * (n_pw + (lu_elem == 8 ? n_pw64 : 0)));
     // the substitution vector shares the rate-term scratch when it fits:
     // the rate terms live only inside one f evaluation, the vector only
     // inside one Newton solve, and the Jacobian assembly keeps its FP32
@@ -78,7 +78,7 @@ struct CellPtr {
     double *ys, *rs, *kf, *kr, *pw;
     LT *x, *lu;
     __device__ CellPtr(char *base, const DevMech &m) {
-        CellSmem c = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw);
+        CellSmem c = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw, m.n_pw64);
         ys = (double *)(base + c.ys);
         rs = (double *)(base + c.rs);
         kf = (double *)(base + c.kf);
@@ -314,14 +314,32 @@ __device__ __forceinline__ double gather_entry(const DevMech &m, int q, const do
 }
 
 // ---- the water parameter (Sect. 2.2.2; Table 4, ZSRAerosolWater) ----------
-// Per-cell scratch c.pw: kf0, kr0 and d r / d L of each parameterised
-// process, then the electrolyte weights, L_env and 1 / L of each section, then
-// the g sums d f_i / d L_b.
-__device__ __forceinline__ double *pw_dl(const DevMech &m, double *pw) { return pw + 2 * m.n_pp; }
-__device__ __forceinline__ double *pw_wt(const DevMech &m, double *pw) { return pw + 3 * m.n_pp; }
-__device__ __forceinline__ double *pw_lenv(const DevMech &m, double *pw) { return pw_wt(m, pw) + m.n_el; }
-__device__ __forceinline__ double *pw_invl(const DevMech &m, double *pw) { return pw_lenv(m, pw) + m.n_wsec; }
-__device__ __forceinline__ double *pw_g(const DevMech &m, double *pw) { return pw_invl(m, pw) + m.n_wsec; }
+// With the parameter, the constants of the section processes stay per unit
+// volume in kf / kr, and the powers of 1/L(y) are applied where they are
+// used (the rate terms, the Jacobian's constants, the chain rule), from each
+// process's record: bits 16-26 of rpack.w hold its section + 1 (0: not a
+// section process), bits 27-28 la and bits 29-30 lb.  Per-cell scratch c.pw:
+// the electrolyte weights, L_env and 1/L of each section (1/L stored as 0
+// for a section whose water is not positive: its processes take no part),
+// then, in the FP64 form only, the Jacobian's reverse constants.
+__device__ __forceinline__ double *pw_wt(const DevMech &, double *pw) { return pw; }
+__device__ __forceinline__ double *pw_lenv(const DevMech &m, double *pw) { return pw + m.n_el; }
+__device__ __forceinline__ double *pw_invl(const DevMech &m, double *pw) { return pw + m.n_el + m.n_wsec; }
+__device__ __forceinline__ double *pw_kr64(const DevMech &m, double *pw) { return pw + m.n_pw; }
+
+struct WaterTag {
+    int sec, la, lb;  // sec = -1: not a section process
+};
+__device__ __forceinline__ WaterTag water_tag(int w) {
+    const int h = hi16(w);
+    return {(h & 0x7ff) - 1, (h >> 11) & 3, (h >> 13) & 3};
+}
+// factor of kf (p = la) or kr (p = lb) at the current volumes
+__device__ __forceinline__ double water_scale(int sec, int p, const double *invl) {
+    if (sec < 0) return 1.0;
+    const double il = invl[sec];
+    return il > 0.0 ? ipowd(il, p) : 0.0;
+}
 
 // Water per ppb of electrolyte e [m^3 per m^3 air]: 1e-9 P / (R T) mol m^-3
 // per ppb over the molality m_e(a_w) of its binary solution (ZSR:
@@ -344,29 +362,21 @@ __device__ inline double zsr_weight(const DevMech &m, int e, const double *__res
     return 1e-9 * P / (RG * T) / mol / 1000.0;
 }
 
-// After the rate constants: keep each parameterised process's per-volume
-// constants, the electrolyte weights and the sections' env volumes.
+// Per cell, once: the electrolyte weights and the sections' env volumes.
 template <int G>
-__device__ __forceinline__ void water_setup(const DevMech &m, double *pw, const double *kf, const double *kr,
-                                         const double *__restrict__ env, int lane, unsigned gm) {
-    for (int j = lane; j < m.n_pp; j += G) {
-        const int4 r = __ldg(m.pp + j);
-        pw[j] = kf[r.x];
-        pw[m.n_pp + j] = r.w >= 0 ? kr[r.w] : 0.0;
-    }
+__device__ __forceinline__ void water_setup(const DevMech &m, double *pw, const double *__restrict__ env,
+                                            int lane, unsigned gm) {
     double *wt = pw_wt(m, pw), *lenv = pw_lenv(m, pw);
     for (int e = lane; e < m.n_el; e += G) wt[e] = zsr_weight(m, e, env);
     for (int b = lane; b < m.n_wsec; b += G) lenv[b] = env[m.env_sec_base + 3 * b + 2];
     gsync<G>(gm);
 }
 
-// The parameter at the state in ys: L_b = L_env,b + sum_e w_e y_e, then the
-// constants kf = kf0 L^-la, kr = kr0 L^-lb of every section process.  A
-// section whose water is not positive takes no part, as one with no water
-// in env does: 1/L is stored as 0 and its processes' constants as 0.
+// The parameter at the state in ys: L_b = L_env,b + sum_e w_e y_e, kept as
+// 1/L_b (0 for a section whose water is not positive).
 template <int G>
-__device__ __forceinline__ void water_update(const DevMech &m, double *pw, double *kf, double *kr,
-                                          const double *ys, int lane, unsigned gm) {
+__device__ __forceinline__ void water_update(const DevMech &m, double *pw, const double *ys, int lane,
+                                             unsigned gm) {
     const double *wt = pw_wt(m, pw), *lenv = pw_lenv(m, pw);
     double *invl = pw_invl(m, pw);
     for (int b = lane; b < m.n_wsec; b += G) {
@@ -379,67 +389,78 @@ __device__ __forceinline__ void water_update(const DevMech &m, double *pw, doubl
         invl[b] = v > 0.0 ? 1.0 / v : 0.0;
     }
     gsync<G>(gm);
-    for (int j = lane; j < m.n_pp; j += G) {
-        const int4 r = __ldg(m.pp + j);
-        const double il = invl[r.y];
-        const bool wet = il > 0.0;
-        kf[r.x] = wet ? pw[j] * ipowd(il, r.z & 0xff) : 0.0;
-        if (r.w >= 0) kr[r.w] = wet ? pw[m.n_pp + j] * ipowd(il, r.z >> 8) : 0.0;
-    }
-    gsync<G>(gm);
 }
 
-// Before a Jacobian assembly at ys: the parameter and constants at ys, then
-// d r_j / d L_b = -(la F_j - lb B_j) / L_b of each parameterised process
-// (F, B its forward and reverse terms) and the sums g = d f_i / d L_b.
-template <int G>
-__device__ __forceinline__ void water_jacobian_prep(const DevMech &m, double *pw, double *kf, double *kr,
-                                                 const double *ys, int lane, unsigned gm) {
-    water_update<G>(m, pw, kf, kr, ys, lane, gm);
-    double *dl = pw_dl(m, pw), *g = pw_g(m, pw);
-    const double *invl = pw_invl(m, pw);
-    for (int j = lane; j < m.n_pp; j += G) {
-        const int4 r = __ldg(m.pp + j);
-        const int4 rp = __ldg(m.rpack + r.x);
-        const int a0 = lo16(rp.x), a1 = hi16(rp.x), a2 = lo16(rp.y);
-        double F = kf[r.x];
-        if (a0 != NONE16) F *= ys[a0];
-        if (a1 != NONE16) F *= ys[a1];
-        if (a2 != NONE16) F *= ys[a2];
-        double B = 0.0;
-        if (r.w >= 0) {
-            const int b0 = lo16(rp.z), b1 = hi16(rp.z), b2 = lo16(rp.w);
-            B = kr[r.w];
-            if (b0 != NONE16) B *= ys[b0];
-            if (b1 != NONE16) B *= ys[b1];
-            if (b2 != NONE16) B *= ys[b2];
-        }
-        dl[j] = -((double)(r.z & 0xff) * F - (double)(r.z >> 8) * B) * invl[r.y];
+// r_k with the powers of 1/L of a section process applied (the water build's
+// rate term)
+__device__ __forceinline__ double rate_term_water(const DevMech &m, int k, const double *ys, const double *kf,
+                                                  const double *kr, const double *invl) {
+    const int4 rp = __ldg(m.rpack + k);
+    const WaterTag t = water_tag(rp.w);
+    double il = 1.0;
+    if (t.sec >= 0) {
+        il = invl[t.sec];
+        if (!(il > 0.0)) return 0.0;
     }
-    gsync<G>(gm);
-    for (int i = lane; i < m.n_g; i += G) {
-        double acc = 0.0;
-        const int q1 = __ldg(m.g_ptr + i + 1);
-        for (int q = __ldg(m.g_ptr + i); q < q1; q++) acc += __ldg(m.g_coef + q) * dl[__ldg(m.g_ent + q)];
-        g[i] = acc;
+    const int a0 = lo16(rp.x), a1 = hi16(rp.x), a2 = lo16(rp.y), rv = hi16(rp.y);
+    double a = kf[k] * ipowd(il, t.la);
+    if (a0 != NONE16) a *= ys[a0];
+    if (a1 != NONE16) a *= ys[a1];
+    if (a2 != NONE16) a *= ys[a2];
+    if (rv != NONE16) {
+        const int b0 = lo16(rp.z), b1 = hi16(rp.z), b2 = lo16(rp.w);
+        double b = kr[rv] * ipowd(il, t.lb);
+        if (b0 != NONE16) b *= ys[b0];
+        if (b1 != NONE16) b *= ys[b1];
+        if (b2 != NONE16) b *= ys[b2];
+        a -= b;
     }
-    gsync<G>(gm);
+    return a;
 }
 
-// The chain-rule term J_p P_y of Sect. 2.2.2 after the direct assembly:
-// J_ie += g_(i,b) w_e for each electrolyte e of section b.  Each entry is a
+// The chain-rule term J_p P_y of Sect. 2.2.2 after the direct assembly: for
+// each (row i, section b) pair g, g = d f_i / d L_b = sum_j nu_ij dr_j/dL_b
+// with dr/dL = -(la F - lb B) / L (F, B the forward and reverse terms at the
+// assembly's state y), then J_ie += g w_e for each electrolyte e of b.  The
+// entries of one g are its n_el consecutive chain records; every record is a
 // distinct (row, electrolyte) pair, so lanes need no atomics.
 template <int G, typename LT>
-__device__ __forceinline__ void water_chain(const DevMech &m, double *pw, LT *lu, double gamma, int lane,
-                                         int mode, double *out) {
-    const double *wt = pw_wt(m, pw), *g = pw_g(m, pw);
-    for (int i = lane; i < m.n_ch; i += G) {
-        const int4 r = __ldg(m.ch + i);
-        const double v = g[r.y] * wt[r.z];
-        if (mode == 0)
-            lu[r.x] -= to_lu<LT>(gamma * v);
-        else
-            out[r.w] += v;
+__device__ __forceinline__ void water_chain(const DevMech &m, double *pw, const double *kf, const double *kr,
+                                            const LT *y, LT *lu, double gamma, int lane, int mode,
+                                            double *out) {
+    const double *wt = pw_wt(m, pw), *invl = pw_invl(m, pw);
+    for (int g = lane; g < m.n_g; g += G) {
+        double acc = 0.0;
+        const int q1 = __ldg(m.g_ptr + g + 1);
+        for (int q = __ldg(m.g_ptr + g); q < q1; q++) {
+            const int4 r = __ldg(m.pp + __ldg(m.g_ent + q));
+            const double il = invl[r.y];
+            if (!(il > 0.0)) continue;
+            const int la = r.z & 0xff, lb = r.z >> 8;
+            const int4 rp = __ldg(m.rpack + r.x);
+            const int a0 = lo16(rp.x), a1 = hi16(rp.x), a2 = lo16(rp.y);
+            double F = kf[r.x] * ipowd(il, la);
+            if (a0 != NONE16) F *= (double)y[a0];
+            if (a1 != NONE16) F *= (double)y[a1];
+            if (a2 != NONE16) F *= (double)y[a2];
+            double B = 0.0;
+            if (r.w >= 0) {
+                const int b0 = lo16(rp.z), b1 = hi16(rp.z), b2 = lo16(rp.w);
+                B = kr[r.w] * ipowd(il, lb);
+                if (b0 != NONE16) B *= (double)y[b0];
+                if (b1 != NONE16) B *= (double)y[b1];
+                if (b2 != NONE16) B *= (double)y[b2];
+            }
+            acc += __ldg(m.g_coef + q) * (-((double)la * F - (double)lb * B) * il);
+        }
+        for (int e = 0; e < m.n_el; e++) {
+            const int4 ch = __ldg(m.ch + g * m.n_el + e);
+            const double v = acc * wt[e];
+            if (mode == 0)
+                lu[ch.x] -= to_lu<LT>(gamma * v);
+            else
+                out[ch.w] += v;
+        }
     }
 }
 
@@ -450,8 +471,13 @@ __device__ __forceinline__ void water_chain(const DevMech &m, double *pw, LT *lu
 template <int G, int NPL, typename LT, bool W>
 __device__ __forceinline__ void eval_f_ys(const DevMech &m, const CellPtr<LT> &c, double (&f)[NPL],
                                           int lane, unsigned gm) {
-    if constexpr (W) water_update<G>(m, c.pw, c.kf, c.kr, c.ys, lane, gm);
-    for (int k = lane; k < m.R; k += G) c.rs[k] = rate_term(m, k, c.ys, c.kf[k], c.kr);
+    if constexpr (W) {
+        water_update<G>(m, c.pw, c.ys, lane, gm);
+        const double *invl = pw_invl(m, c.pw);
+        for (int k = lane; k < m.R; k += G) c.rs[k] = rate_term_water(m, k, c.ys, c.kf, c.kr, invl);
+    } else {
+        for (int k = lane; k < m.R; k += G) c.rs[k] = rate_term(m, k, c.ys, c.kf[k], c.kr);
+    }
     gsync<G>(gm);
     double *fs = c.ys;  // y is no longer needed
     double *fp = c.rs + m.R;
@@ -524,12 +550,29 @@ __device__ __forceinline__ void eval_f_at(const DevMech &m, const CellPtr<LT> &c
 template <int G, typename LT, bool W>
 __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c, double gamma,
                                          int lane, unsigned gm, int mode, double *out) {
-    if constexpr (W) water_jacobian_prep<G>(m, c.pw, c.kf, c.kr, c.ys, lane, gm);
     const LT *kfv, *krv, *yv;
+    // the water build: 1/L at this state, and the constants with their
+    // powers of 1/L applied (FP64 form: into the rate scratch and the
+    // parameter block)
+    auto water_constants = [&](LT *kfw, LT *krw) {
+        const double *invl = pw_invl(m, c.pw);
+        for (int k = lane; k < m.R; k += G) {
+            const int4 rp = __ldg(m.rpack + k);
+            const WaterTag t = water_tag(rp.w);
+            kfw[k] = to_lu<LT>(c.kf[k] * water_scale(t.sec, t.la, invl));
+            const int rv = hi16(rp.y);
+            if (rv != NONE16) krw[rv] = to_lu<LT>(c.kr[rv] * water_scale(t.sec, t.lb, invl));
+        }
+    };
+    if constexpr (W) water_update<G>(m, c.pw, c.ys, lane, gm);
     if constexpr (sizeof(LT) == 4) {
         LT *kf32 = (LT *)c.rs, *kr32 = kf32 + m.R, *y32 = (LT *)c.ys;
-        for (int k = lane; k < m.R; k += G) kf32[k] = (LT)c.kf[k];
-        for (int k = lane; k < m.n_rev; k += G) kr32[k] = (LT)c.kr[k];
+        if constexpr (W) {
+            water_constants(kf32, kr32);
+        } else {
+            for (int k = lane; k < m.R; k += G) kf32[k] = (LT)c.kf[k];
+            for (int k = lane; k < m.n_rev; k += G) kr32[k] = (LT)c.kr[k];
+        }
         // y to FP32 in place, G positions at a time: a chunk's FP32 values
         // overwrite only FP64 values of this or earlier chunks, and the
         // group reads its chunk before any lane writes it
@@ -543,8 +586,15 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
         krv = kr32;
         yv = y32;
     } else {
-        kfv = (const LT *)c.kf;
-        krv = (const LT *)c.kr;
+        if constexpr (W) {
+            LT *kf64 = (LT *)c.rs, *kr64 = (LT *)pw_kr64(m, c.pw);
+            water_constants(kf64, kr64);
+            kfv = kf64;
+            krv = kr64;
+        } else {
+            kfv = (const LT *)c.kf;
+            krv = (const LT *)c.kr;
+        }
         yv = (const LT *)c.ys;
     }
     if (mode == 0) {  // 16-byte stores: the LU array starts 16-byte aligned
@@ -601,7 +651,7 @@ __device__ __forceinline__ void assemble(const DevMech &m, const CellPtr<LT> &c,
     }
     gsync<G>(gm);
     if constexpr (W) {
-        water_chain<G, LT>(m, c.pw, c.lu, gamma, lane, mode, out);
+        water_chain<G, LT>(m, c.pw, c.kf, c.kr, yv, c.lu, gamma, lane, mode, out);
         gsync<G>(gm);
     }
 }
@@ -1111,7 +1161,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
         if (rv >= 0) c.kr[rv] = b;
     }
     gsync<G>(gm);
-    if constexpr (W) water_setup<G>(m, c.pw, c.kf, c.kr, env_cell, lane, gm);
+    if constexpr (W) water_setup<G>(m, c.pw, env_cell, lane, gm);
 
     // atol is re-read (an L1 hit) rather than held in registers
     auto set_weights = [&]() {

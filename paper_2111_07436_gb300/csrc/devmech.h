@@ -155,9 +155,11 @@ struct DevMech {
     // liquid volume of section b is L_b(y) = L_env,b + sum_e w_e y_e over its
     // electrolytes, w_e = 1e-9 P / (R T) / (1000 m_e(a_w)) with the molality
     // fit sqrt(m_e) = sum_j Y_j a_w^j at a_w = RH (held at the fit's lowest
-    // activity below it).  Section processes then get per-unit-volume
-    // constants kf0, kr0 and the kernels apply kf0 L^-la, kr0 L^-lb at every
-    // state; the Jacobian adds the chain-rule term J_p P_y.
+    // activity below it).  Section processes then keep per-unit-volume
+    // constants in kf / kr; the kernels apply L^-la, L^-lb where the
+    // constants are used (each section process's rpack record carries
+    // section + 1 in bits 16-26 of w, la in bits 27-28 and lb in bits 29-30),
+    // and the Jacobian adds the chain-rule term J_p P_y.
     int n_wsec;           // sections with a water parameter (0: none)
     int n_el;             // electrolytes
     int rh_slot;          // env index of the relative humidity
@@ -165,10 +167,8 @@ struct DevMech {
     const double *zsr_low;// [n_el]
     const int *pw_ptr;    // [n_wsec+1] into pw
     const int *pw;        // electrolyte entries: position | electrolyte << 16
-    int n_pp;             // section processes, rescaled at every state
-    // x = process, y = section, z = la | lb << 8 (powers of 1/L in kf, kr),
-    // w = kr index (-1: none); a section whose water is not positive takes
-    // no part (its processes' constants are 0)
+    int n_pp;             // section processes with a power of 1/L (chain rule)
+    // x = process, y = section, z = la | lb << 8, w = kr index (-1: none)
     const int4 *pp;       // [n_pp]
     // d f_i / d L_b for each (row, section) pair g: sum over entries of
     // coefficient * d r_j / d L_b of parameterised process j
@@ -176,11 +176,13 @@ struct DevMech {
     const int *g_ptr;     // [n_g+1] into g_ent, g_coef
     const int *g_ent;     // parameterised process index
     const double *g_coef; // net stoichiometric coefficient
-    // chain-rule entries J_ij += g_(i,b) w_e: x = LU offset of (i, e),
-    // y = g index, z = electrolyte, w = species-CSR non-zero
+    // chain-rule entries J_ij += g_(i,b) w_e, n_el consecutive records per
+    // g: x = LU offset of (i, e), y = g index, z = electrolyte e, w =
+    // species-CSR non-zero
     int n_ch;
     const int4 *ch;
-    int n_pw;             // per-cell FP64 scratch of the parameter (0: none)
+    int n_pw;             // per-cell FP64 values of the parameter (0: none)
+    int n_pw64;           // more of them in the FP64 form (reverse constants)
 
     // BDF coefficients: l-vector of prod_{i=1..q}(1 + x/i), local-error
     // constants 1/((q+1) l_1(q)), factorials

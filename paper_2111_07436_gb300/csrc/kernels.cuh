@@ -32,7 +32,7 @@ __global__ void __maxnreg__((sizeof(LT) == 8 || G > 32) ? 255 : (NPL >= 6 ? 224 
     extern __shared__ __align__(16) char smem[];
     const int group = threadIdx.x / G, lane = threadIdx.x % G;
     const unsigned gm = group_mask<G>();
-    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw);
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw, m.n_pw64);
     CellPtr<LT> c(smem + group * L.bytes, m);
     long long cell = a.queue ? 0 : (long long)blockIdx.x * a.cpb + group;
     for (;;) {
@@ -101,7 +101,7 @@ __device__ __forceinline__ void load_cell(const DevMech &m, const CellPtr<LT> &c
         if (p < m.n) c.ys[p] = yr[s];
     }
     gsync<G>(gm);
-    if constexpr (W) water_setup<G>(m, c.pw, c.kf, c.kr, env, lane, gm);
+    if constexpr (W) water_setup<G>(m, c.pw, env, lane, gm);
 }
 
 // f(y) of every cell, [cell][n] in declaration order.
@@ -113,7 +113,7 @@ __global__ void k_forcing(DevMech m, long long n_cells, const double *state, con
     const unsigned gm = group_mask<G>();
     const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
     if (cell >= n_cells) return;
-    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw);
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw, m.n_pw64);
     CellPtr<LT> c(smem + group * L.bytes, m);
     double y[NPL], f[NPL];
     load_cell<G, NPL, LT, W>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
@@ -135,7 +135,7 @@ __global__ void k_jacobian(DevMech m, long long n_cells, const double *state, co
     const unsigned gm = group_mask<G>();
     const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
     if (cell >= n_cells) return;
-    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw);
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw, m.n_pw64);
     CellPtr<LT> c(smem + group * L.bytes, m);
     double y[NPL];
     load_cell<G, NPL, LT, W>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);
@@ -153,7 +153,7 @@ __global__ void k_lu_solve(DevMech m, long long n_cells, const double *state, co
     const unsigned gm = group_mask<G>();
     const long long cell = (long long)blockIdx.x * (blockDim.x / G) + group;
     if (cell >= n_cells) return;
-    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw);
+    const CellSmem L = cell_smem(m.n, m.R, m.n_rev, m.nlu, (int)sizeof(LT), m.n_part, m.n_pw, m.n_pw64);
     CellPtr<LT> c(smem + group * L.bytes, m);
     double y[NPL];
     load_cell<G, NPL, LT, W>(m, c, state + cell * m.n, env + cell * m.n_env, y, lane, gm);

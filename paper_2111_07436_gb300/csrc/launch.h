@@ -51,7 +51,7 @@ cudaError_t camp_launch_solve_f32(const DevMech &m, const SolveArgs &a, int grid
 cudaError_t camp_launch_solve_f64(const DevMech &m, const SolveArgs &a, int grid, cudaStream_t s);
 cudaError_t camp_occupancy_f32(const DevMech &m, int cpb, int *blocks_per_sm);
 cudaError_t camp_occupancy_f64(const DevMech &m, int cpb, int *blocks_per_sm);
-// the same for mechanisms with a water parameter (DevMech::n_pp > 0)
+// the same for mechanisms with a water parameter (DevMech::n_wsec > 0)
 cudaError_t camp_launch_solve_f32w(const DevMech &m, const SolveArgs &a, int grid, cudaStream_t s);
 cudaError_t camp_launch_solve_f64w(const DevMech &m, const SolveArgs &a, int grid, cudaStream_t s);
 cudaError_t camp_occupancy_f32w(const DevMech &m, int cpb, int *blocks_per_sm);

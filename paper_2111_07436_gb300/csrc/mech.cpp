@@ -285,6 +285,12 @@ static void pack_records(HostMech &h) {
         o[1] = field16(f[2]) | (field16(h.rrev[k]) << 16);
         o[2] = field16(f[3]) | (field16(f[4]) << 16);
         o[3] = field16(f[5]);
+        // the water parameter: section + 1 and the powers of 1/L
+        const Process &p = h.procs[k];
+        if (!h.el_phase.empty() && is_sectioned(p.type)) {
+            if (p.slot + 1 > 0x7ff || p.la > 3 || p.lb > 3) throw std::runtime_error("water tag does not fit");
+            o[3] |= ((p.slot + 1) | (p.la << 11) | (p.lb << 13)) << 16;
+        }
     }
     // gather entries as 4 bytes each: process | index into the table of the
     // mechanism's distinct coefficients << 16
@@ -831,7 +837,7 @@ static void build_tables(HostMech &h) {
     // carry powers of 1/L, d f_i / d L_b sums and the chain-rule entries
     h.pw_ptr.clear(); h.pw.clear(); h.pp.clear(); h.g_ptr.clear(); h.g_ent.clear();
     h.g_coef.clear(); h.ch.clear();
-    h.n_pw = 0;
+    h.n_pw = h.n_pw64 = 0;
     if (!h.el_phase.empty()) {
         const int S = h.n_sections, n_el = (int)h.el_phase.size();
         h.pw_ptr.assign(1, 0);
@@ -842,18 +848,15 @@ static void build_tables(HostMech &h) {
         std::map<std::pair<int, int>, int> gidx;  // (species, section) -> g
         std::vector<std::pair<int, int>> grow;    // g -> (species, section)
         std::vector<std::vector<std::pair<int, double>>> gl;
-        // every section process is rescaled at each state (a section whose
-        // water is not positive switches its processes off); only those with
-        // powers of 1/L enter the chain rule
+        // the processes with powers of 1/L enter the chain rule
         for (int k = 0; k < R; k++) {
             const Process &p = h.procs[k];
-            if (!is_sectioned(p.type)) continue;
+            if (!p.la && !p.lb) continue;
             const int j = (int)h.pp.size() / 4;
             h.pp.push_back(k);
             h.pp.push_back(p.slot);
             h.pp.push_back(p.la | (p.lb << 8));
             h.pp.push_back(h.rrev[k]);
-            if (!p.la && !p.lb) continue;
             for (int i : touched(p)) {
                 const double nu = net_coef(p, i);
                 if (nu == 0.0) continue;
@@ -886,10 +889,10 @@ static void build_tables(HostMech &h) {
                 h.ch.push_back(csr_pos(i, col));
             }
         }
-        const int n_pp = (int)h.pp.size() / 4;
-        // per cell: kf0, kr0 and d r / d L per parameterised process, the
-        // weights, L_env and 1 / L per section, and the g sums
-        h.n_pw = 3 * n_pp + n_el + 2 * S + (int)grow.size();
+        // per cell: the weights, L_env and 1 / L per section; the FP64 form
+        // also keeps the Jacobian's reverse constants there
+        h.n_pw = n_el + 2 * S;
+        h.n_pw64 = h.n_rev;
     }
 
     // sparse factorisation ops, row by row; levels: sparse rows by level, then
@@ -1078,6 +1081,11 @@ static void validate_tables(const HostMech &h) {
             if (lo != NONE && !in(lo, 0, n)) fail("rpack");
             if (c == 1 && hi != NONE && !in(hi, 0, h.n_rev)) fail("rpack");
             if ((c == 0 || c == 2) && hi != NONE && !in(hi, 0, n)) fail("rpack");
+            if (c == 3) {  // water tag: section + 1, la, lb (0 without the parameter)
+                const int sec = (hi & 0x7ff) - 1;
+                if (h.el_phase.empty() ? hi != 0 : !in(sec, -1, h.n_sections)) fail("rpack water tag");
+                if (sec < 0 && hi != 0) fail("rpack water tag");
+            }
         }
     }
     // forcing gather
@@ -1156,9 +1164,11 @@ static void validate_tables(const HostMech &h) {
         }
         if (h.g_ptr.front() != 0 || h.g_ptr.back() != (int)h.g_ent.size()) fail("g_ptr");
         for (int j : h.g_ent) if (!in(j, 0, n_pp)) fail("g_ent");
+        if ((int)h.ch.size() != 4 * n_g * n_el) fail("ch size");
         for (size_t c = 0; c < h.ch.size() / 4; c++) {
             const int *r = &h.ch[4 * c];
             if (!in(r[0], 0, nlu) || !in(r[1], 0, n_g) || !in(r[2], 0, n_el) || !in(r[3], 0, nnzJ)) fail("ch");
+            if (r[1] != (int)c / n_el || r[2] != (int)c % n_el) fail("ch order");
         }
         if (!in(h.rh_slot, 2, h.env_sec_base)) fail("rh_slot");
     }
@@ -1283,6 +1293,7 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.n_ch = (int)h.ch.size() / 4;
     dm.ch = reinterpret_cast<const int4 *>(pk.put(h.ch));
     dm.n_pw = h.n_pw;
+    dm.n_pw64 = h.n_pw64;
     bdf_coefficients(dm);
     return pk.img;
 }

@@ -35,7 +35,7 @@ struct HostMech {
     std::vector<double> zsr_Y, zsr_low;        // [n_el][CAMP_ZSR_NY], [n_el]
     std::vector<int> pw_ptr, pw, pp, g_ptr, g_ent, ch;
     std::vector<double> g_coef;
-    int n_pw = 0;
+    int n_pw = 0, n_pw64 = 0;
 
     // integer structure (species numbering except the LU, which is permuted)
     std::vector<int> rowptr, colidx, rxn_map, perm, iperm;
