@@ -872,7 +872,7 @@ __device__ bool factor(const DevMech &m, const CellPtr<LT> &c, int lane, unsigne
 // value is broadcast with a shuffle, and the loops run one 32-row diagonal
 // block at a time so that only that block's rows need a comparison.  Rows
 // past the block end read the last row (a valid address) and are discarded.
-template <int NS, typename LT>
+template <int NS, typename LT, int SP>
 __device__ __forceinline__ void dense_subst(const LT *A, int D, int LD, LT *xb, int lane, unsigned gm) {
     LT xr[NS];
     int rowc[NS];
@@ -882,6 +882,7 @@ __device__ __forceinline__ void dense_subst(const LT *A, int D, int LD, LT *xb, 
         rowc[t] = (i < D ? i : D - 1) * LD;
         xr[t] = i < D ? xb[i] : (LT)0;
     }
+    if constexpr (SP == 2) {
     // forward, unit lower, two pivots per round: x_k and the not yet final
     // x_{k+1} come by two independent shuffles, every lane finishes x_{k+1}
     // with the broadcast L(k+1,k), then both columns update the rows below
@@ -952,6 +953,96 @@ __device__ __forceinline__ void dense_subst(const LT *A, int D, int LD, LT *xb, 
             }
         }
     }
+    } else {
+    // forward, unit lower, SP pivots per round: the not yet final x_k ..
+    // x_{k+SP-1} come by independent shuffles, every lane finishes them with
+    // the broadcast L entries of the diagonal block (a chain SP-1 deep), then
+    // the SP columns update the rows below
+#pragma unroll
+    for (int kb = 0; kb < NS; kb++) {
+        const int k0 = 32 * kb, k1 = min(D, k0 + 32);
+        int k = k0;
+#pragma unroll 1
+        for (; k + SP <= k1; k += SP) {
+            const int o = k - k0;
+            LT xf[SP];
+#pragma unroll
+            for (int p = 0; p < SP; p++) xf[p] = __shfl_sync(gm, xr[kb], o + p);
+#pragma unroll
+            for (int p = 1; p < SP; p++) {
+#pragma unroll
+                for (int q = 0; q < p; q++) xf[p] -= A[(k + p) * LD + k + q] * xf[q];
+            }
+#pragma unroll
+            for (int t = kb; t < NS; t++) {
+                LT a[SP];
+#pragma unroll
+                for (int p = 0; p < SP; p++) a[p] = A[rowc[t] + k + p];
+                if (t > kb || lane > o + SP - 1) {
+#pragma unroll
+                    for (int p = 0; p < SP; p++) xr[t] -= a[p] * xf[p];
+                } else {
+#pragma unroll
+                    for (int p = 1; p < SP; p++)
+                        if (lane == o + p) xr[t] = xf[p];
+                }
+            }
+        }
+        for (; k < k1; k++) {  // the block's last pivots, one at a time
+            const int o = k - k0;
+            const LT xk = __shfl_sync(gm, xr[kb], o);
+#pragma unroll
+            for (int t = kb; t < NS; t++) {
+                const LT a = A[rowc[t] + k];
+                if (t > kb || lane > o) xr[t] -= a * xk;
+            }
+        }
+    }
+    // backward, upper with reciprocal diagonal, SP pivots per round (k, k-1,
+    // ..., k-SP+1)
+#pragma unroll
+    for (int kb = NS - 1; kb >= 0; kb--) {
+        const int k0 = 32 * kb, k1 = min(D, k0 + 32);
+        int k = k1 - 1;
+#pragma unroll 1
+        for (; k - (SP - 1) >= k0; k -= SP) {
+            const int o = k - k0;
+            LT xf[SP];
+#pragma unroll
+            for (int p = 0; p < SP; p++) xf[p] = __shfl_sync(gm, xr[kb], o - p);
+#pragma unroll
+            for (int p = 0; p < SP; p++) {
+#pragma unroll
+                for (int q = 0; q < p; q++) xf[p] -= A[(k - p) * LD + k - q] * xf[q];
+                xf[p] *= A[(k - p) * LD + k - p];
+            }
+#pragma unroll
+            for (int t = 0; t <= kb; t++) {
+                LT a[SP];
+#pragma unroll
+                for (int p = 0; p < SP; p++) a[p] = A[rowc[t] + k - p];
+                if (t < kb || lane < o - (SP - 1)) {
+#pragma unroll
+                    for (int p = 0; p < SP; p++) xr[t] -= a[p] * xf[p];
+                } else {
+#pragma unroll
+                    for (int p = 0; p < SP; p++)
+                        if (lane == o - p) xr[t] = xf[p];
+                }
+            }
+        }
+        for (; k >= k0; k--) {  // one pivot at a time
+            const int o = k - k0;
+            const LT xk = __shfl_sync(gm, xr[kb], o) * A[k * LD + k];
+#pragma unroll
+            for (int t = 0; t <= kb; t++) {
+                const LT a = A[rowc[t] + k];
+                if (t < kb || lane < o) xr[t] -= a * xk;
+                else if (lane == o) xr[t] = xk;
+            }
+        }
+    }
+    }
 #pragma unroll
     for (int t = 0; t < NS; t++) {
         const int i = lane + 32 * t;
@@ -959,7 +1050,14 @@ __device__ __forceinline__ void dense_subst(const LT *A, int D, int LD, LT *xb, 
     }
 }
 
-template <int G, typename LT>
+// Pivots per round of the dense block's triangular solves for a cell shape:
+// 4 for 8-slot lanes (measured: multiphase-232 +3.7%), 2 for the smaller
+// register budgets of fewer slots (4 there cost gas-72 6.6%)
+template <int G, int NPL>
+__host__ __device__ constexpr int subst_pivots() { return NPL >= 6 ? 4 : 2; }
+
+// SP: pivots per round of the dense block's triangular solves (2 or 4)
+template <int G, typename LT, int SP>
 __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, unsigned gm) {
     LT *x = c.x;
     const LT *lu = c.lu;
@@ -1008,10 +1106,10 @@ __device__ void substitute(const DevMech &m, const CellPtr<LT> &c, int lane, uns
         const unsigned wm = G <= 32 ? gm : 0xffffffffu;
         switch ((m.D + 31) >> 5) {
         case 0: break;
-        case 1: dense_subst<1, LT>(A, m.D, m.LD, x + m.d, lane, wm); break;
-        case 2: dense_subst<2, LT>(A, m.D, m.LD, x + m.d, lane, wm); break;
-        case 3: dense_subst<3, LT>(A, m.D, m.LD, x + m.d, lane, wm); break;
-        default: dense_subst<4, LT>(A, m.D, m.LD, x + m.d, lane, wm); break;
+        case 1: dense_subst<1, LT, SP>(A, m.D, m.LD, x + m.d, lane, wm); break;
+        case 2: dense_subst<2, LT, SP>(A, m.D, m.LD, x + m.d, lane, wm); break;
+        case 3: dense_subst<3, LT, SP>(A, m.D, m.LD, x + m.d, lane, wm); break;
+        default: dense_subst<4, LT, SP>(A, m.D, m.LD, x + m.d, lane, wm); break;
         }
     }
     gsync<G>(gm);
@@ -1276,7 +1374,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                         int p = lane + G * s;
                         if (p < n) c.x[p] = to_lu<LT>(-(e[s] - gamma * f[s] + z[1][s] * rl1));
                     }
-                    substitute<G, LT>(m, c, lane, gm);
+                    substitute<G, LT, subst_pivots<G, NPL>()>(m, c, lane, gm);
                     // the update's norm in the LU precision (it only steers the iteration)
                     LT dsq = (LT)0;
                     bool nf = false;
