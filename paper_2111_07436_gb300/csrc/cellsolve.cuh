@@ -1050,11 +1050,13 @@ __device__ __forceinline__ void dense_subst(const LT *A, int D, int LD, LT *xb, 
     }
 }
 
-// Pivots per round of the dense block's triangular solves for a cell shape:
-// 4 for 8-slot lanes (measured: multiphase-232 +3.7%), 2 for the smaller
-// register budgets of fewer slots (4 there cost gas-72 6.6%)
-template <int G, int NPL>
-__host__ __device__ constexpr int subst_pivots() { return NPL >= 6 ? 4 : 2; }
+// Pivots per round of the dense block's triangular solves for a cell shape
+// and LU precision: 4 for the FP32 LU of 8-slot lanes (measured:
+// multiphase-232 +3.6%, water parameter +2.0%), 2 otherwise (4 cost the
+// 3-slot gas-72 kernel 6.6% and the FP64 8-slot kernels 6-7%, 3 cost
+// gas-72 3.5%)
+template <int G, int NPL, typename LT>
+__host__ __device__ constexpr int subst_pivots() { return (sizeof(LT) == 4 && NPL >= 6) ? 4 : 2; }
 
 // SP: pivots per round of the dense block's triangular solves (2 or 4)
 template <int G, typename LT, int SP>
@@ -1374,7 +1376,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                         int p = lane + G * s;
                         if (p < n) c.x[p] = to_lu<LT>(-(e[s] - gamma * f[s] + z[1][s] * rl1));
                     }
-                    substitute<G, LT, subst_pivots<G, NPL>()>(m, c, lane, gm);
+                    substitute<G, LT, subst_pivots<G, NPL, LT>()>(m, c, lane, gm);
                     // the update's norm in the LU precision (it only steers the iteration)
                     LT dsq = (LT)0;
                     bool nf = false;

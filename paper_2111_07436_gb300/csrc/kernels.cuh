@@ -162,7 +162,7 @@ __global__ void k_lu_solve(DevMech m, long long n_cells, const double *state, co
     if (lane == 0) status[cell] = ok ? 0 : ST_SINGULAR;
     if (!ok) return;
     for (int p = lane; p < m.n; p += G) c.x[p] = (LT)b[cell * m.n + __ldg(m.perm + p)];
-    substitute<G, LT, subst_pivots<G, NPL>()>(m, c, lane, gm);
+    substitute<G, LT, subst_pivots<G, NPL, LT>()>(m, c, lane, gm);
     for (int p = lane; p < m.n; p += G) x[cell * m.n + __ldg(m.perm + p)] = (double)c.x[p];
 }
 
