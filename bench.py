@@ -31,11 +31,11 @@ FP64_PEAK_NOMINAL_GFLOPS = 1250.0  # GB300 dense FP64, nominal
 # DRAM bytes (read + write) per cell of one mixed-form k_solve launch, from
 # one ncu capture of the same kernel on a smaller launch of the same
 # workload (gas-72: 4096 cells, 4.18 MB; multiphase-232: 2048 cells,
-# 5.36 MB; particles: 512 cells, 5.91 MB; water: 2048 cells, 5.56 MB): the
+# 5.35 MB; particles: 512 cells, 5.91 MB; water: 2048 cells, 5.56 MB): the
 # inputs only, so traffic scales with the cells.  To be taken again
 # whenever the kernel changes.
-DRAM_BYTES_PER_CELL = {"gas72": 4.180480e6 / 4096, "multiphase232": 5.358592e6 / 2048,
-                       "particles": 5.905152e6 / 512, "water": 5.556224e6 / 2048}
+DRAM_BYTES_PER_CELL = {"gas72": 4.180480e6 / 4096, "multiphase232": 5.347840e6 / 2048,
+                       "particles": 5.905152e6 / 512, "water": 5.557248e6 / 2048}
 
 
 def args():
