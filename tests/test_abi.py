@@ -69,3 +69,15 @@ def test_info_reports_the_water_parameter():
     lay = w.layout(mj)
     assert inf.n_electrolytes == 2 and inf.env_rh == lay.env.index("RH")
     assert inf.n_env == len(lay.env)
+
+
+def test_long_rows_keep_their_partial_sums_within_budget():
+    """The chain-rule entries of a water parameter lengthen the gas rows that
+    every particle couples to; cutting those rows into chunks must not blow
+    up the per-cell partial sums (the compiler caps them per level).  Without
+    the cap the 100-particle cell needed 166 KB of shared memory and the
+    160-particle one did not fit."""
+    from tests import mechs as M
+    for n_particles, limit in ((40, 30000), (100, 60000), (160, 75000)):
+        inf = camp.Mechanism(json.dumps(M.water_particles_mechanism(n_particles)), device=False).info
+        assert inf.smem_per_cell_mixed < limit, (n_particles, inf.smem_per_cell_mixed)
