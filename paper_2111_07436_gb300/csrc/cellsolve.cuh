@@ -1052,9 +1052,9 @@ __device__ __forceinline__ void dense_subst(const LT *A, int D, int LD, LT *xb, 
 
 // Pivots per round of the dense block's triangular solves for a cell shape
 // and LU precision: 4 for the FP32 LU of 8-slot lanes (measured:
-// multiphase-232 +3.6%, water parameter +2.0%), 2 otherwise (4 cost the
-// 3-slot gas-72 kernel 6.6% and the FP64 8-slot kernels 6-7%, 3 cost
-// gas-72 3.5%)
+// multiphase-232 +3.6%, water parameter +2.0%; 8 cost it 1%), 2 otherwise
+// (4 cost the 3-slot gas-72 kernel 6.6% and the FP64 8-slot kernels 6-7%,
+// 3 cost gas-72 3.5%)
 template <int G, int NPL, typename LT>
 __host__ __device__ constexpr int subst_pivots() { return (sizeof(LT) == 4 && NPL >= 6) ? 4 : 2; }
 
