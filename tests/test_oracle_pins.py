@@ -574,3 +574,19 @@ def test_status_codes():
     assert m.integrate(np.array([1.0]), bad, 10.0, 1e-4, 1e-5)[1] == 5
     y, s, st = m.integrate(np.array([1.0]), env, 1e4, 1e-8, 1e-12, max_steps=3)
     assert s == 1 and y[0] == 1.0 and st[0] == 3
+
+
+# ---------------------------------------------------------------- accuracy
+
+def test_rate_constants_match_50_digit_evaluation():
+    """The oracle's FP64 rate constants against the same expressions in
+    50-digit arithmetic (every Arrhenius parameter active, Troe with N != 1,
+    the custom types, the Henry partition H_cc L and K_eq(T))."""
+    pytest.importorskip("mpmath")
+    from tests import highprec
+    m = oracle.Mechanism(highprec.mechanism())
+    for T, P, L in highprec.CONDITIONS:
+        kf, kr = m.rate_constants(env_of(m, T, P, sections=[(1e-6, 1e8, L)]))
+        for k, kind, exact in highprec.constants(T, P, L):
+            got = kf[k] if kind == "kf" else kf[k] / kr[k]
+            assert abs(got / float(exact) - 1) < 1e-14, (k, kind, T)
