@@ -339,3 +339,23 @@ def test_water_parameter_dry_sections(form):
     parity.check(om, y0, env, wl.dt, wl.rtol, wl.atol, yg, yo)
     dry = [lay.species.index(s) for s in lay.species if s.startswith("bin0.")]
     assert np.array_equal(yg[::2][:, dry], y0[::2][:, dry])
+
+
+@pytest.mark.parametrize("variant,tol", [(camp.VARIANT_FP64, 1e-10), (camp.VARIANT_MIXED, 1e-5)],
+                         ids=["fp64", "mixed"])
+def test_linear_invariant_is_conserved(variant, tol):
+    """With emission and loss off, the chemistry conserves an integer atom
+    count per species, and BDF with Newton keeps linear invariants up to the
+    Newton residual: FP64 to 1e-10 relative, the mixed form (FP32 iteration
+    matrix) to 0.1 rtol."""
+    wl = w.workload(3)
+    lay = w.layout(wl.mech)
+    gm = camp.Mechanism(wl.json())
+    y0, env = wl.inputs(512)
+    for k, kind in enumerate(lay.runtime_kind):
+        if kind in ("EMISSION", "FIRST_ORDER_LOSS"):
+            env[:, 2 + k] = 0.0
+    yg, st = _gpu_solve(gm, y0, env, wl.dt, wl.rtol, wl.atol, variant, variant == camp.VARIANT_MIXED)
+    assert (st == 0).all()
+    w0, w1 = y0 @ lay.atoms, yg @ lay.atoms
+    assert np.max(np.abs(w1 / w0 - 1)) < tol
