@@ -590,3 +590,22 @@ def test_rate_constants_match_50_digit_evaluation():
         for k, kind, exact in highprec.constants(T, P, L):
             got = kf[k] if kind == "kf" else kf[k] / kr[k]
             assert abs(got / float(exact) - 1) < 1e-14, (k, kind, T)
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4, 5])
+def test_fixed_order_global_error_slope(q):
+    """Order of accuracy: BDF-q at a fixed step from exact starting history
+    integrates y' = -y to t = 1 with a global error O(h^q), so halving h
+    divides the error by 2^q."""
+    m = oracle.Mechanism(M.mech(["X"], [M.loss("X")]))
+    env = env_of(m, 298.0, 1e5, runtime=[1.0])
+    errs = []
+    for n_steps in (16, 32, 64):
+        h = 1.0 / n_steps
+        z = np.array([[(-h) ** j / math.factorial(j)] for j in range(q + 1)])  # exact Nordsieck
+        for _ in range(n_steps):
+            z, _, err = m.bdf_step(env, z, q, h, 1e-12, 1e-20)
+            assert err >= 0.0
+        errs.append(abs(z[0, 0] - math.exp(-1.0)))
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(s - q) < 0.35 for s in slopes), (q, slopes, errs)
