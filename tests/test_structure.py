@@ -150,3 +150,27 @@ def test_compiler_rejects_malformed_input():
                 '{"species": [{"name": "A"}, {"name": "A"}], "reactions": []}'):
         with pytest.raises(camp.CampError):
             camp.Mechanism(bad, device=False)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_water_mechanisms_compile_bit_exact(seed):
+    """Random small sectional mechanisms with a water parameter over random
+    electrolytes: the compiler's tables pass its own bounds checks (loading
+    raises otherwise) and its structure equals the oracle's enumeration."""
+    from paper_2111_07436_gb300 import camp
+    rng = np.random.default_rng(600 + seed)
+    n_gas = int(rng.integers(6, 10))
+    mj = w.add_aqueous_sections(
+        w.gas_mechanism(f"rw{seed}", n_gas, int(rng.integers(2, n_gas)), 1, 1, 1, 1, seed=700 + seed,
+                        max_occupancy=3 * n_gas),
+        seed=800 + seed, n_sections=int(rng.integers(1, 4)), n_phase_species=6, n_henry=2,
+        n_split_eq=1, n_simple_eq=1)
+    phase = [p["name"] for p in mj["phases"]["aqueous"]]
+    chosen = rng.choice(phase, int(rng.integers(1, 4)), replace=False)
+    mj["parameters"] = [{"type": "ZSR_AEROSOL_WATER", "electrolytes": [
+        {"species": str(e), "Y": [float(rng.uniform(2, 4)), float(rng.uniform(-2, -0.5))]} for e in chosen]}]
+    text = json.dumps(mj)
+    got = camp.Mechanism(text, device=False).structure()
+    want = oracle.Mechanism(text).structure()
+    for key, v in want.items():
+        assert np.array_equal(got[key], np.asarray(v, dtype=np.int32)), key
