@@ -1194,12 +1194,13 @@ __device__ __forceinline__ void nord_rescale(double (&z)[QMAX + 1][NPL], int q, 
     }
 }
 
-// x^p for the step-size and order heuristics.  Only the accept/reject tests
-// need FP64; a step-size factor needs a few digits, so this takes FP32
-// log2/exp2 (x = 0 gives 0 for p > 0 and +inf for p < 0).
+// x^p for the step-size and order heuristics of the mixed form.  Only the
+// accept/reject tests need FP64; a step-size factor needs a few digits, so
+// this takes FP32 log2/exp2 (x = 0 gives 0 for p > 0 and +inf for p < 0).
 __device__ __forceinline__ float ctl_powf(float x, float p) {
     return exp2f(p * __log2f(x));
 }
+
 
 // 1/d for d > 0 to ~1e-14 relative: an FP32 estimate refined by one
 // Newton-Raphson step w <- w (2 - d w) in FP64; outside the FP32 normal
@@ -1211,6 +1212,42 @@ __device__ __forceinline__ double recip_refined(double d) {
     }
     return 1.0 / d;
 }
+
+// The step controller's scalar arithmetic.  EXACT (the plain FP64 form)
+// takes every scalar decision with the oracle's own FP64 operations --
+// divisions, square roots and pow -- so that the two follow the same step
+// sequence up to the roundoff of f, J and the LU; otherwise (the mixed form)
+// the cheaper forms: reciprocals, squared norms and FP32 powers.  A norm v
+// is carried as the norm itself (EXACT: v = c WRMS, from a root) or as its
+// square (v = (c WRMS)^2, no root); either way the tests compare v with 1.
+template <bool EXACT>
+struct Ctl {
+    // v from the sum s of n squared weighted terms and the coefficient c
+    static __device__ __forceinline__ double norm(double c, double c2, double s, int n, double rn) {
+        if constexpr (EXACT) return c * sqrt(s / (double)n);
+        else return c2 * (s * rn);
+    }
+    // (k err)^(1/p)
+    static __device__ __forceinline__ double pow_err(double k, double v, int p) {
+        if constexpr (EXACT) return pow(k * v, 1.0 / (double)p);
+        else return (double)ctl_powf((float)(k * k) * (float)v, 0.5f / (float)p);
+    }
+    // 0.9 err^(-1/p): the step factor after an error-test failure
+    static __device__ __forceinline__ double fail_eta(double v, int p) {
+        if constexpr (EXACT) return 0.9 * pow(v, -1.0 / (double)p);
+        else return (double)(0.9f * ctl_powf((float)v, -0.5f / (float)p));
+    }
+    // a / b for the ratio of step-size coefficients (rb = 1 / b)
+    static __device__ __forceinline__ double ratio(double a, double b, double rb) {
+        if constexpr (EXACT) return a / b;
+        else return a * rb;
+    }
+    // the error weight 1 / (rtol |y| + atol)
+    static __device__ __forceinline__ double weight(double rtol, double y, double atol) {
+        if constexpr (EXACT) return 1.0 / __dadd_rn(__dmul_rn(rtol, fabs(y)), atol);
+        else return recip_refined(fma(rtol, fabs(y), atol));
+    }
+};
 
 struct CellStats {
     int steps, newton, jac, errfail, ordsum;
@@ -1228,6 +1265,8 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                               double hmin_frac, double *step_io, int lane, unsigned gm,
                               CellStats &st) {
     const int n = m.n;
+    constexpr bool EXACT = sizeof(LT) == 8;  // the plain FP64 form
+    using C = Ctl<EXACT>;
     const double h_in = step_io ? *step_io : 0.0;
     st.steps = st.newton = st.jac = st.errfail = st.ordsum = 0;
 
@@ -1270,7 +1309,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
             int p = lane + G * s;
             double a = 1.0;
             if (p < n) a = atol_len == 1 ? __ldg(atol) : __ldg(atol + __ldg(m.perm + p));
-            w[s] = (p < n) ? recip_refined(fma(rtol, fabs(z[0][s]), a)) : 0.0;
+            w[s] = (p < n) ? C::weight(rtol, z[0][s], a) : 0.0;
         }
     };
     auto any_nonfinite = [&](const double(&v)[NPL]) {
@@ -1314,10 +1353,12 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
     bool have_lu = false, need_setup = true, ep_valid = false;
     double t = 0.0, gamma_lu = 0.0, rgamma_lu = 0.0;
     int status = ST_OK;
-    // Squared-norm forms of the controller's tests (same decisions as
-    // comparing the norms themselves): Newton converged when
-    // dn^2 min(1, rho^2) <= tol^2, diverged when rho^2 > RHO_DIV^2; the step
-    // is accepted when ecoef^2 mean((e w)^2) <= 1.
+    // The mixed form takes the controller's tests on squared norms (the same
+    // decisions as comparing the norms themselves, without roots): Newton
+    // converged when dn^2 min(1, rho^2) <= tol^2, diverged when
+    // rho^2 > RHO_DIV^2; the step is accepted when ecoef^2 mean((e w)^2) <= 1.
+    // The FP64 form compares the norms themselves, as the oracle does
+    // (err2 and dn2 then hold the norms, not their squares).
     constexpr double NEWTON_TOL2 = NEWTON_TOL * NEWTON_TOL;
     constexpr double RHO_DIV2 = RHO_DIV * RHO_DIV;
 
@@ -1341,9 +1382,10 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
             }
             nord_predict<NPL>(z, q);
             const double rl1 = m.inv_l1[q];
-            const double gamma = h * rl1;
+            const double gamma = C::ratio(h, m.lcoef[q][1], rl1);
             bool jcur = false, lu_fail = false;
-            if (!have_lu || need_setup || nst >= nst_lu + MSBJ || fabs(gamma * rgamma_lu - 1.0) > DGMAX) {
+            if (!have_lu || need_setup || nst >= nst_lu + MSBJ ||
+                fabs(C::ratio(gamma, gamma_lu, rgamma_lu) - 1.0) > DGMAX) {
 #pragma unroll
                 for (int s = 0; s < NPL; s++) {
                     int p = lane + G * s;
@@ -1366,7 +1408,9 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                 LT dprev2 = (LT)0;
 #pragma unroll
                 for (int s = 0; s < NPL; s++) e[s] = 0.0;
-                const LT scale = (gamma != gamma_lu) ? (LT)2 / ((LT)1 + to_lu<LT>(gamma * rgamma_lu)) : (LT)1;
+                const LT scale = (gamma != gamma_lu)
+                                     ? (LT)2 / ((LT)1 + to_lu<LT>(C::ratio(gamma, gamma_lu, rgamma_lu)))
+                                     : (LT)1;
                 for (int it = 0; it < NEWTON_MAXIT; it++) {
                     eval_f_at<G, NPL, LT, W>(m, c, z[0], 1.0, e, f, lane, gm);
                     st.newton++;
@@ -1389,15 +1433,18 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                         dsq += upd_term(xl, w[s]);
                         nf |= !isfinite(xl);
                     }
-                    const LT dn2 = gsum_t<G, LT>(dsq, gm) * (LT)m.rn;
+                    // EXACT: the norm itself, as the oracle tests it; mixed:
+                    // its square in the LU precision
+                    const LT dn2 = EXACT ? (LT)sqrt((double)gsum_t<G, LT>(dsq, gm) / (double)n)
+                                         : gsum_t<G, LT>(dsq, gm) * (LT)m.rn;
                     if (gany<G>(nf, gm) || !isfinite(dn2)) break;
                     LT test2 = dn2;
                     if (it > 0) {
                         const LT rho2 = dn2 / dprev2;
-                        if (rho2 > (LT)RHO_DIV2) break;
+                        if (rho2 > (LT)(EXACT ? RHO_DIV : RHO_DIV2)) break;
                         if (rho2 < (LT)1) test2 = dn2 * rho2;
                     }
-                    if (test2 <= (LT)NEWTON_TOL2) { conv = true; break; }
+                    if (test2 <= (LT)(EXACT ? NEWTON_TOL : NEWTON_TOL2)) { conv = true; break; }
                     dprev2 = dn2;
                 }
             }
@@ -1416,7 +1463,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                 double es = 0.0;
 #pragma unroll
                 for (int s = 0; s < NPL; s++) { double a = e[s] * w[s]; es += a * a; }
-                err2 = m.ecoef2[q] * (gsum<G>(es, gm) * m.rn);
+                err2 = C::norm(m.ecoef[q], m.ecoef2[q], gsum<G>(es, gm), n, m.rn);
             }
             if (err2 > 1.0) {
                 nord_retract<NPL>(z, q);
@@ -1430,12 +1477,11 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
 #pragma unroll
                     for (int s = 0; s < NPL; s++) z[1][s] = h * f[s];
                 } else {
-                    // 0.9 err^(-1/(q+1)) = 0.9 (err^2)^(-1/(2(q+1)))
-                    float eta = 0.9f * ctl_powf((float)err2, -0.5f / (float)(q + 1));
-                    if (eta < 0.2f) eta = 0.2f;
-                    h *= (double)eta;
+                    double eta = C::fail_eta(err2, q + 1);
+                    if (eta < 0.2) eta = 0.2;
+                    h *= eta;
                     if (h < hmin) { status = ST_ERRTEST; break; }
-                    nord_rescale<NPL>(z, q, (double)eta);
+                    nord_rescale<NPL>(z, q, eta);
                 }
                 qwait = q + 1;
                 continue;
@@ -1459,9 +1505,9 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
         if (any_nonfinite(z[0])) { status = ST_NONFINITE; break; }
 
         if (--qwait <= 0 && t < T) {
-            // eta = 1 / ((c err)^(1/(p+1)) + 1e-6), taken from squared norms
-            float eta_q = 1.0f / (ctl_powf(1.44f * (float)err2, 0.5f / (float)(q + 1)) + 1e-6f);
-            float eta_m = 0.0f, eta_p = 0.0f;
+            // eta = 1 / ((c err)^(1/(p+1)) + 1e-6), from the squared norms
+            double eta_q = 1.0 / (C::pow_err(1.2, err2, q + 1) + 1e-6);
+            double eta_m = 0.0, eta_p = 0.0;
             if (q > 1) {
                 double zs = 0.0;
 #pragma unroll
@@ -1471,24 +1517,25 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                         for (int s = 0; s < NPL; s++) { double a = z[j][s] * w[s]; zs += a * a; }
                     }
                 }
-                const double em2 = m.ecoef2[q - 1] * m.fact[q] * m.fact[q] * (gsum<G>(zs, gm) * m.rn);
-                eta_m = 1.0f / (ctl_powf(1.69f * (float)em2, 0.5f / (float)q) + 1e-6f);
+                const double ce = m.ecoef[q - 1] * m.fact[q];
+                const double em2 = C::norm(ce, ce * ce, gsum<G>(zs, gm), n, m.rn);
+                eta_m = 1.0 / (C::pow_err(1.3, em2, q) + 1e-6);
             }
             if (q < QMAX && ep_valid) {
                 double ds = 0.0;
 #pragma unroll
                 for (int s = 0; s < NPL; s++) { double a = (e[s] - ep[s]) * w[s]; ds += a * a; }
-                const double ep2 = m.ecoef2[q + 1] * (gsum<G>(ds, gm) * m.rn);
-                eta_p = 1.0f / (ctl_powf(1.96f * (float)ep2, 0.5f / (float)(q + 2)) + 1e-6f);
+                const double ep2 = C::norm(m.ecoef[q + 1], m.ecoef2[q + 1], gsum<G>(ds, gm), n, m.rn);
+                eta_p = 1.0 / (C::pow_err(1.4, ep2, q + 2) + 1e-6);
             }
-            float eta = eta_q;
+            double eta = eta_q;
             int qn = q;
             if (eta_m > eta) { eta = eta_m; qn = q - 1; }
             if (eta_p > eta) { eta = eta_p; qn = q + 1; }
-            if (eta < (float)ETA_THRESH) {
+            if (eta < ETA_THRESH) {
                 qwait = 2;
             } else {
-                if (eta > (float)ETA_MAX) eta = (float)ETA_MAX;
+                if (eta > ETA_MAX) eta = ETA_MAX;
                 if (qn == q + 1) {
                     const double c_up = m.lcoef[q][q] / (double)(q + 1);
 #pragma unroll
@@ -1500,8 +1547,8 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                     }
                 }
                 q = qn;
-                h *= (double)eta;
-                nord_rescale<NPL>(z, q, (double)eta);
+                h *= eta;
+                nord_rescale<NPL>(z, q, eta);
                 qwait = q + 1;
             }
         }
