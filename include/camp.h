@@ -93,6 +93,11 @@ typedef struct {
     int32_t env_rh;         /* env index of the relative humidity, -1 without
                                a ZSR_AEROSOL_WATER parameter */
     int32_t n_electrolytes; /* electrolytes of the water parameter (0: none) */
+    int64_t model_forcing;  /* sum over process instances of 2 |reactants| +
+                               |products| (distinct species): the flops of one
+                               f(y) in a per-process cost model that counts
+                               one multiply per reactant factor and one add
+                               per stoichiometric term */
 } camp_mech_info;
 
 /*
@@ -247,15 +252,18 @@ int camp_solve_host(const camp_mech *m, int64_t n_cells, double *state, const do
  *   Same arguments and results as camp_solve_host (host arrays in and out,
  *   synchronous on `stream`; opts->stats, if set, is a host array).
  *   The chunk must fit: n_cells * (8 n_species + 8 n_env + 4 [+ 20 with
- *   stats]) plus alignment must not exceed the array; larger calls return
- *   CAMP_E_INVAL and touch nothing -- split the chunk.
+ *   opts->stats] [+ 8 with opts->step]) + 8 atol_len, each array rounded
+ *   up to 256 bytes, plus 256 bytes for the work counter, must not exceed
+ *   the array; larger calls return CAMP_E_INVAL and touch nothing -- split
+ *   the chunk.
  *   The first call on a device looks up the array's device address (with
  *   that device current) and caches it; make that first call before any
  *   stream capture.
  *   All calls share the array and leave their data in it; the work counter
  *   is reset by every call.  Calls hold a process-wide lock and synchronise
- *   their stream before returning; calls that still overlap on the GPU (for
- *   example replays of a captured call on two streams) race on the array.
+ *   their stream before returning, on error paths too once a copy has been
+ *   enqueued; calls that still overlap on the GPU (for example replays of a
+ *   captured call on two streams) race on the array.
  * The paper has no counterpart to this entry point. */
 #define CAMP_STATIC_SCRATCH_BYTES (16u << 20)
 int camp_solve_host_static(const camp_mech *m, int64_t n_cells, double *state, const double *env,
@@ -286,6 +294,18 @@ typedef struct {
 
 int camp_solve_batch(const camp_group *groups, int32_t n_groups, double dt, double rtol,
                      const camp_solve_opts *opts, void *stream);
+
+/* camp_solve_batch on HOST arrays (paper Sect. 2.4.2: the host passes the
+ * state of each air mass and reads it back): every group's state, env,
+ * atol, status and the optional stats / step are host arrays (workspace is
+ * ignored).  Copies all groups in, solves them in one camp_solve_batch,
+ * copies states, statuses (and stats / steps) back and synchronises
+ * `stream` before returning.  The device staging buffer is kept by the
+ * library per device between calls (grown as needed, freed at exit); calls
+ * are serialised.  Pinned host memory gives asynchronous copies.  Errors as
+ * camp_solve_batch; on an error nothing is copied back. */
+int camp_solve_batch_host(const camp_group *groups, int32_t n_groups, double dt, double rtol,
+                          const camp_solve_opts *opts, void *stream);
 
 /* ---- launch autotuning ------------------------------------------------------ */
 /* Time camp_solve on the given cells (device arrays, left unchanged) for
@@ -381,8 +401,53 @@ int camp_server_stats(camp_server *s, int32_t *pending, int32_t *inflight, size_
  * part of the serving loop this library adds. */
 int camp_server_cancel(camp_server *s, uint64_t req_id);
 
-/* Finish every queued and in-flight chunk, then release the server. */
+/* Finish every queued and in-flight chunk, then release the server (and
+ * every resident cell set still alive). */
 int camp_server_destroy(camp_server *s);
+
+/* ---- resident cell sets ---------------------------------------------------
+ * The host model hands the SAME air masses to the solver every time step
+ * (Sect. 2.4.2).  A resident set keeps one chunk's state (and status, and
+ * with warm_start each cell's step size) in device memory across the host's
+ * consecutive steps: create it once from the initial state, then submit one
+ * step at a time with that step's env and dt -- only env (8 n_env bytes a
+ * cell) crosses the bus -- and read or overwrite the state on demand.  The
+ * set's memory counts against the server's budget from create to destroy.
+ * Steps of one set run in submission order (each waits for the previous);
+ * steps of different sets and ordinary chunks overlap as usual.  With
+ * warm_start = 0 every step is a cold start and gives the result of a lone
+ * camp_solve of the set's current state; with warm_start = 1 each cell
+ * carries its step size from one step to the next (camp_solve_opts.step,
+ * starting cold). */
+typedef struct camp_resident camp_resident;
+
+/* Allocate the set on the server's device and copy the initial state (HOST
+ * [n_cells][n_species]) in; synchronous.  CAMP_E_BUDGET if the set does not
+ * fit in what the budget has left. */
+int camp_server_resident_create(camp_server *s, const camp_mech *m, int64_t n_cells,
+                                const double *state, int32_t warm_start, camp_resident **out);
+
+/* Queue one step of the set: env (HOST [n_cells][n_env]) is copied in when
+ * the step is admitted and must stay valid until the request finishes;
+ * status (HOST [n_cells], or NULL to leave it on the device) receives the
+ * per-cell status.  opts as for camp_server_submit (its stats, step and
+ * workspace are ignored).  Completion as for any request (poll / wait). */
+int camp_server_resident_step(camp_server *s, camp_resident *r, const double *env, double dt, double rtol,
+                              double atol, int32_t *status, const camp_solve_opts *opts, uint64_t *req_id);
+
+/* Wait (up to timeout_ms; CAMP_E_TIMEOUT) until every step submitted to the
+ * set has finished, then copy its state (and, if not NULL, the last step's
+ * status and the carried step sizes) to HOST arrays. */
+int camp_server_resident_read(camp_server *s, camp_resident *r, double *state, int32_t *status,
+                              double *step, int32_t timeout_ms);
+
+/* Wait as for read, then overwrite the set's state from a HOST array (the
+ * host model's other processes -- transport, emissions -- changed it).
+ * Carried step sizes are kept. */
+int camp_server_resident_write(camp_server *s, camp_resident *r, const double *state, int32_t timeout_ms);
+
+/* Wait for the set's steps, then release its device memory and budget. */
+int camp_server_resident_destroy(camp_server *s, camp_resident *r);
 
 /* ---- measurement --------------------------------------------------------- */
 /* Sustained fused multiply-add throughput of the current device in GFLOP/s

@@ -72,13 +72,21 @@ extern "C" int camp_solve_host_static(const camp_mech *m, int64_t n_cells, doubl
     double *d_step = host_step ? (double *)(base + b_state + b_env + b_status + b_atol + b_stats + b_ws) : nullptr;
 
     cudaStream_t s = (cudaStream_t)stream;
+    // Once a copy is enqueued, every return waits for the stream first: the
+    // lock is released on return, and the next call (perhaps on another
+    // stream) must not overwrite the array while this call's work is in
+    // flight.
+    auto drain = [&](int code, const std::string &msg) {
+        cudaStreamSynchronize(s);
+        if (code == CAMP_OK) return CAMP_OK;
+        return msg.empty() ? code : camp_record_error(code, msg.c_str());
+    };
     const size_t n_state = (size_t)n_cells * inf.n_species * 8, n_env = (size_t)n_cells * inf.n_env * 8;
     cudaError_t e = cudaMemcpyAsync(d_state, state, n_state, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_env, env, n_env, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_atol, atol, (size_t)atol_len * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && host_step) e = cudaMemcpyAsync(d_step, host_step, (size_t)n_cells * 8, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess)
-        return camp_record_error(CAMP_E_CUDA, (std::string("staging copy: ") + cudaGetErrorString(e)).c_str());
+    if (e != cudaSuccess) return drain(CAMP_E_CUDA, std::string("staging copy: ") + cudaGetErrorString(e));
     camp_solve_opts o;
     camp_solve_opts_default(&o, opts ? opts->variant : CAMP_VARIANT_MIXED);
     if (opts) o = *opts;
@@ -86,7 +94,7 @@ extern "C" int camp_solve_host_static(const camp_mech *m, int64_t n_cells, doubl
     o.step = d_step;
     o.workspace = d_ws;  // the persistent grid's counter: zeroed by camp_solve
     int rc = camp_solve(m, n_cells, d_state, d_env, dt, rtol, d_atol, atol_len, d_status, &o, stream);
-    if (rc != CAMP_OK) return rc;
+    if (rc != CAMP_OK) return drain(rc, "");  // camp_solve recorded the message
     e = cudaMemcpyAsync(state, d_state, n_state, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(status, d_status, (size_t)n_cells * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && host_stats)
@@ -94,7 +102,6 @@ extern "C" int camp_solve_host_static(const camp_mech *m, int64_t n_cells, doubl
     if (e == cudaSuccess && host_step)
         e = cudaMemcpyAsync(host_step, d_step, (size_t)n_cells * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess)
-        return camp_record_error(CAMP_E_CUDA, (std::string("result copy: ") + cudaGetErrorString(e)).c_str());
+    if (e != cudaSuccess) return drain(CAMP_E_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
     return CAMP_OK;
 }
