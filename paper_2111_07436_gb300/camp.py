@@ -36,7 +36,8 @@ class MechInfo(ctypes.Structure):
                 ("smem_per_cell_fp64", ctypes.c_int32), ("factor_updates", ctypes.c_int64),
                 ("flops_forcing", ctypes.c_int64), ("flops_jacobian", ctypes.c_int64),
                 ("flops_factor", ctypes.c_int64), ("flops_solve", ctypes.c_int64),
-                ("env_rh", ctypes.c_int32), ("n_electrolytes", ctypes.c_int32)]
+                ("env_rh", ctypes.c_int32), ("n_electrolytes", ctypes.c_int32),
+                ("model_forcing", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -79,7 +80,9 @@ EXPORTS = ["camp_mech_load", "camp_mech_compile", "camp_mech_free", "camp_mech_i
            "camp_lu_solve", "camp_last_error", "camp_server_create", "camp_server_submit",
            "camp_server_poll", "camp_server_wait", "camp_server_stats", "camp_server_cancel",
            "camp_server_destroy",
-           "camp_solve_batch", "camp_autotune", "camp_probe_fma_rate", "camp_solve_host_static"]
+           "camp_solve_batch", "camp_solve_batch_host", "camp_autotune", "camp_probe_fma_rate",
+           "camp_solve_host_static", "camp_server_resident_create", "camp_server_resident_step",
+           "camp_server_resident_read", "camp_server_resident_write", "camp_server_resident_destroy"]
 
 
 def lib():
@@ -119,7 +122,14 @@ def lib():
     L.camp_server_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_size_t)]
     L.camp_server_cancel.argtypes = [vp, ctypes.c_uint64]
     L.camp_server_destroy.argtypes = [vp]
+    L.camp_server_resident_create.argtypes = [vp, vp, i64, vp, i32, ctypes.POINTER(vp)]
+    L.camp_server_resident_step.argtypes = [vp, vp, vp, dbl, dbl, dbl, vp, ctypes.POINTER(SolveOpts),
+                                            ctypes.POINTER(ctypes.c_uint64)]
+    L.camp_server_resident_read.argtypes = [vp, vp, vp, vp, vp, i32]
+    L.camp_server_resident_write.argtypes = [vp, vp, vp, i32]
+    L.camp_server_resident_destroy.argtypes = [vp, vp]
     L.camp_solve_batch.argtypes = [ctypes.POINTER(Group), i32, dbl, dbl, ctypes.POINTER(SolveOpts), vp]
+    L.camp_solve_batch_host.argtypes = L.camp_solve_batch.argtypes
     L.camp_autotune.argtypes = [vp, i64, vp, vp, dbl, dbl, vp, i32, i32, ctypes.POINTER(i32),
                                 ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
     L.camp_probe_fma_rate.argtypes = [i32, ctypes.POINTER(dbl), vp]
@@ -374,6 +384,11 @@ class Server:
         _check(rc)
         return True
 
+    def resident(self, mech, state, warm_start=False):
+        """A resident cell set initialised from the host array state [C, n]
+        (copied in; the set keeps its state on the device)."""
+        return Resident(self, mech, state, warm_start)
+
     def stats(self):
         p, i, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
         _check(lib().camp_server_stats(self._h, ctypes.byref(p), ctypes.byref(i), ctypes.byref(b)))
@@ -388,6 +403,63 @@ class Server:
     def __del__(self):
         if _lib is not None:
             self.close()
+
+
+class Resident:
+    """A chunk whose state stays on the device across the host's steps
+    (camp_server_resident_*).  step() queues one step (env copied in at
+    admission; keep env alive until the request finishes); read() / write()
+    move the state on demand."""
+
+    def __init__(self, server, mech, state, warm_start=False):
+        st = np.ascontiguousarray(state, dtype=np.float64)
+        if st.ndim != 2 or st.shape[1] != mech.n:
+            raise CampError("state must be [C, n_species]")
+        h = ctypes.c_void_p()
+        _check(lib().camp_server_resident_create(server._h, mech._h, st.shape[0], ctypes.c_void_p(st.ctypes.data),
+                                                 int(bool(warm_start)), ctypes.byref(h)))
+        self._srv, self._h, self.mech, self.n_cells = server, h, mech, st.shape[0]
+
+    def step(self, env, dt, rtol, atol, status=None, variant=VARIANT_MIXED, persistent=None):
+        ev = env if isinstance(env, np.ndarray) else env.numpy()
+        if ev.dtype != np.float64 or not ev.flags.c_contiguous or ev.shape != (self.n_cells, self.mech.n_env):
+            raise CampError("env must be C-contiguous float64 [C, n_env]")
+        ss = None
+        if status is not None:
+            ss = status if isinstance(status, np.ndarray) else status.numpy()
+            if ss.dtype != np.int32 or ss.shape != (self.n_cells,):
+                raise CampError("status must be int32 [C]")
+        o = self.mech.opts(variant, persistent)
+        rid = ctypes.c_uint64()
+        _check(lib().camp_server_resident_step(self._srv._h, self._h, ctypes.c_void_p(ev.ctypes.data), float(dt),
+                                               float(rtol), float(atol),
+                                               ctypes.c_void_p(ss.ctypes.data) if ss is not None else None,
+                                               ctypes.byref(o), ctypes.byref(rid)))
+        self._srv._keep[rid.value] = (env, status, self)
+        return rid.value
+
+    def read(self, timeout_ms=600000, with_step=False):
+        """(state [C, n], status of the last step [C][, carried step sizes])"""
+        y = np.zeros((self.n_cells, self.mech.n))
+        st = np.zeros(self.n_cells, dtype=np.int32)
+        hs = np.zeros(self.n_cells) if with_step else None
+        _check(lib().camp_server_resident_read(self._srv._h, self._h, ctypes.c_void_p(y.ctypes.data),
+                                               ctypes.c_void_p(st.ctypes.data),
+                                               ctypes.c_void_p(hs.ctypes.data) if hs is not None else None,
+                                               int(timeout_ms)))
+        return (y, st, hs) if with_step else (y, st)
+
+    def write(self, state, timeout_ms=600000):
+        st = np.ascontiguousarray(state, dtype=np.float64)
+        if st.shape != (self.n_cells, self.mech.n):
+            raise CampError("state must be [C, n_species]")
+        _check(lib().camp_server_resident_write(self._srv._h, self._h, ctypes.c_void_p(st.ctypes.data),
+                                                int(timeout_ms)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._srv._h is not None:
+            _check(lib().camp_server_resident_destroy(self._srv._h, self._h))
+        self._h = None
 
 
 def workspace(device):
@@ -413,6 +485,39 @@ def solve_batch(groups, dt, rtol, variant=VARIANT_MIXED, stream=None):
     o = SolveOpts()
     lib().camp_solve_opts_default(ctypes.byref(o), variant)
     _check(lib().camp_solve_batch(arr, len(groups), float(dt), float(rtol), ctypes.byref(o), _stream(stream)))
+
+
+def _host_arr(a, dtype, shape, name):
+    a = a if isinstance(a, np.ndarray) else a.numpy()
+    if a.dtype != dtype or not a.flags.c_contiguous or tuple(a.shape) != tuple(shape):
+        raise CampError(f"{name} must be a C-contiguous {np.dtype(dtype).name} host array of shape {shape}")
+    return a
+
+
+def solve_batch_host(groups, dt, rtol, variant=VARIANT_MIXED, stream=None):
+    """groups: list of dicts {mech, state, env, atol, status, stats?, step?}
+    of host arrays (numpy, or pinned torch tensors); states are updated in
+    place.  One synchronous call: copies in, one camp_solve_batch, copies out."""
+    arr = (Group * len(groups))()
+    keep = []
+    for i, g in enumerate(groups):
+        m = g["mech"]
+        st = g["state"] if isinstance(g["state"], np.ndarray) else g["state"].numpy()
+        C = st.shape[0]
+        st = _host_arr(st, np.float64, (C, m.n), "state")
+        ev = _host_arr(g["env"], np.float64, (C, m.n_env), "env")
+        a = np.ascontiguousarray(np.atleast_1d(np.asarray(g["atol"], dtype=np.float64)))
+        ss = _host_arr(g["status"], np.int32, (C,), "status")
+        stats = _host_arr(g["stats"], np.int32, (C, NSTATS), "stats") if g.get("stats") is not None else None
+        step = _host_arr(g["step"], np.float64, (C,), "step") if g.get("step") is not None else None
+        keep += [st, ev, a, ss, stats, step]
+        arr[i] = Group(m._h.value, C, st.ctypes.data, ev.ctypes.data, a.ctypes.data, a.size, ss.ctypes.data,
+                       stats.ctypes.data if stats is not None else None, None,
+                       step.ctypes.data if step is not None else None)
+    o = SolveOpts()
+    lib().camp_solve_opts_default(ctypes.byref(o), variant)
+    _check(lib().camp_solve_batch_host(arr, len(groups), float(dt), float(rtol), ctypes.byref(o),
+                                       _stream(stream)))
 
 
 def probe_fma_rate(fp64=True, stream=None):

@@ -225,6 +225,7 @@ int camp_mech_info_get(const camp_mech *m, camp_mech_info *o) {
     o->flops_solve = h.flops_solve;
     o->env_rh = h.rh_slot;
     o->n_electrolytes = (int32_t)h.el_phase.size();
+    o->model_forcing = h.model_forcing;
     return CAMP_OK;
 }
 
@@ -469,6 +470,95 @@ int camp_solve_batch(const camp_group *groups, int32_t n_groups, double dt, doub
         CUDA_TRY(cudaStreamWaitEvent(parent, ev_join[i], 0));
         if (rc != CAMP_OK) return rc;
     }
+    return CAMP_OK;
+}
+
+int camp_solve_batch_host(const camp_group *groups, int32_t n_groups, double dt, double rtol,
+                          const camp_solve_opts *opts, void *stream) {
+    CampRange range_("camp_solve_batch_host");
+    if (!groups || n_groups < 0 || n_groups > CAMP_MAX_GROUPS) return fail(CAMP_E_INVAL, "bad group count");
+    if (n_groups == 0) return CAMP_OK;
+    static std::mutex mu;
+    static void *stage[64] = {};
+    static size_t stage_bytes[64] = {};
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CAMP_E_INVAL, "device ordinal out of range");
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    struct Part { size_t state, env, atol, status, stats, step, ws; };
+    Part part[CAMP_MAX_GROUPS];
+    size_t need = 0;
+    for (int g = 0; g < n_groups; g++) {
+        const camp_group &gr = groups[g];
+        if (!gr.mech) return fail(CAMP_E_INVAL, "NULL mechanism in group");
+        if (gr.n_cells < 0) return fail(CAMP_E_INVAL, "n_cells < 0");
+        if (gr.n_cells > 0 && (!gr.state || !gr.env || !gr.atol || !gr.status))
+            return fail(CAMP_E_INVAL, "NULL array in group");
+        if (gr.atol_len != 1 && gr.atol_len != gr.mech->h.n) return fail(CAMP_E_INVAL, "atol_len must be 1 or n_species");
+        if (int rc = check_device(gr.mech)) return rc;
+        const size_t C = (size_t)gr.n_cells;
+        Part &p = part[g];
+        p.state = need; need += al(C * gr.mech->h.n * 8);
+        p.env = need; need += al(C * gr.mech->h.n_env * 8);
+        p.atol = need; need += al((size_t)gr.atol_len * 8);
+        p.status = need; need += al(C * 4);
+        p.stats = need; need += gr.stats ? al(C * 4 * CAMP_NSTATS) : 0;
+        p.step = need; need += gr.step ? al(C * 8) : 0;
+        p.ws = need; need += al(camp_workspace_bytes());
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (stage_bytes[dev] < need) {
+        if (stage[dev]) cudaFree(stage[dev]);
+        stage[dev] = nullptr;
+        stage_bytes[dev] = 0;
+        CUDA_TRY(cudaMalloc(&stage[dev], need));
+        stage_bytes[dev] = need;
+    }
+    char *base = (char *)stage[dev];
+    cudaStream_t s = (cudaStream_t)stream;
+    camp_group dg[CAMP_MAX_GROUPS];
+    // once a copy is enqueued, every return waits for the stream: the next
+    // call may reuse the buffer as soon as the lock is released
+    auto drain = [&](int rc) {
+        cudaStreamSynchronize(s);
+        return rc;
+    };
+    for (int g = 0; g < n_groups; g++) {
+        const camp_group &gr = groups[g];
+        const Part &p = part[g];
+        const size_t C = (size_t)gr.n_cells;
+        dg[g] = gr;
+        dg[g].state = (double *)(base + p.state);
+        dg[g].env = (const double *)(base + p.env);
+        dg[g].atol = (const double *)(base + p.atol);
+        dg[g].status = (int32_t *)(base + p.status);
+        dg[g].stats = gr.stats ? (int32_t *)(base + p.stats) : nullptr;
+        dg[g].step = gr.step ? (double *)(base + p.step) : nullptr;
+        dg[g].workspace = base + p.ws;
+        if (C == 0) continue;
+        cudaError_t e = cudaMemcpyAsync(dg[g].state, gr.state, C * gr.mech->h.n * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((void *)dg[g].env, gr.env, C * gr.mech->h.n_env * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((void *)dg[g].atol, gr.atol, (size_t)gr.atol_len * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && gr.step) e = cudaMemcpyAsync(dg[g].step, gr.step, C * 8, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess)
+            return drain(fail(CAMP_E_CUDA, std::string("staging copy: ") + cudaGetErrorString(e)));
+    }
+    int rc = camp_solve_batch(dg, n_groups, dt, rtol, opts, stream);
+    if (rc != CAMP_OK) return drain(rc);
+    for (int g = 0; g < n_groups; g++) {
+        const camp_group &gr = groups[g];
+        const size_t C = (size_t)gr.n_cells;
+        if (C == 0) continue;
+        cudaError_t e = cudaMemcpyAsync(gr.state, dg[g].state, C * gr.mech->h.n * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(gr.status, dg[g].status, C * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && gr.stats)
+            e = cudaMemcpyAsync(gr.stats, dg[g].stats, C * 4 * CAMP_NSTATS, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && gr.step) e = cudaMemcpyAsync(gr.step, dg[g].step, C * 8, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return drain(fail(CAMP_E_CUDA, std::string("result copy: ") + cudaGetErrorString(e)));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
     return CAMP_OK;
 }
 

@@ -923,6 +923,8 @@ static void build_tables(HostMech &h) {
         for (int m2 = 3; m2 < 6; m2++) nb += h.rfac[(size_t)k * 6 + m2] >= 0;
         h.flops_forcing += nf + (h.procs[k].reversible() ? nb + 1 : 0);
     }
+    h.model_forcing = 0;
+    for (const auto &p : h.procs) h.model_forcing += 2LL * (long long)p.react.size() + (long long)p.prod.size();
     h.flops_jacobian = 2LL * (long long)h.colidx.size();
     for (size_t e = 0; e < h.jk.size(); e++)
         h.flops_jacobian += 2 + (h.jo[2 * e] >= 0) + (h.jo[2 * e + 1] >= 0);

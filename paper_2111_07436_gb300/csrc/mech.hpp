@@ -74,6 +74,7 @@ struct HostMech {
     long long flops_jacobian = 0;  // one J assembly into I - gamma J
     long long flops_factor = 0;    // one sparse LU factorisation (2 per update + divisions)
     long long flops_solve = 0;     // one pair of triangular solves
+    long long model_forcing = 0;   // sum over processes of 2 |reactants| + |products|
 };
 
 // Throws std::runtime_error with a message on malformed input.

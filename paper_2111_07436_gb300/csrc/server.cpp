@@ -8,7 +8,9 @@
 // each chunk on its own stream (copy in, solve, copy out), and retires
 // chunks as their completion events fire, so admitted chunks overlap on the
 // device and memory is recycled continuously.  Mechanism tables stay resident
-// on the device for the server's life.
+// on the device for the server's life, and so, for resident cell sets, does a
+// chunk's state across the host's consecutive steps: a step of such a set
+// moves only its env in (and, optionally, its status out).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,6 +25,19 @@
 
 #include "camp.h"
 #include "launch.h"
+
+struct camp_resident {
+    const camp_mech *mech = nullptr;
+    int64_t n_cells = 0;
+    int n = 0, n_env = 0;
+    bool warm = false;
+    size_t bytes = 0;
+    void *dev = nullptr;
+    double *d_state = nullptr, *d_env = nullptr, *d_step = nullptr, *d_atol = nullptr;
+    int32_t *d_status = nullptr;
+    cudaEvent_t last = nullptr;  // the latest enqueued operation on the set's memory
+    int queued = 0;              // steps submitted and not yet finished (server lock)
+};
 
 namespace {
 
@@ -42,6 +57,7 @@ struct Request {
     camp_solve_opts opts{};
     size_t bytes = 0;
     int n = 0, n_env = 0;
+    camp_resident *res = nullptr;  // a step of a resident set (state stays on the device)
     // progress
     int slot = -1;
     void *dev = nullptr;
@@ -57,6 +73,8 @@ struct camp_server {
     size_t used = 0;
     int device = 0;
     std::vector<cudaStream_t> streams;
+    cudaStream_t res_stream = nullptr;  // creation, reads and writes of resident sets
+    std::vector<camp_resident *> residents;
     std::vector<void *> workspaces;
     std::vector<char> slot_busy;
     std::deque<Request *> pending;
@@ -76,7 +94,35 @@ struct camp_server {
                al((size_t)r.n_cells * 4) + 256;
     }
 
+    // a step of a resident set: wait for the set's previous operation, copy
+    // env (and atol) in, solve in place, optionally copy the status out
+    void issue_resident(Request *r) {
+        CampRange range_("camp_server: step a resident set");
+        cudaStream_t s = streams[r->slot];
+        camp_resident *R = r->res;
+        cudaError_t e = cudaStreamWaitEvent(s, R->last, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(R->d_env, r->env, (size_t)r->n_cells * r->n_env * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(R->d_atol, &r->atol, 8, cudaMemcpyHostToDevice, s);
+        int rc = CAMP_OK;
+        if (e == cudaSuccess) {
+            camp_solve_opts o = r->opts;
+            o.workspace = workspaces[r->slot];
+            o.stats = nullptr;
+            o.step = R->warm ? R->d_step : nullptr;
+            rc = camp_solve(r->mech, r->n_cells, R->d_state, R->d_env, r->dt, r->rtol, R->d_atol, 1, R->d_status,
+                            &o, s);
+        }
+        if (e == cudaSuccess && rc == CAMP_OK && r->status)
+            e = cudaMemcpyAsync(r->status, R->d_status, (size_t)r->n_cells * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(R->last, s);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(r->done_ev, s);
+        r->info.rc = (e != cudaSuccess) ? CAMP_E_CUDA : rc;
+    }
+
     void issue(Request *r) {
+        if (r->res) return issue_resident(r);
         CampRange range_("camp_server: stage and launch a chunk");
         cudaStream_t s = streams[r->slot];
         const size_t bs = (size_t)r->n_cells * r->n * 8, be = (size_t)r->n_cells * r->n_env * 8;
@@ -149,6 +195,7 @@ struct camp_server {
                 r->info.t_done = now_s() - t0;
                 r->finished = true;
                 used -= r->bytes;
+                if (r->res) r->res->queued--;
                 slot_busy[r->slot] = 0;
                 inflight[i] = inflight.back();
                 inflight.pop_back();
@@ -175,6 +222,10 @@ int camp_server_create(const camp_server_opts *o, camp_server **out) {
     s->budget = o->hbm_budget_bytes;
     int slots = o->max_inflight > 0 ? o->max_inflight : 8;
     if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return CAMP_E_CUDA; }
+    if (cudaStreamCreateWithFlags(&s->res_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        return CAMP_E_CUDA;
+    }
     for (int i = 0; i < slots; i++) {
         cudaStream_t st;
         void *ws = nullptr;
@@ -182,6 +233,7 @@ int camp_server_create(const camp_server_opts *o, camp_server **out) {
             cudaMalloc(&ws, camp_workspace_bytes()) != cudaSuccess) {
             for (auto x : s->streams) cudaStreamDestroy(x);
             for (auto w : s->workspaces) cudaFree(w);
+            cudaStreamDestroy(s->res_stream);
             delete s;
             return CAMP_E_CUDA;
         }
@@ -279,6 +331,7 @@ int camp_server_cancel(camp_server *s, uint64_t id) {
         auto pos = std::find(s->pending.begin(), s->pending.end(), r);
         if (pos == s->pending.end()) return CAMP_E_UNSUPPORTED;  // admitted or finished
         s->pending.erase(pos);
+        if (r->res) r->res->queued--;
         r->info.rc = CAMP_E_CANCELLED;
         r->info.t_admit = r->info.t_done = now_s() - s->t0;
         r->finished = true;
@@ -311,8 +364,181 @@ int camp_server_destroy(camp_server *s) {
     }
     for (auto w : s->workspaces) cudaFree(w);
     for (auto &kv : s->all) delete kv.second;
+    for (camp_resident *R : s->residents) {
+        cudaStreamWaitEvent(s->res_stream, R->last, 0);
+        cudaFreeAsync(R->dev, s->res_stream);
+        cudaStreamSynchronize(s->res_stream);
+        cudaEventDestroy(R->last);
+        delete R;
+    }
+    cudaStreamDestroy(s->res_stream);
     delete s;
     return CAMP_OK;
+}
+
+// ---- resident cell sets ------------------------------------------------------
+static int resident_wait_idle(camp_server *s, camp_resident *r, int32_t timeout_ms,
+                              std::unique_lock<std::mutex> &lk) {
+    auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    while (r->queued > 0) {
+        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && r->queued > 0) return CAMP_E_TIMEOUT;
+    }
+    return CAMP_OK;
+}
+
+static bool known_resident(camp_server *s, camp_resident *r) {
+    return std::find(s->residents.begin(), s->residents.end(), r) != s->residents.end();
+}
+
+int camp_server_resident_create(camp_server *s, const camp_mech *m, int64_t n_cells, const double *state,
+                                int32_t warm_start, camp_resident **out) {
+    if (!s || !m || n_cells <= 0 || !state || !out) return CAMP_E_INVAL;
+    *out = nullptr;
+    camp_mech_info inf;
+    if (camp_mech_info_get(m, &inf) != CAMP_OK) return CAMP_E_INVAL;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t C = (size_t)n_cells;
+    const size_t b_state = al(C * inf.n_species * 8), b_env = al(C * inf.n_env * 8), b_st = al(C * 4);
+    const size_t b_step = warm_start ? al(C * 8) : 0;
+    camp_resident *R = new camp_resident();
+    R->mech = m;
+    R->n_cells = n_cells;
+    R->n = inf.n_species;
+    R->n_env = inf.n_env;
+    R->warm = warm_start != 0;
+    R->bytes = b_state + b_env + b_st + b_step + 256;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) { delete R; return CAMP_E_INVAL; }
+        if (s->used + R->bytes > s->budget) { delete R; return CAMP_E_BUDGET; }
+        s->used += R->bytes;
+    }
+    cudaStream_t st = s->res_stream;
+    cudaError_t e = cudaMallocAsync(&R->dev, R->bytes, st);
+    if (e == cudaSuccess) {
+        char *base = (char *)R->dev;
+        R->d_state = (double *)base;
+        R->d_env = (double *)(base + b_state);
+        R->d_status = (int32_t *)(base + b_state + b_env);
+        R->d_step = warm_start ? (double *)(base + b_state + b_env + b_st) : nullptr;
+        R->d_atol = (double *)(base + b_state + b_env + b_st + b_step);
+        e = cudaMemcpyAsync(R->d_state, state, C * inf.n_species * 8, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(R->d_status, 0, C * 4, st);
+    if (e == cudaSuccess && R->d_step) e = cudaMemsetAsync(R->d_step, 0, C * 8, st);  // the first step starts cold
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&R->last, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(R->last, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        if (R->dev) {
+            cudaFreeAsync(R->dev, st);
+            cudaStreamSynchronize(st);
+        }
+        if (R->last) cudaEventDestroy(R->last);
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->used -= R->bytes;
+        delete R;
+        return e == cudaErrorMemoryAllocation ? CAMP_E_NOMEM : CAMP_E_CUDA;
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->residents.push_back(R);
+    }
+    *out = R;
+    return CAMP_OK;
+}
+
+int camp_server_resident_step(camp_server *s, camp_resident *R, const double *env, double dt, double rtol,
+                              double atol, int32_t *status, const camp_solve_opts *opts, uint64_t *req_id) {
+    if (!s || !R || !env || !req_id) return CAMP_E_INVAL;
+    if (!(dt > 0.0) || !(rtol > 0.0) || !(atol > 0.0)) return CAMP_E_INVAL;
+    Request *r = new Request();
+    r->mech = R->mech;
+    r->n_cells = R->n_cells;
+    r->env = env;
+    r->status = status;
+    r->dt = dt;
+    r->rtol = rtol;
+    r->atol = atol;
+    r->n = R->n;
+    r->n_env = R->n_env;
+    r->res = R;
+    camp_solve_opts_default(&r->opts, opts ? opts->variant : CAMP_VARIANT_MIXED);
+    if (opts) r->opts = *opts;
+    r->bytes = 0;  // the set's memory is already counted
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop || !known_resident(s, R)) { delete r; return CAMP_E_INVAL; }
+        r->id = s->next_id++;
+        r->info.n_cells = R->n_cells;
+        r->info.t_submit = now_s() - s->t0;
+        r->info.rc = CAMP_OK;
+        s->all[r->id] = r;
+        s->pending.push_back(r);
+        R->queued++;
+        *req_id = r->id;
+    }
+    s->cv_work.notify_one();
+    return CAMP_OK;
+}
+
+int camp_server_resident_read(camp_server *s, camp_resident *R, double *state, int32_t *status, double *step,
+                              int32_t timeout_ms) {
+    if (!s || !R || !state) return CAMP_E_INVAL;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        if (!known_resident(s, R)) return CAMP_E_INVAL;
+        if (int rc = resident_wait_idle(s, R, timeout_ms, lk)) return rc;
+    }
+    cudaStream_t st = s->res_stream;
+    const size_t C = (size_t)R->n_cells;
+    cudaError_t e = cudaStreamWaitEvent(st, R->last, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(state, R->d_state, C * R->n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, R->d_status, C * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && step) {
+        if (R->d_step) e = cudaMemcpyAsync(step, R->d_step, C * 8, cudaMemcpyDeviceToHost, st);
+        else std::fill(step, step + C, 0.0);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? CAMP_OK : CAMP_E_CUDA;
+}
+
+int camp_server_resident_write(camp_server *s, camp_resident *R, const double *state, int32_t timeout_ms) {
+    if (!s || !R || !state) return CAMP_E_INVAL;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        if (!known_resident(s, R)) return CAMP_E_INVAL;
+        if (int rc = resident_wait_idle(s, R, timeout_ms, lk)) return rc;
+    }
+    cudaStream_t st = s->res_stream;
+    cudaError_t e = cudaStreamWaitEvent(st, R->last, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(R->d_state, state, (size_t)R->n_cells * R->n * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(R->last, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? CAMP_OK : CAMP_E_CUDA;
+}
+
+int camp_server_resident_destroy(camp_server *s, camp_resident *R) {
+    if (!s || !R) return CAMP_E_INVAL;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        if (!known_resident(s, R)) return CAMP_E_INVAL;
+        while (R->queued > 0) s->cv_done.wait(lk);
+        s->residents.erase(std::find(s->residents.begin(), s->residents.end(), R));
+    }
+    cudaStream_t st = s->res_stream;
+    cudaStreamWaitEvent(st, R->last, 0);
+    cudaFreeAsync(R->dev, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaEventDestroy(R->last);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->used -= R->bytes;
+    }
+    s->cv_work.notify_one();  // freed budget may admit a waiting chunk
+    delete R;
+    return e == cudaSuccess ? CAMP_OK : CAMP_E_CUDA;
 }
 
 }  // extern "C"

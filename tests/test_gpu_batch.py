@@ -56,6 +56,29 @@ def test_batch_equals_separate_solves_and_the_oracle(groups):
         parity.check(om, g["y0"][idx], g["env_np"][idx], 180.0, 1e-4, 1e-5, yb[idx], yo)
 
 
+def test_host_buffer_batch_equals_device_batch(groups):
+    """camp_solve_batch_host (host arrays in and out, one synchronous call)
+    gives the device-pointer batch's results bit for bit, stats included."""
+    import torch
+    _reset(groups)
+    stats = [torch.zeros((len(g["y0"]), camp.NSTATS), dtype=torch.int32, device="cuda") for g in groups]
+    args = _args(groups)
+    for a_, s in zip(args, stats):
+        a_["stats"] = s
+    camp.solve_batch(args, 180.0, 1e-4)
+    torch.cuda.synchronize()
+    ref = [(g["state"].cpu().numpy(), g["status"].cpu().numpy(), s.cpu().numpy()) for g, s in zip(groups, stats)]
+    for rep in range(2):  # the second call reuses the library's staging buffer
+        host = [{"mech": g["mech"], "state": g["y0"].copy(), "env": g["env_np"], "atol": 1e-5,
+                 "status": np.full(len(g["y0"]), -1, dtype=np.int32),
+                 "stats": np.zeros((len(g["y0"]), camp.NSTATS), dtype=np.int32)} for g in groups]
+        camp.solve_batch_host(host, 180.0, 1e-4)
+        for h, (y, st, sts) in zip(host, ref):
+            assert np.array_equal(h["state"], y)
+            assert np.array_equal(h["status"], st)
+            assert np.array_equal(h["stats"], sts)
+
+
 def test_cloud_cells_take_more_steps(groups):
     import torch
     _reset(groups)
@@ -115,7 +138,9 @@ def test_full_size_uneven_batch_sampled(cuda):
     benchmark's seeds) in the launch configuration the benchmark times:
     autotuned, both mechanisms in one camp_solve_batch call captured in a
     CUDA graph; then the plain FP64 form, one static launch per mechanism.
-    A seeded sample of each group is re-solved by the oracle."""
+    A stratified sample of 4096 cells (by mechanism and dark / lit, in
+    proportion) is re-solved by the oracle; every sampled cell is under the
+    parity rule and the arbiter."""
     import torch
     gs, _ = w.uneven_batch(131072)
     G = []
@@ -152,14 +177,16 @@ def test_full_size_uneven_batch_sampled(cuda):
                         variant=camp.VARIANT_FP64, persistent=False)
     torch.cuda.synchronize()
     plain = [(g["state"].cpu().numpy(), g["status"].cpu().numpy()) for g in G]
+    sample = w.stratified_sample(gs, 4096)
     for gi, g in enumerate(G):
         assert (mixed[gi][1] == 0).all() and (plain[gi][1] == 0).all()
-        idx = np.sort(np.random.default_rng(7 + gi).choice(len(g["y0"]), 20, replace=False))
+        idx = sample[gi]
         om = oracle.Mechanism(json.dumps(g["mj"]))
         yo, so, _ = om.solve(g["y0"][idx], g["env_np"][idx], 180.0, 1e-4, 1e-5)
         assert (so == 0).all()
-        for y_gpu, _ in (mixed[gi], plain[gi]):
-            parity.check(om, g["y0"][idx], g["env_np"][idx], 180.0, 1e-4, 1e-5, y_gpu[idx], yo)
+        for name, (y_gpu, _) in (("mixed", mixed[gi]), ("fp64", plain[gi])):
+            stats = parity.check(om, g["y0"][idx], g["env_np"][idx], 180.0, 1e-4, 1e-5, y_gpu[idx], yo)
+            print(f"group {gi} ({len(idx)} sampled cells) {name}: {stats}")
 
 
 def test_batch_with_a_water_parameter_mechanism(cuda):
