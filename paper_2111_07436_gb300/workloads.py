@@ -558,6 +558,37 @@ def uneven_batch(n_cells=131072, seed=204, cloud_fraction=0.1, night_fraction=0.
     return [(gas, yg, eg), (mp, ym, em)], np.flatnonzero(cloudy)
 
 
+def dark_cells(mech, env):
+    """Boolean [cells]: cells whose photolysis rates are all zero (night,
+    or the sun below the horizon)."""
+    lay = layout(mech)
+    ks = [2 + k for k, kind in enumerate(lay.runtime_kind) if kind == "PHOTOLYSIS"]
+    return (env[:, ks] == 0.0).all(axis=1) if ks else np.zeros(len(env), dtype=bool)
+
+
+def stratified_sample(groups, n, seed=17):
+    """A seeded random sample of about n cells of an uneven batch (the
+    [(mechanism, y0, env), ...] of uneven_batch), stratified by group and by
+    dark / lit cells, each stratum's share in proportion to its size (at
+    least one cell of every non-empty stratum).  Returns one sorted index
+    array per group; a timing over group g's sample extrapolates to the
+    whole group by len(group) / len(sample)."""
+    rng = np.random.default_rng(seed)
+    total = sum(len(y) for _, y, _ in groups)
+    out = []
+    for mj, y, env in groups:
+        dark = dark_cells(mj, env)
+        picks = []
+        for mask in (dark, ~dark):
+            idx = np.flatnonzero(mask)
+            if len(idx) == 0:
+                continue
+            k = min(len(idx), max(1, int(round(n * len(idx) / total))))
+            picks.append(rng.choice(idx, k, replace=False))
+        out.append(np.sort(np.concatenate(picks)) if picks else np.zeros(0, dtype=np.int64))
+    return out
+
+
 def serving_requests(n_requests=2000, seed=205, gas_share=0.7, cells_lo=256, cells_hi=65536,
                      dt_lo=60.0, dt_hi=600.0):
     """A stream of chunk requests: size log-uniform in [cells_lo, cells_hi],

@@ -1,7 +1,7 @@
 """Whole solves on the GPU against the oracle, through the C ABI, for both
 forms (plain FP64; mixed FP32 J/LU with FP64 state and error test), static
 and persistent mappings, at small sizes in full and at the benchmark sizes on
-sampled cells; plus the edge cases of the method.  Parity rule and arbiter:
+every cell; plus the edge cases of the method.  Parity rule and arbiter:
 tests/parity.py."""
 import json
 
@@ -52,6 +52,41 @@ def test_small_mechanism_one_hour(mechs, form):
 
 
 @pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
+def test_outer_steps_in_one_launch_equal_separate_launches(mechs, form):
+    """camp_solve_sequence: the small mechanism's 60 outer steps in one
+    launch write, after every step, the state 60 separate launches give (bit
+    for bit); the same for 64 cells of the 72-species mechanism over three
+    steps; a cell that fails stops there with its status."""
+    import torch
+    for k, C, n_steps in ((1, 1, 60), (2, 64, 3)):
+        wl, gm, om = mechs[k]
+        y0, env = wl.inputs(C)
+        ty = torch.tensor(y0, device="cuda")
+        traj = torch.zeros((n_steps, C, gm.n), dtype=torch.float64, device="cuda")
+        st = gm.solve_sequence(ty, torch.tensor(env, device="cuda"), wl.dt, n_steps, wl.rtol, wl.atol,
+                               trajectory=traj, variant=form[0], persistent=form[1])
+        torch.cuda.synchronize()
+        assert (st.cpu().numpy() == 0).all()
+        traj = traj.cpu().numpy()
+        yg = y0.copy()
+        for j in range(n_steps):
+            yg, stj = _gpu_solve(gm, yg, env, wl.dt, wl.rtol, wl.atol, *form)
+            assert (stj == 0).all()
+            assert np.array_equal(traj[j], yg)
+        assert np.array_equal(ty.cpu().numpy(), yg)
+    # a step budget too small for the first step: status 1, nothing written
+    wl, gm, om = mechs[2]
+    y0, env = wl.inputs(4)
+    ty = torch.tensor(y0, device="cuda")
+    traj = torch.full((3, 4, gm.n), -1.0, dtype=torch.float64, device="cuda")
+    status = gm.solve_sequence(ty, torch.tensor(env, device="cuda"), wl.dt, 3, wl.rtol, wl.atol, trajectory=traj,
+                               variant=form[0], persistent=form[1], max_steps=3)
+    torch.cuda.synchronize()
+    assert (status.cpu().numpy() == 1).all()
+    assert np.array_equal(ty.cpu().numpy(), y0) and (traj.cpu().numpy() == -1.0).all()
+
+
+@pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
 @pytest.mark.parametrize("k,C", [(2, 301), (3, 67)])
 def test_full_parity_small_batches(mechs, form, k, C):
     wl, gm, om = mechs[k]
@@ -62,19 +97,32 @@ def test_full_parity_small_batches(mechs, form, k, C):
     parity.check(om, y0, env, wl.dt, wl.rtol, wl.atol, yg, yo)
 
 
+@pytest.fixture(scope="module")
+def full_oracle(mechs):
+    """The oracle's results on every cell of the 72- and 232-species
+    workloads at their full sizes (16384 and 4096 cells), computed once."""
+    out = {}
+    for k in (2, 3):
+        wl, gm, om = mechs[k]
+        y0, env = wl.inputs()
+        yo, so, _ = om.solve(y0, env, wl.dt, wl.rtol, wl.atol)
+        assert (so == 0).all()
+        out[k] = (y0, env, yo)
+    return out
+
+
 @pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
-@pytest.mark.parametrize("k,sample", [(2, 96), (3, 24)])
-def test_benchmark_size_sampled(mechs, form, k, sample):
-    """The full workload in one launch; a seeded sample of cells re-solved by
-    the oracle one by one."""
+@pytest.mark.parametrize("k", [2, 3])
+def test_every_cell_at_full_size(mechs, full_oracle, form, k):
+    """The full workload in one launch (16384 cells of the 72-species
+    mechanism, 4096 of the 232-species one), every cell under the parity
+    rule, every violating cell through the arbiter."""
     wl, gm, om = mechs[k]
-    y0, env = wl.inputs()
+    y0, env, yo = full_oracle[k]
     yg, st = _gpu_solve(gm, y0, env, wl.dt, wl.rtol, wl.atol, *form)
     assert (st == 0).all()
-    idx = np.sort(np.random.default_rng(k).choice(wl.n_cells, sample, replace=False))
-    yo, sto, _ = om.solve(y0[idx], env[idx], wl.dt, wl.rtol, wl.atol)
-    assert (sto == 0).all()
-    parity.check(om, y0[idx], env[idx], wl.dt, wl.rtol, wl.atol, yg[idx], yo)
+    stats = parity.check(om, y0, env, wl.dt, wl.rtol, wl.atol, yg, yo)
+    print(f"workload {k} {form}: {stats}")
 
 
 def test_results_do_not_depend_on_batch_or_mapping(mechs):
@@ -149,19 +197,31 @@ def test_host_entry_point_matches_device_entry_point(mechs):
     assert np.array_equal(yh, yd) and np.array_equal(sth, std)
 
 
-def test_stats_are_close_to_the_oracle(mechs):
+@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("variant,share", [(camp.VARIANT_FP64, 0.99), (camp.VARIANT_MIXED, 0.98)],
+                         ids=["fp64", "mixed"])
+def test_forms_take_the_oracles_step_sequence(mechs, full_oracle, k, variant, share):
+    """The same controller: the plain form, with the oracle's FP64
+    arithmetic, takes the oracle's step sequence (steps, Newton iterations,
+    Jacobian setups, error-test failures) on at least 99% of the cells of
+    the full workload (measured: all of them); the mixed form, whose FP32
+    iteration matrix perturbs the Newton corrections, on at least 98%
+    (measured: 99.7% and 99.8%).  The rest differ where a decision sits on a
+    tie within that perturbation."""
     import torch
-    wl, gm, om = mechs[2]
-    y0, env = wl.inputs(64)
+    wl, gm, om = mechs[k]
+    y0, env, _ = full_oracle[k]
+    C = len(y0)
     ty = torch.tensor(y0, device="cuda")
-    stats = torch.zeros((64, camp.NSTATS), dtype=torch.int32, device="cuda")
-    gm.solve(ty, torch.tensor(env, device="cuda"), wl.dt, wl.rtol, wl.atol, variant=camp.VARIANT_FP64,
-             persistent=False, stats=stats)
+    stats = torch.zeros((C, camp.NSTATS), dtype=torch.int32, device="cuda")
+    gm.solve(ty, torch.tensor(env, device="cuda"), wl.dt, wl.rtol, wl.atol, variant=variant,
+             persistent=variant == camp.VARIANT_MIXED, stats=stats)
     sg = stats.cpu().numpy()
     _, _, so = om.solve(y0, env, wl.dt, wl.rtol, wl.atol)
-    # same controller: the FP64 form takes the oracle's step sequence on most cells
-    assert np.mean(sg[:, 0] == so[:, 0]) > 0.5
-    assert abs(sg[:, 0].mean() / so[:, 0].mean() - 1) < 0.1
+    same = (sg[:, :4] == so[:, :4]).all(axis=1)
+    print(f"workload {k} variant {variant}: identical step sequence on {same.mean():.4f} of cells")
+    assert same.mean() >= share
+    assert abs(sg[:, 0].mean() / so[:, 0].mean() - 1) < 0.01
 
 
 @pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
@@ -253,21 +313,30 @@ def test_random_tiny_mechanisms(form, name):
     parity.check(om, y0[ok], env[ok], 300.0, 1e-4, 1e-5, yg[ok], yo[ok])
 
 
+@pytest.fixture(scope="module")
+def water_oracle():
+    """The oracle on every cell of the 240-species water workload, once."""
+    wl = w.workload(7)
+    om = oracle.Mechanism(wl.json())
+    y0, env = wl.inputs()
+    yo, sto, _ = om.solve(y0, env, wl.dt, wl.rtol, wl.atol)
+    assert (sto == 0).all()
+    return wl, om, y0, env, yo
+
+
 @pytest.mark.parametrize("form", FORMS, ids=FORM_IDS)
-def test_water_parameter_workload(form):
+def test_water_parameter_workload(cuda, water_oracle, form):
     """Aerosol water as a parameter of the state (Sect. 2.2.2): the
     240-species workload whose section water is held by a salt and by the
     species that Henry's-law uptake feeds.  The full workload in one launch;
-    a seeded sample of cells re-solved by the oracle."""
-    wl = w.workload(7)
-    gm, om = camp.Mechanism(wl.json()), oracle.Mechanism(wl.json())
-    y0, env = wl.inputs()
+    every cell (4096) under the parity rule and the arbiter."""
+    wl, om, y0, env, yo = water_oracle
+    gm = camp.Mechanism(wl.json())
     yg, st = _gpu_solve(gm, y0, env, wl.dt, wl.rtol, wl.atol, *form)
     assert (st == 0).all()
-    idx = np.sort(np.random.default_rng(7).choice(wl.n_cells, 48, replace=False))
-    yo, sto, _ = om.solve(y0[idx], env[idx], wl.dt, wl.rtol, wl.atol)
-    assert (sto == 0).all()
-    parity.check(om, y0[idx], env[idx], wl.dt, wl.rtol, wl.atol, yg[idx], yo)
+    stats = parity.check(om, y0, env, wl.dt, wl.rtol, wl.atol, yg, yo)
+    print(f"water workload {form}: {stats}")
+    idx = np.random.default_rng(7).choice(wl.n_cells, 48, replace=False)
     # the water follows the state
     dL = [np.max(np.abs(om.water(env[c], yg[c]) / om.water(env[c], y0[c]) - 1)) for c in idx]
     assert max(dL) > 1e-4
