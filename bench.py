@@ -1,19 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the batched chemistry solve: cell-steps/s at rtol 1e-4.
 
-One step = one call of the whole hot path (rate constants, BDF + Newton +
-sparse LU for every cell over one outer step) on the full workload, with the
-inputs resident in HBM; a fresh copy of the initial state is taken at the
-start of every step and L2 is flushed (256 MB write) between timed steps.
-Default workload: 16384 cells of the 72-species / 186-process gas mechanism,
-one 180 s step.  Prints one JSON line (rank 0).
+Default workload: uneven stiffness, 131072 cells per GPU (half dark, 10%
+cloud cells carrying eight aqueous sections on the 232-species multiphase
+mechanism, the rest on the 72-species gas mechanism), one 180 s step.  One
+bench step = one call of the whole hot path (rate constants, BDF + Newton +
+sparse LU for every cell over the outer step): both mechanisms in one
+camp_solve_batch call (a persistent grid per mechanism, autotuned launch
+shape), captured once in a CUDA graph and replayed, with the inputs resident
+in HBM; a fresh copy of the initial state is taken inside every step and L2
+is flushed (256 MB write) between timed steps.  The same line carries the
+plain FP64 form (one static launch per mechanism per step), the end-to-end
+rate through the host-buffer call, the FP64 oracle on the host cores over a
+stratified sample, the error against it with every violating cell
+arbitrated, and the roofline of the cost models.  Prints one JSON line
+(rank 0).
 
-    python bench.py [--steps K] [--warmup W] [--gpus N] [--workload gas72]
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--workload uneven]
+    python bench.py --workload gas72|multiphase232|particles|water|small|serving
     python bench.py --impl reference   # the FP64 CPU oracle on the host cores
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -28,14 +38,12 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {"small": 1, "gas72": 2, "multiphase232": 3, "uneven": 4, "serving": 5, "particles": 6,
              "water": 7}
 FP64_PEAK_NOMINAL_GFLOPS = 1250.0  # GB300 dense FP64, nominal
+HBM_FALLBACK_GBS = 6800.0          # used only when the measured peaks file is absent
 # DRAM bytes (read + write) per cell of one mixed-form k_solve launch, from
 # one ncu capture of the same kernel on a smaller launch of the same
-# workload (gas-72: 4096 cells, 4.18 MB; multiphase-232: 2048 cells,
-# 5.35 MB; particles: 512 cells, 5.91 MB; water: 2048 cells, 5.56 MB): the
-# inputs only, so traffic scales with the cells.  To be taken again
-# whenever the kernel changes.
-DRAM_BYTES_PER_CELL = {"gas72": 4.180480e6 / 4096, "multiphase232": 5.347840e6 / 2048,
-                       "particles": 5.905152e6 / 512, "water": 5.557248e6 / 2048}
+# workload, valid only for the kernel sources whose digest is given (the
+# bench reports null traffic once the kernels have changed since).
+DRAM_BYTES_PER_CELL = {}
 
 
 def args():
@@ -44,16 +52,36 @@ def args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="camp", choices=["camp", "reference"])
-    p.add_argument("--workload", default="gas72", choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default="uneven", choices=sorted(WORKLOADS))
     p.add_argument("--cells", type=int, default=0, help="override the workload's cell count")
     p.add_argument("--variant", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--cpb", type=int, default=0, help="cells per block (0: library default)")
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--sample", type=int, default=4096, help="uneven: cells of the stratified oracle sample")
     p.add_argument("--requests", type=int, default=2000, help="serving: number of chunk requests")
     p.add_argument("--load", type=float, default=0.8, help="serving: offered load / measured capacity")
     return p.parse_args()
+
+
+def kernel_digest():
+    """Digest of the kernel sources (the DRAM traffic table is tied to it)."""
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2111_07436_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
 
 
 # ----------------------------------------------------------------- clocks
@@ -100,83 +128,418 @@ class ClockSampler:
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
-# ----------------------------------------------------------------- CPU oracle
-def oracle_rate(wl, seconds, rank_seed=0):
-    """Oracle cell-steps/s on this host's cores over a bounded sample of the
-    workload's cells (about `seconds` of work)."""
+# ----------------------------------------------------------------- error vs oracle
+def error_vs_oracle(parts, atol, rtol, truth_cells=128):
+    """GPU results against the oracle's on the sampled cells, merged over
+    mechanisms.  parts: [(oracle mechanism, y0, env, dt, y_gpu, y_oracle)].
+    Relative error over the species above atol in either (the parity rule's
+    set), the same over values above 100 atol, the difference in units of the
+    solver's tolerance rtol |y| + atol; the parity rule with every violating
+    cell sent to the two-tier arbiter (tests/parity.py); and, on a seeded
+    subset of each group, the error of both against the true solution (a
+    tight oracle run) in the solver's tolerance units."""
     import numpy as np
-    import oracle
-    om = oracle.Mechanism(wl.json())
-    y0, env = wl.inputs()
-    threads = os.cpu_count() or 1
-    probe = min(wl.n_cells, 8 * threads)
-    t = time.perf_counter()
-    om.solve(y0[:probe], env[:probe], wl.dt, wl.rtol, wl.atol, threads=threads)
-    per_cell = (time.perf_counter() - t) / probe
-    n = int(min(wl.n_cells, max(probe, seconds / max(per_cell, 1e-9))))
-    idx = np.random.default_rng(rank_seed + 17).choice(wl.n_cells, n, replace=False)
-    t = time.perf_counter()
-    y_o, st, _ = om.solve(y0[idx], env[idx], wl.dt, wl.rtol, wl.atol, threads=threads)
-    dt = time.perf_counter() - t
-    return {"value": n * wl.n_outer / dt, "unit": "cell-steps/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n} of {wl.n_cells} cells (seeded random), {wl.n_outer} outer step(s), "
-                      f"{threads} threads, {dt:.1f} s", "ok_cells": int((st == 0).sum()),
-            "_result": (idx, y_o, st)}
-
-
-def error_vs_oracle(y_gpu, sample, rtol, atol):
-    """GPU results against the oracle's on the sampled cells: relative error
-    over the species above atol in either (the parity rule's set), the same
-    over values above 100 atol, and the difference in units of the solver's
-    tolerance rtol |y| + atol over all species."""
-    import numpy as np
-    idx, y_o, st = sample
-    ok = st == 0
-    g, o = y_gpu[idx][ok], y_o[ok]
-    d = np.abs(g - o)
-    mask = np.maximum(np.abs(g), np.abs(o)) > atol
-    if not mask.any():
+    from tests import parity
+    rels, tols, big_rel, eg_t, eo_t = [], [], [], [], []
+    agg = {"cells": 0, "arbitrated": 0, "arbiter_pass_strict": 0, "arbiter_pass": 0, "failed": 0}
+    for om, y0, env, dt, g, o in parts:
+        d = np.abs(g - o)
+        mask = np.maximum(np.abs(g), np.abs(o)) > atol
+        rels.append(d[mask] / np.abs(o)[mask])
+        big = np.abs(o) > 100 * atol
+        big_rel.append(d[big] / np.abs(o)[big])
+        tols.append((d / (rtol * np.abs(o) + atol)).ravel())
+        rep = parity.arbiter_report(om, y0, env, dt, rtol, atol, g, o)
+        agg["cells"] += rep["cells"]
+        agg["arbitrated"] += rep["arbitrated"]
+        agg["arbiter_pass_strict"] += rep["arbiter_pass_strict"]
+        agg["arbiter_pass"] += rep["arbiter_pass"]
+        agg["failed"] += len(rep["failed_cells"])
+        idx = np.arange(len(g)) if len(g) <= truth_cells else \
+            np.sort(np.random.default_rng(5).choice(len(g), truth_cells, replace=False))
+        yt = parity.tight_solution(om, y0[idx], env[idx], dt)
+        eg_t.append(parity.tol_units(g[idx], yt, rtol, atol))
+        eo_t.append(parity.tol_units(o[idx], yt, rtol, atol))
+    rel, tol, br = np.concatenate(rels), np.concatenate(tols), np.concatenate(big_rel)
+    if rel.size == 0:
         return None
-    rel = d[mask] / np.abs(o)[mask]
-    big = np.abs(o) > 100 * atol
-    tol = d / (rtol * np.abs(o) + atol)
-    return {"max_rel": float(rel.max()), "p99_rel": float(np.percentile(rel, 99)),
+    egt, eot = np.concatenate(eg_t), np.concatenate(eo_t)
+    return {"cells": agg["cells"], "max_rel": float(rel.max()), "p99_rel": float(np.percentile(rel, 99)),
             "median_rel": float(np.median(rel)), "values": int(rel.size),
-            "max_rel_above_100atol": float((d[big] / np.abs(o)[big]).max()) if big.any() else None,
-            "max_in_tol_units": float(tol.max()), "p99_in_tol_units": float(np.percentile(tol, 99))}
+            "max_rel_above_100atol": float(br.max()) if br.size else None,
+            "max_in_tol_units": float(tol.max()), "p99_in_tol_units": float(np.percentile(tol, 99)),
+            "arbitrated": agg["arbitrated"], "arbitrated_share": agg["arbitrated"] / max(1, agg["cells"]),
+            "arbiter_pass_strict": agg["arbiter_pass_strict"], "arbiter_pass": agg["arbiter_pass"],
+            "arbiter_failed": agg["failed"], "all_pass": agg["failed"] == 0,
+            "vs_truth": {"cells": int(len(egt)), "unit": "max over species of |y - y_true| / (rtol |y_true| + atol)",
+                         "gpu_p99": float(np.percentile(egt, 99)), "gpu_max": float(egt.max()),
+                         "oracle_p99": float(np.percentile(eot, 99)), "oracle_max": float(eot.max())}}
+
+
+# ----------------------------------------------------------------- cost models
+def cost_models(info, st, lu_bytes, calls=1):
+    """Algorithmic work of one solve from its per-cell counters st [C, 5]
+    (steps, Newton iterations, setups, error-test failures, order sum):
+    FP64 flops and bytes of the per-internal-step cost model
+      flops = m F + (q+1)^2 n / 2 + 10 n,
+      bytes = 16 (q+1) n + m (24 n + b nnzLU) + rho (2 b nnzLU + 8 R) + 24 n,
+    (m Newton iterations and rho setups per step, q the mean order, F the
+    per-process forcing count, b the LU element size), and the FP64 flops the
+    kernel's own steps count (f evaluations, Newton updates, Nordsieck
+    prediction and correction, norms)."""
+    import numpy as np
+    st = np.asarray(st, dtype=np.float64)
+    C = len(st)
+    steps, newton, jac, ordsum = st[:, 0].sum(), st[:, 1].sum(), st[:, 2].sum(), st[:, 4].sum()
+    s = max(steps, 1.0)
+    m, rho, q = newton / s, jac / s, ordsum / s
+    n, nnz, R = info.n_species, info.nnz_lu, info.n_rxn
+    model_flops = steps * (m * info.model_forcing + (q + 1) ** 2 * n / 2 + 10 * n)
+    model_bytes = steps * (16 * (q + 1) * n + m * (24 * n + lu_bytes * nnz) + rho * (2 * lu_bytes * nnz + 8 * R)
+                           + 24 * n)
+    f_evals = newton + 2 * C * calls  # Newton iterations plus the two of each call's starting step
+    counted = f_evals * info.flops_forcing + newton * 8 * n + steps * (q * (q + 1) / 2 + 2 * (q + 1) + 8) * n
+    lu = jac * (info.flops_jacobian + info.flops_factor) + newton * info.flops_solve
+    return {"steps": steps, "newton": newton, "setups": jac, "mean_order": q, "model_flops": model_flops,
+            "model_bytes": model_bytes, "counted_fp64": counted, "lu_flops": lu}
+
+
+def roofline(models, seconds, peak64, lu_dtype, traffic, kernel, per):
+    """The roofline object of the bench line: bound by the FP64 pipe
+    (achieved = cost-model FP64 flops / time against the measured FP64 FMA
+    rate), with the bytes model against the HBM peak beside it."""
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    fl = sum(x["model_flops"] for x in models)
+    by = sum(x["model_bytes"] for x in models)
+    counted = sum(x["counted_fp64"] for x in models)
+    lu = sum(x["lu_flops"] for x in models)
+    ach = fl / seconds / 1e9
+    return {"bound": "alu", "unit": "GFLOP/s (fp64)", "achieved": ach, "peak": peak64,
+            "peak_source": "measured FP64 FMA chains on this GPU (camp_probe_fma_rate)",
+            "frac": ach / peak64, "frac_of_nominal": ach / FP64_PEAK_NOMINAL_GFLOPS,
+            "traffic": traffic, "traffic_unit": "DRAM bytes (read + write) per launch, from ncu",
+            "kernel": kernel, "per": per,
+            "model": "FP64 flops per internal cell-step m F + (q+1)^2 n/2 + 10 n",
+            "fp64_flops_per_launch": fl,
+            "hbm_model": {"bytes_per_launch": by, "achieved_gbs": by / seconds / 1e9, "peak_gbs": hbm,
+                          "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
+                          else "fallback 6800 GB/s", "frac": by / seconds / 1e9 / hbm,
+                          "model": "bytes per internal cell-step 16 (q+1) n + m (24 n + b nnzLU) "
+                                   "+ rho (2 b nnzLU + 8 R) + 24 n"},
+            "fp64_counted": {"flops_per_launch": counted, "achieved": counted / seconds / 1e9,
+                             "frac": counted / seconds / 1e9 / peak64,
+                             "what": "the kernel's own FP64 steps: f evaluations, Newton updates, "
+                                     "Nordsieck prediction and correction, norms"},
+            "lu_flops_per_launch": lu, "lu_dtype": lu_dtype}
+
+
+# ----------------------------------------------------------------- oracle timing
+def oracle_sample_rate(groups, sample, dt, rtol, atol, threads):
+    """Oracle cell-steps/s over a per-group sample, extrapolated group by
+    group (a group's time scales by its cells over its sampled cells).
+    Returns (rate, per-group (oracle mechanism, y0, env, y_oracle), seconds)."""
+    import oracle
+    total, wall, res = 0.0, 0.0, []
+    for (mj, y, env), idx in zip(groups, sample):
+        om = oracle.Mechanism(json.dumps(mj))
+        t = time.perf_counter()
+        yo, so, _ = om.solve(y[idx], env[idx], dt, rtol, atol, threads=threads)
+        el = time.perf_counter() - t
+        wall += el
+        total += el * len(y) / max(1, len(idx))
+        res.append((om, y[idx], env[idx], yo, so))
+    n = sum(len(y) for _, y, _ in groups)
+    return n / total, res, wall
+
+
+def uneven_config(n_cells, groups, cloud_idx, gpus):
+    from paper_2111_07436_gb300 import workloads as w
+    return {"workload": f"uneven stiffness (config 4): {n_cells} cells per GPU, 50% dark, {len(cloud_idx)} "
+                        "cloud cells (liquid water 0.1-1 g/m3) on the multiphase-232 mechanism, the rest on "
+                        "gas-72, random order, dt 180 s",
+            "cells_per_gpu": n_cells, "groups": [int(len(y)) for _, y, _ in groups],
+            "species": [len(w.layout(mj).species) for mj, _, _ in groups],
+            "dt_s": 180.0, "rtol": 1e-4, "atol_ppb": 1e-5,
+            "parallelism": f"replicas x{gpus} (cells split, no collective)",
+            "l2": "flushed between timed steps (256 MB write)"}
 
 
 # ----------------------------------------------------------------- main
 def main():
     a = args()
-    if a.workload == "uneven" and a.impl == "camp":
+    if a.workload == "uneven":
         return bench_uneven(a)
     if a.workload == "serving" and a.impl == "camp":
         return bench_serving(a)
-    from paper_2111_07436_gb300 import workloads as w
+    return bench_single(a)
+
+
+def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def bench_uneven(a):
+    """Config 4: 131072 cells of uneven stiffness per GPU; both mechanisms in
+    one camp_solve_batch call replayed from a CUDA graph, with the autotuned
+    launch shapes; against the plain FP64 form, one static launch per
+    mechanism per step."""
+    import numpy as np
+    from paper_2111_07436_gb300 import replicas, workloads as w
+    rank, world, local = _dist()
+    n_cells = a.cells or 131072
+    dt, rtol, atol = 180.0, 1e-4, 1e-5
+    groups, cloud_idx = w.uneven_batch(n_cells, seed=replicas.cell_seed(204, rank))
+    config = uneven_config(n_cells, groups, cloud_idx, a.gpus)
+    metric = f"cell-steps/s at rtol {rtol:g}"
+    threads = os.cpu_count() or 1
+
+    if a.impl == "reference":  # the FP64 oracle on the host cores, rank 0 only
+        if rank != 0:
+            return
+        sample = w.stratified_sample(groups, a.sample)
+        vals, wall = [], 0.0
+        for _ in range(a.warmup + a.steps):
+            v, _, el = oracle_sample_rate(groups, sample, dt, rtol, atol, threads)
+            vals.append(v)
+            wall = el
+        v = statistics.mean(vals[a.warmup:])
+        cpu = {"value": v, "unit": "cell-steps/s", "cores": threads, "kind": "oracle",
+               "sample": f"stratified {sum(len(s) for s in sample)} of {n_cells} cells (by mechanism and "
+                         f"dark/lit, in proportion), each group's time extrapolated to all its cells; "
+                         f"{threads} threads, {wall:.1f} s per step"}
+        print(json.dumps({"impl": "reference", "metric": metric, "value": v, "unit": "cell-steps/s",
+                          "n_gpus": 0, "steps": a.steps, "warmup": a.warmup,
+                          "ms_per_step": 1e3 * n_cells / v, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                          "cpu_baseline": cpu,
+                          "e2e": {"value": v, "unit": "cell-steps/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+    from paper_2111_07436_gb300 import build, camp
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    G = _groups_on_device(groups, dev)
+    tuned = []
+    for g in G:  # autotune on a 4096-cell sample of each group
+        k = min(4096, g["y0"].shape[0])
+        tuned.append(g["mech"].autotune(g["y0"][:k].contiguous(), g["env"][:k].contiguous(), dt, rtol,
+                                        g["atol"]))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    side = torch.cuda.Stream()
+    keys = ("mech", "state", "env", "atol", "status", "workspace")
+
+    def step(stream, stats=False):
+        for g in G:
+            g["state"].copy_(g["y0"])
+        camp.solve_batch([dict({k: g[k] for k in keys}, stats=g["stats"] if stats else None) for g in G],
+                         dt, rtol, stream=stream)
+
+    for g in G:
+        g["stats"] = torch.zeros((g["y0"].shape[0], camp.NSTATS), dtype=torch.int32, device=dev)
+    with torch.cuda.stream(side):  # first call creates the fork streams outside capture
+        step(side, stats=True)     # and counts the algorithmic work (untimed)
+    torch.cuda.synchronize()
+    counters = [g["stats"].cpu().numpy() for g in G]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        step(side)
+    torch.cuda.synchronize()
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    times = []
+    with ClockSampler(dev.index) as clk:
+        for i in range(a.warmup + a.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            if i >= a.warmup:
+                times.append((e0, e1))
+        torch.cuda.synchronize()
+    ms_list = [e0.elapsed_time(e1) for e0, e1 in times]
+    if dist:
+        dist.barrier()
+    _, t_max, value = replicas.aggregate(n_cells * a.steps, sum(ms_list) / 1e3, dist)
+    ms = 1e3 * t_max / a.steps
+    ok = sum(int((g["status"] == 0).sum().item()) for g in G)
+    y_mixed = [g["state"].cpu().numpy() for g in G]
+
+    # plain FP64: one static launch per mechanism per step
+    plain = None
+    y_plain = None
+    if not a.no_plain:
+        pt = []
+        for i in range(1 + max(1, a.steps // 2)):
+            flush.zero_()
+            for g in G:
+                g["state"].copy_(g["y0"])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for g in G:
+                g["mech"].solve(g["state"], g["env"], dt, rtol, g["atol"], status=g["status"],
+                                variant=camp.VARIANT_FP64, persistent=False, stream=stream)
+            e1.record(stream)
+            pt.append((e0, e1))
+        torch.cuda.synchronize()
+        pms = sum(e0.elapsed_time(e1) for e0, e1 in pt[1:]) / (len(pt) - 1)
+        y_plain = [g["state"].cpu().numpy() for g in G]
+        plain = {"value": n_cells / (pms / 1e3), "ms_per_step": pms,
+                 "form": "fp64, one static launch per mechanism per step",
+                 "ok_cells": sum(int((g["status"] == 0).sum().item()) for g in G)}
+
+    # the heavier group's kernel alone: its launch duration on its stream
+    gi = int(np.argmax([c[:, 1].sum() for c in counters]))
+    g = G[gi]
+    kt = []
+    for i in range(4):
+        flush.zero_()
+        g["state"].copy_(g["y0"])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g["mech"].solve(g["state"], g["env"], dt, rtol, g["atol"], status=g["status"],
+                        variant=camp.VARIANT_MIXED, persistent=True, workspace=g["workspace"], stream=stream)
+        e1.record(stream)
+        kt.append((e0, e1))
+    torch.cuda.synchronize()
+    k_ms = sum(e0.elapsed_time(e1) for e0, e1 in kt[1:]) / (len(kt) - 1)
+
+    # end to end: the host-buffer call (pinned host arrays, copies timed)
+    e2e = None
+    if not a.no_e2e:
+        H = []
+        for (mj, y, env), g in zip(groups, G):
+            H.append({"mech": g["mech"], "y0": y, "state": torch.empty(y.shape, dtype=torch.float64).pin_memory(),
+                      "env": torch.from_numpy(env).pin_memory(), "atol": np.array([atol]),
+                      "status": torch.zeros(len(y), dtype=torch.int32).pin_memory()})
+        e2e_t = []
+        for i in range(a.warmup + a.steps):
+            for h in H:
+                h["state"].copy_(torch.from_numpy(h["y0"]))
+            t = time.perf_counter()
+            camp.solve_batch_host([{k: h[k] for k in ("mech", "state", "env", "atol", "status")} for h in H],
+                                  dt, rtol, stream=stream)
+            if i >= a.warmup:
+                e2e_t.append(time.perf_counter() - t)
+        _, _, e2e_value = replicas.aggregate(n_cells * a.steps, sum(e2e_t), dist)
+        e2e = {"value": e2e_value, "unit": "cell-steps/s",
+               "h2d_bytes_per_step": int(sum(h["state"].numel() * 8 + h["env"].numel() * 8 + 8 for h in H)),
+               "d2h_bytes_per_step": int(sum(h["state"].numel() * 8 + h["status"].numel() * 4 for h in H)),
+               "call": "camp_solve_batch_host (pinned host arrays, synchronous)",
+               "ok_cells": sum(int((h["status"] == 0).sum().item()) for h in H)}
+
+    cpu = err = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        sample = w.stratified_sample(groups, a.sample)
+        v, res, wall = oracle_sample_rate(groups, sample, dt, rtol, atol, threads)
+        cpu = {"value": v, "unit": "cell-steps/s", "cores": threads, "kind": "oracle",
+               "sample": f"stratified {sum(len(s) for s in sample)} of {n_cells} cells (by mechanism and "
+                         f"dark/lit, in proportion), each group's time extrapolated to all its cells; "
+                         f"{threads} threads, {wall:.1f} s",
+               "ok_cells": int(sum((r[4] == 0).sum() for r in res))}
+        err = {"rule": "species above atol, relative to the FP64 oracle; violating cells arbitrated against a "
+                       "tight oracle run (rtol 1e-10), strict per-species tier then error-control tier"}
+        for name, ys in (("mixed", y_mixed), ("fp64", y_plain)):
+            if ys is None:
+                continue
+            parts = [(om, y0s, envs, dt, ys[gi2][idx], yo)
+                     for gi2, ((om, y0s, envs, yo, so), idx) in enumerate(zip(res, sample))]
+            err[name] = error_vs_oracle(parts, atol, rtol)
+
+    if rank != 0:
+        return
+    peak64 = camp.probe_fma_rate(True)
+    models = [cost_models(g["mech"].info, c, 4) for g, c in zip(G, counters)]
+    digest = kernel_digest()
+    tr = DRAM_BYTES_PER_CELL.get("uneven")
+    traffic = (sum(tr["bytes_per_cell"][i] * len(y) for i, (_, y, _) in enumerate(groups))
+               if tr and tr["digest"] == digest else None)
+    roof = roofline(models, ms / 1e3, peak64, "f32", traffic, "k_solve (two launches, one per mechanism)",
+                    "step: both launches of one camp_solve_batch, CUDA events on the replay stream")
+    km = cost_models(G[gi]["mech"].info, counters[gi], 4)
+    roof["dominant_kernel"] = {
+        "kernel": f"k_solve of the {config['species'][gi]}-species group, launched alone",
+        "ms_per_launch": k_ms, "fp64_model_gflops": km["model_flops"] / k_ms / 1e6,
+        "frac": km["model_flops"] / k_ms / 1e6 / peak64,
+        "hbm_model_frac": km["model_bytes"] / k_ms / 1e6 / roof["hbm_model"]["peak_gbs"]}
+    work = {"bdf_steps": sum(x["steps"] for x in models), "newton_iters": sum(x["newton"] for x in models),
+            "lu_setups": sum(x["setups"] for x in models),
+            "per_group": [{k: x[k] for k in ("steps", "newton", "setups", "mean_order")} for x in models]}
+    out = {"metric": metric, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64 state / f32 J+LU",
+           "data": "synthetic (seeded generator shaped like the paper's gas mechanism and sectional aerosol)",
+           "config": config, "form": "mixed persistent, camp_solve_batch replayed from a CUDA graph",
+           "autotuned": [{"cells_per_block": t[0], "persistent": t[1], "ms": t[2]} for t in tuned],
+           "ok_cells": ok, "gpu_launches": 2 * a.steps, "work": work,
+           "plain_fp64": plain, "mixed_over_plain": (value / world / plain["value"]) if plain else None,
+           "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err,
+           "kernel_digest": digest, "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
+def bench_single(a):
+    """One mechanism's workload (gas72, multiphase232, particles, water,
+    small): the solve of every cell over every outer step of the workload."""
+    from paper_2111_07436_gb300 import replicas, workloads as w
+    rank, world, local = _dist()
     wl = w.workload(WORKLOADS[a.workload])
     if a.cells:
         wl.n_cells = a.cells
     metric = f"cell-steps/s at rtol {wl.rtol:g}"
     config = {"workload": f"{wl.mech['name']} x {wl.n_cells} cells, dt {wl.dt:g} s",
-              "cells_per_gpu": wl.n_cells, "species": None, "dt_s": wl.dt, "rtol": wl.rtol,
-              "atol_ppb": wl.atol, "parallelism": f"replicas x{a.gpus} (cells split, no collective)",
+              "cells_per_gpu": wl.n_cells, "species": len(w.layout(wl.mech).species),
+              "dt_s": wl.dt, "outer_steps": wl.n_outer,
+              "rtol": wl.rtol, "atol_ppb": wl.atol,
+              "parallelism": f"replicas x{a.gpus} (cells split, no collective)",
               "l2": "flushed between timed steps (256 MB write)"}
+    wl.cell_seed = replicas.cell_seed(wl.cell_seed, rank)  # each replica solves its own cells
+    threads = os.cpu_count() or 1
+
+    def oracle_rate(seconds):
+        import numpy as np
+        import oracle
+        om = oracle.Mechanism(wl.json())
+        y0, env = wl.inputs()
+        probe = min(wl.n_cells, 8 * threads)
+        t = time.perf_counter()
+        om.solve(y0[:probe], env[:probe], wl.dt, wl.rtol, wl.atol, threads=threads)
+        per_cell = (time.perf_counter() - t) / probe
+        n = int(min(wl.n_cells, max(probe, seconds / max(per_cell, 1e-9))))
+        idx = np.sort(np.random.default_rng(17).choice(wl.n_cells, n, replace=False))
+        t = time.perf_counter()
+        y_o, st, _ = om.solve(y0[idx], env[idx], wl.dt, wl.rtol, wl.atol, threads=threads)
+        el = time.perf_counter() - t
+        cpu = {"value": n * wl.n_outer / el, "unit": "cell-steps/s", "cores": threads, "kind": "oracle",
+               "sample": f"{n} of {wl.n_cells} cells (seeded random), {wl.n_outer} outer step(s), "
+                         f"{threads} threads, {el:.1f} s", "ok_cells": int((st == 0).sum())}
+        return cpu, (om, idx, y0, env, y_o, st)
 
     if a.impl == "reference":
         if rank != 0:
             return
-        cpu = oracle_rate(wl, a.cpu_seconds)
-        cpu.pop("_result")
-        steps_t = []
-        for _ in range(a.warmup + a.steps):
-            r = oracle_rate(wl, a.cpu_seconds / 2)
-            r.pop("_result")
-            steps_t.append(r["value"])
-        v = statistics.mean(steps_t[a.warmup:])
+        cpu, _ = oracle_rate(a.cpu_seconds)
+        vals = [oracle_rate(a.cpu_seconds / 2)[0]["value"] for _ in range(a.warmup + a.steps)]
+        v = statistics.mean(vals[a.warmup:])
         cpu["value"] = v
         print(json.dumps({"impl": "reference", "metric": metric, "value": v, "unit": "cell-steps/s",
                           "n_gpus": 0, "steps": a.steps, "warmup": a.warmup,
@@ -187,7 +550,6 @@ def main():
                                   "d2h_bytes_per_step": 0}}))
         return
 
-    import numpy as np
     import torch
     from paper_2111_07436_gb300 import build, camp
     if world > 1:
@@ -203,9 +565,6 @@ def main():
         dist.barrier()
     dev = torch.device("cuda", torch.cuda.current_device())
     gm = camp.Mechanism(wl.json())
-    config["species"] = gm.n
-    from paper_2111_07436_gb300 import replicas
-    wl.cell_seed = replicas.cell_seed(wl.cell_seed, rank)  # each replica solves its own cells
     y0, env = wl.inputs()
     C = wl.n_cells
     y0_d = torch.tensor(y0, device=dev)
@@ -225,109 +584,100 @@ def main():
             state.copy_(y0_d)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(wl.n_outer):  # one bench step = every outer step of the workload
+            if wl.n_outer == 1:
                 gm.solve(state, env_d, wl.dt, wl.rtol, atol, status=status, variant=var, persistent=pers,
                          cells_per_block=a.cpb, stats=stats if i == 0 else None, stream=stream)
+            else:  # one bench step = every outer step of the workload, in one launch
+                gm.solve_sequence(state, env_d, wl.dt, wl.n_outer, wl.rtol, atol, status=status, variant=var,
+                                  persistent=pers, stats=stats if i == 0 else None, stream=stream)
             e1.record(stream)
             if i >= W:
                 times.append((e0, e1))
         torch.cuda.synchronize()
         return [e0.elapsed_time(e1) for e0, e1 in times]
 
-    # algorithmic work from one instrumented (untimed) solve
+    # algorithmic work from one instrumented (untimed) solve of every outer step
     stats = torch.zeros((C, camp.NSTATS), dtype=torch.int32, device=dev)
-    run(variant, persistent, 0, 1, stats=stats)
-    st = stats.cpu().numpy().astype(np.float64)
-    ok = int((status.cpu().numpy() == 0).sum())
-    inf = gm.info
-    n = gm.n
-    steps, newton, jac, ordsum = st[:, 0].sum(), st[:, 1].sum(), st[:, 2].sum(), st[:, 4].sum()
-    qbar = ordsum / max(steps, 1)
-    f_evals = newton + 2 * C  # Newton iterations plus the two of the starting step
-    fp64 = f_evals * inf.flops_forcing + newton * 8 * n + steps * (qbar * (qbar + 1) / 2 + 2 * (qbar + 1) + 8) * n
-    lu = jac * (inf.flops_jacobian + inf.flops_factor) + newton * inf.flops_solve
-    if variant == camp.VARIANT_FP64:
-        fp64 += lu
+    state.copy_(y0_d)
+    gm.solve_sequence(state, env_d, wl.dt, wl.n_outer, wl.rtol, atol, status=status, variant=variant,
+                      persistent=persistent, stats=stats, stream=stream)
+    torch.cuda.synchronize()
+    counters = stats.cpu().numpy()
 
-    # timed region
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev.index) as clk:
         times = run(variant, persistent, a.steps, a.warmup)
+    ok = int((status.cpu().numpy() == 0).sum())
     y_main = state.cpu().numpy()  # this form's result of the last timed step
     if dist:
         dist.barrier()
     _, t_max, value = replicas.aggregate(C * wl.n_outer * a.steps, sum(times) / 1e3, dist)
     ms = 1e3 * t_max / a.steps
 
-    # plain FP64 form, one launch per outer step, for the mixed-vs-plain ratio
-    plain = None
+    plain = y_plain = None
     if not a.no_plain and variant == camp.VARIANT_MIXED:
         pt = run(camp.VARIANT_FP64, False, max(1, a.steps // 2), 1)
         y_plain = state.cpu().numpy()
         pms = sum(pt) / len(pt)
         plain = {"value": C * wl.n_outer / (pms / 1e3), "ms_per_step": pms, "form": "fp64 static grid"}
 
-    # end to end through the host-pointer C-ABI call, pinned host buffers
-    y_h = torch.empty((C, n), dtype=torch.float64).pin_memory()
-    e_h = torch.tensor(env, dtype=torch.float64).pin_memory()
-    st_h = None
-    e2e_t = []
-    for i in range(a.warmup + a.steps):
-        y_h.copy_(torch.from_numpy(y0))
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        for _ in range(wl.n_outer):
-            st_h = gm.solve_host(y_h, e_h, wl.dt, wl.rtol, wl.atol, variant=variant, persistent=persistent,
-                                 cells_per_block=a.cpb)
-        if i >= a.warmup:
-            e2e_t.append(time.perf_counter() - t)
-    _, _, e2e_value = replicas.aggregate(C * wl.n_outer * a.steps, sum(e2e_t), dist)
-    e2e = {"value": e2e_value, "unit": "cell-steps/s",
-           "h2d_bytes_per_step": int(wl.n_outer * (y_h.numel() * 8 + e_h.numel() * 8 + 8)),
-           "d2h_bytes_per_step": int(wl.n_outer * (y_h.numel() * 8 + C * 4)),
-           "ok_cells": int((st_h == 0).sum())}
+    e2e = None
+    if not a.no_e2e:
+        y_h = torch.empty((C, gm.n), dtype=torch.float64).pin_memory()
+        e_h = torch.tensor(env, dtype=torch.float64).pin_memory()
+        st_h = None
+        e2e_t = []
+        for i in range(a.warmup + a.steps):
+            y_h.copy_(torch.from_numpy(y0))
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            for _ in range(wl.n_outer):
+                st_h = gm.solve_host(y_h, e_h, wl.dt, wl.rtol, wl.atol, variant=variant, persistent=persistent,
+                                     cells_per_block=a.cpb)
+            if i >= a.warmup:
+                e2e_t.append(time.perf_counter() - t)
+        _, _, e2e_value = replicas.aggregate(C * wl.n_outer * a.steps, sum(e2e_t), dist)
+        e2e = {"value": e2e_value, "unit": "cell-steps/s",
+               "h2d_bytes_per_step": int(wl.n_outer * (y_h.numel() * 8 + e_h.numel() * 8 + 8)),
+               "d2h_bytes_per_step": int(wl.n_outer * (y_h.numel() * 8 + C * 4)),
+               "call": "camp_solve_host (pinned host arrays, synchronous)", "ok_cells": int((st_h == 0).sum())}
 
-    cpu = None
-    err = None
+    cpu = err = None
     if rank == 0 and world == 1 and not a.no_cpu:
-        cpu = oracle_rate(wl, a.cpu_seconds)
-        sample = cpu.pop("_result")
+        cpu, (om, idx, y0s, envs, y_o, st_o) = oracle_rate(a.cpu_seconds)
         if wl.n_outer == 1:  # the oracle's sample covers one outer step
-            err = {"cells": int(len(sample[0])), "rule": "species above atol, relative to the FP64 oracle",
-                   a.variant: error_vs_oracle(y_main, sample, wl.rtol, wl.atol)}
-            if plain is not None:
-                err["fp64"] = error_vs_oracle(y_plain, sample, wl.rtol, wl.atol)
+            okc = st_o == 0
+            err = {"rule": "species above atol, relative to the FP64 oracle; violating cells arbitrated against a "
+                           "tight oracle run (rtol 1e-10), strict per-species tier then error-control tier"}
+            for name, ys in ((a.variant, y_main), ("fp64", y_plain)):
+                if ys is None or (name == "fp64" and a.variant == "fp64" and ys is y_plain):
+                    continue
+                err[name] = error_vs_oracle([(om, y0s[idx][okc], envs[idx][okc], wl.dt, ys[idx][okc],
+                                              y_o[okc])], wl.atol, wl.rtol)
 
     if rank != 0:
         return
-    achieved = fp64 * wl.n_outer / (ms / 1e3) / 1e9  # the counters are one outer step's
     peak64 = camp.probe_fma_rate(True)
-    peak32 = camp.probe_fma_rate(False)
-    roof = {"bound": "alu", "unit": "GFLOP/s (fp64)", "achieved": achieved,
-            "peak": peak64, "peak_source": "measured FP64 FMA chains on this GPU (camp_probe_fma_rate)",
-            "peak_nominal": FP64_PEAK_NOMINAL_GFLOPS, "peak_fp32_measured": peak32,
-            "frac": achieved / peak64, "frac_of_nominal": achieved / FP64_PEAK_NOMINAL_GFLOPS,
-            "traffic": (DRAM_BYTES_PER_CELL[a.workload] * C
-                        if variant == camp.VARIANT_MIXED and a.workload in DRAM_BYTES_PER_CELL else None),
-            "traffic_unit": "bytes per launch (ncu dram read + write, scaled by cells)",
-            "kernel": "k_solve", "fp64_flops_per_launch": fp64, "lu_flops_per_launch": lu,
-            "lu_dtype": "f32" if variant == camp.VARIANT_MIXED else "f64"}
-    hbm = (y0.nbytes * 2 + env.nbytes + C * 4) / (ms / 1e3) / 1e9
+    lu_b = 4 if variant == camp.VARIANT_MIXED else 8
+    models = [cost_models(gm.info, counters, lu_b, wl.n_outer)]
+    digest = kernel_digest()
+    tr = DRAM_BYTES_PER_CELL.get(a.workload)
+    traffic = tr["bytes_per_cell"][0] * C if tr and tr["digest"] == digest and variant == camp.VARIANT_MIXED else None
+    roof = roofline(models, ms / 1e3, peak64, "f32" if lu_b == 4 else "f64", traffic, "k_solve",
+                    "step (one launch per outer step), CUDA events on the launch stream")
     out = {"metric": metric, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64 state / f32 J+LU" if variant == camp.VARIANT_MIXED else "f64",
-           "data": "synthetic (seeded generator shaped like the paper's gas mechanism)",
+           "data": "synthetic (seeded generator shaped like the paper's mechanisms)",
            "config": config, "form": f"{a.variant} {'persistent' if persistent else 'static'}",
-           "ok_cells": ok, "gpu_launches": a.steps * wl.n_outer,
-           "work": {"bdf_steps": steps, "newton_iters": newton, "lu_setups": jac, "mean_order": qbar,
-                    "steps_per_cell": steps / C,
-                    "per_s": {k: v * wl.n_outer * world / (ms / 1e3) for k, v in
-                              (("bdf_steps", steps), ("newton_iters", newton), ("lu_setups", jac))}},
+           "ok_cells": ok, "gpu_launches": a.steps,
+           "us_per_outer_step": 1e3 * ms / wl.n_outer,
+           "work": {k: models[0][k] for k in ("steps", "newton", "setups", "mean_order")},
            "plain_fp64": plain, "mixed_over_plain": (value / world / plain["value"]) if plain else None,
-           "roofline": roof, "hbm_io_gbs": hbm, "e2e": e2e, "cpu_baseline": cpu,
-           "error_vs_oracle": err, "clocks": clk.summary()}
+           "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err,
+           "kernel_digest": digest, "clocks": clk.summary()}
     print(json.dumps(out))
 
 
@@ -343,85 +693,6 @@ def _groups_on_device(groups, dev):
                     "atol": torch.full((1,), 1e-5, dtype=torch.float64, device=dev),
                     "workspace": camp.workspace(dev)})
     return out
-
-
-def bench_uneven(a):
-    """131072 cells of uneven stiffness (half dark, 10% cloud cells on the
-    multiphase mechanism): both mechanisms in one camp_solve_batch call, its
-    launches captured once in a CUDA graph and replayed per step, with the
-    autotuned cells-per-block; against the plain FP64 form, one static launch
-    per mechanism per step."""
-    import torch
-    from paper_2111_07436_gb300 import build, camp, workloads as w
-    build.build()
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    n_cells = a.cells or 131072
-    groups, cloud_idx = w.uneven_batch(n_cells)
-    G = _groups_on_device(groups, dev)
-    dt, rtol = 180.0, 1e-4
-    tuned = []
-    for g in G:  # autotune on a 4096-cell sample of each group
-        k = min(4096, g["y0"].shape[0])
-        tuned.append(g["mech"].autotune(g["y0"][:k].contiguous(), g["env"][:k].contiguous(), dt, rtol,
-                                        g["atol"]))
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    side = torch.cuda.Stream()
-
-    def step(stream):
-        for g in G:
-            g["state"].copy_(g["y0"])
-        camp.solve_batch([{k: g[k] for k in ("mech", "state", "env", "atol", "status", "workspace")}
-                          for g in G], dt, rtol, stream=stream)
-
-    with torch.cuda.stream(side):  # first call creates the fork streams outside capture
-        step(side)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=side):
-        step(side)
-    torch.cuda.synchronize()
-    times = []
-    with ClockSampler(0) as clk:
-        for i in range(a.warmup + a.steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            graph.replay()
-            e1.record()
-            times.append((e0, e1))
-        torch.cuda.synchronize()
-    ms = sum(e0.elapsed_time(e1) for e0, e1 in times[a.warmup:]) / a.steps
-    ok = sum(int((g["status"] == 0).sum().item()) for g in G)
-    # plain FP64: one static launch per mechanism per step
-    pt = []
-    for i in range(1 + max(1, a.steps // 2)):
-        flush.zero_()
-        for g in G:
-            g["state"].copy_(g["y0"])
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for g in G:
-            g["mech"].solve(g["state"], g["env"], dt, rtol, g["atol"], status=g["status"],
-                            variant=camp.VARIANT_FP64, persistent=False)
-        e1.record()
-        pt.append((e0, e1))
-    torch.cuda.synchronize()
-    pms = sum(e0.elapsed_time(e1) for e0, e1 in pt[1:]) / (len(pt) - 1)
-    value = n_cells / (ms / 1e3)
-    print(json.dumps({
-        "metric": f"cell-steps/s at rtol {rtol:g}", "value": value, "unit": "cell-steps/s", "n_gpus": 1,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64 state / f32 J+LU", "data": "synthetic",
-        "config": {"workload": f"uneven stiffness: {n_cells} cells, 50% dark, {len(cloud_idx)} cloud cells "
-                               f"on the 232-species mechanism, the rest on the 72-species one, dt 180 s",
-                   "groups": [int(g["y0"].shape[0]) for g in G],
-                   "autotuned_cpb_persistent_ms": tuned, "cuda_graph": True,
-                   "l2": "flushed between timed steps (256 MB write)"},
-        "ok_cells": ok, "gpu_launches": 2 * a.steps,
-        "plain_fp64": {"value": n_cells / (pms / 1e3), "ms_per_step": pms,
-                       "form": "fp64, one static launch per mechanism"},
-        "mixed_over_plain": pms / ms, "clocks": clk.summary()}))
 
 
 def bench_serving(a):
@@ -510,10 +781,9 @@ def bench_serving(a):
     n_cap = min(200, a.requests)
     sat = run(camp.VARIANT_MIXED, 0, n_cap)
     sat_p = run(camp.VARIANT_FP64, 0, n_cap)
-    # the Poisson stream at the offered load, for each form
+    # the Poisson stream at the offered load, for each form, over every request
     mixed = run(camp.VARIANT_MIXED, a.load * sat["cell_steps_per_s"], a.requests)
-    n_plain = min(a.requests, 400)
-    plain = run(camp.VARIANT_FP64, a.load * sat_p["cell_steps_per_s"], n_plain)
+    plain = run(camp.VARIANT_FP64, a.load * sat_p["cell_steps_per_s"], a.requests)
     print(json.dumps({
         "metric": "cell-steps/s at rtol 1e-4; p50/p99 chunk latency", "value": mixed["cell_steps_per_s"],
         "unit": "cell-steps/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
