@@ -227,6 +227,21 @@ int camp_solve(const camp_mech *m, int64_t n_cells, double *state, const double 
                const camp_solve_opts *opts, void *stream);
 
 /*
+ * n_steps consecutive outer steps of dt for every cell in ONE launch: the
+ * host model's box run of Sect. 4.1 (a fixed environment, the state carried
+ * from one step to the next), each step integrated as camp_solve would (a
+ * cold start unless opts->step carries the step sizes).  trajectory (device
+ * [n_steps][n_cells][n_species], or NULL) receives the state after each
+ * step; state holds the state after the last step (or after the last step
+ * that succeeded: a failing cell stops there, its status says why, and its
+ * later trajectory rows are not written).  opts->stats, if set, sums the
+ * counters over the steps.  Otherwise as camp_solve; n_steps >= 1.
+ */
+int camp_solve_sequence(const camp_mech *m, int64_t n_cells, double *state, const double *env, double dt,
+                        int32_t n_steps, double *trajectory, double rtol, const double *atol,
+                        int32_t atol_len, int32_t *status, const camp_solve_opts *opts, void *stream);
+
+/*
  * Same as camp_solve with HOST arrays: copies state/env/atol to the device,
  * solves and copies state/status back, synchronously, on `stream`.  Device
  * staging buffers are kept per mechanism between calls (grown as needed);
@@ -274,8 +289,9 @@ int camp_solve_host_static(const camp_mech *m, int64_t n_cells, double *state, c
 /* One group of cells per mechanism (e.g. gas-only cells and cells carrying
  * aqueous phases).  Each group runs as its own persistent grid on a stream
  * forked from `stream` (joined back before the call's work completes), the
- * group with the most estimated work first, so that as one grid drains its
- * counter the next one's blocks take the freed SMs.  Capturable in a CUDA
+ * group whose cells cost the most first, so that as one grid drains its
+ * counter the next one's blocks take the freed SMs and the batch ends on the
+ * cheapest cells.  Capturable in a CUDA
  * graph (the fork/join uses events).  Arrays are device arrays as for
  * camp_solve; groups must not alias.  At most CAMP_MAX_GROUPS groups. */
 #define CAMP_MAX_GROUPS 8

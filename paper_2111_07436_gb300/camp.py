@@ -81,7 +81,7 @@ EXPORTS = ["camp_mech_load", "camp_mech_compile", "camp_mech_free", "camp_mech_i
            "camp_server_poll", "camp_server_wait", "camp_server_stats", "camp_server_cancel",
            "camp_server_destroy",
            "camp_solve_batch", "camp_solve_batch_host", "camp_autotune", "camp_probe_fma_rate",
-           "camp_solve_host_static", "camp_server_resident_create", "camp_server_resident_step",
+           "camp_solve_host_static", "camp_solve_sequence", "camp_server_resident_create", "camp_server_resident_step",
            "camp_server_resident_read", "camp_server_resident_write", "camp_server_resident_destroy"]
 
 
@@ -109,6 +109,7 @@ def lib():
     L.camp_workspace_bytes.restype = ctypes.c_size_t
     L.camp_solve.argtypes = [vp, i64, vp, vp, dbl, dbl, vp, i32, vp, ctypes.POINTER(SolveOpts), vp]
     L.camp_solve_host.argtypes = L.camp_solve.argtypes
+    L.camp_solve_sequence.argtypes = [vp, i64, vp, vp, dbl, i32, vp, dbl, vp, i32, vp, ctypes.POINTER(SolveOpts), vp]
     L.camp_rate_constants.argtypes = [vp, i64, vp, vp, vp, vp]
     L.camp_forcing.argtypes = [vp, i64, vp, vp, vp, vp]
     L.camp_jacobian.argtypes = [vp, i64, vp, vp, vp, i32, vp]
@@ -229,6 +230,30 @@ class Mechanism:
             o.step = step.data_ptr()
         _check(lib().camp_solve(self._h, C, _ptr(state), _ptr(env), float(dt), float(rtol), _ptr(a),
                                 a.numel(), _ptr(status), ctypes.byref(o), _stream(stream)))
+        return status
+
+    def solve_sequence(self, state, env, dt, n_steps, rtol, atol, trajectory=None, status=None,
+                       variant=VARIANT_MIXED, persistent=None, stats=None, stream=None, step=None,
+                       max_steps=10000):
+        """n_steps consecutive outer steps of dt in one launch (camp_solve_
+        sequence); trajectory: optional float64 CUDA tensor [n_steps, C, n]
+        receiving the state after every step.  Returns status."""
+        import torch
+        C = state.shape[0]
+        _dev_f64(state, (C, self.n), "state")
+        _dev_f64(env, (C, self.n_env), "env")
+        if trajectory is not None:
+            _dev_f64(trajectory, (n_steps, C, self.n), "trajectory")
+        if status is None:
+            status = torch.empty(C, dtype=torch.int32, device=state.device)
+        a = atol if isinstance(atol, torch.Tensor) else self._atol(atol, state.device)
+        o = self.opts(variant, persistent, max_steps=max_steps, stats=stats)
+        if step is not None:
+            _dev_f64(step, (C,), "step")
+            o.step = step.data_ptr()
+        _check(lib().camp_solve_sequence(self._h, C, _ptr(state), _ptr(env), float(dt), int(n_steps),
+                                         _ptr(trajectory), float(rtol), _ptr(a), a.numel(), _ptr(status),
+                                         ctypes.byref(o), _stream(stream)))
         return status
 
     def autotune(self, state, env, dt, rtol, atol, variant=VARIANT_MIXED, stream=None):

@@ -269,11 +269,11 @@ void camp_solve_opts_default(camp_solve_opts *o, int variant) {
 
 size_t camp_workspace_bytes(void) { return 256; }
 
-int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double *env, double dt,
-               double rtol, const double *atol, int32_t atol_len, int32_t *status,
-               const camp_solve_opts *opts, void *stream) {
-    CampRange range_("camp_solve");
+static int solve_impl(const camp_mech *mc, int64_t n_cells, double *state, const double *env, double dt,
+                      int32_t n_outer, double *traj, double rtol, const double *atol, int32_t atol_len,
+                      int32_t *status, const camp_solve_opts *opts, void *stream) {
     camp_mech *m = const_cast<camp_mech *>(mc);
+    if (n_outer < 1) return fail(CAMP_E_INVAL, "n_steps must be at least 1");
     if (!m) return fail(CAMP_E_INVAL, "NULL mechanism");
     if (n_cells < 0) return fail(CAMP_E_INVAL, "n_cells < 0");
     if (n_cells == 0) return CAMP_OK;
@@ -339,6 +339,8 @@ int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double
     a.hmin_frac = o.hmin_frac;
     a.cpb = cpb;
     a.queue = nullptr;
+    a.n_outer = n_outer;
+    a.traj = traj;
     cudaStream_t s = (cudaStream_t)stream;
 
     long long grid;
@@ -364,6 +366,21 @@ int camp_solve(const camp_mech *mc, int64_t n_cells, double *state, const double
     else
         CUDA_TRY(f32 ? camp_launch_solve_f32(m->dm, a, (int)grid, s) : camp_launch_solve_f64(m->dm, a, (int)grid, s));
     return CAMP_OK;
+}
+
+int camp_solve(const camp_mech *m, int64_t n_cells, double *state, const double *env, double dt,
+               double rtol, const double *atol, int32_t atol_len, int32_t *status,
+               const camp_solve_opts *opts, void *stream) {
+    CampRange range_("camp_solve");
+    return solve_impl(m, n_cells, state, env, dt, 1, nullptr, rtol, atol, atol_len, status, opts, stream);
+}
+
+int camp_solve_sequence(const camp_mech *m, int64_t n_cells, double *state, const double *env, double dt,
+                        int32_t n_steps, double *trajectory, double rtol, const double *atol,
+                        int32_t atol_len, int32_t *status, const camp_solve_opts *opts, void *stream) {
+    CampRange range_("camp_solve_sequence");
+    return solve_impl(m, n_cells, state, env, dt, n_steps, trajectory, rtol, atol, atol_len, status, opts,
+                      stream);
 }
 
 int camp_solve_host(const camp_mech *mc, int64_t n_cells, double *state, const double *env,
@@ -426,13 +443,16 @@ int camp_solve_batch(const camp_group *groups, int32_t n_groups, double dt, doub
     CampRange range_("camp_solve_batch");
     if (!groups || n_groups < 0 || n_groups > CAMP_MAX_GROUPS) return fail(CAMP_E_INVAL, "bad group count");
     if (n_groups == 0) return CAMP_OK;
-    // estimated work: cells x (per-cell f flops + LU solve flops), heaviest first
+    // estimated work of one cell (f flops + LU solve flops + vector work),
+    // costliest cells first: each group's persistent grid holds the SMs
+    // until its counter runs dry, so the groups run one after the other and
+    // the last group's cells make the batch's tail -- best the shortest ones
     int order[CAMP_MAX_GROUPS];
     double work[CAMP_MAX_GROUPS];
     for (int g = 0; g < n_groups; g++) {
         if (!groups[g].mech) return fail(CAMP_E_INVAL, "NULL mechanism in group");
         const camp::HostMech &h = groups[g].mech->h;
-        work[g] = (double)groups[g].n_cells * (double)(h.flops_forcing + h.flops_solve + 20 * h.n);
+        work[g] = (double)(h.flops_forcing + h.flops_solve + 20 * h.n);
         order[g] = g;
     }
     std::sort(order, order + n_groups, [&](int a, int b) { return work[a] > work[b]; });

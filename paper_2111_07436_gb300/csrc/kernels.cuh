@@ -50,19 +50,32 @@ __global__ void __maxnreg__((sizeof(LT) == 8 || G > 32) ? 255 : (NPL >= 6 ? 224 
             }
         }
         if (cell >= a.n_cells) break;
-        CellStats st;
-        int s = integrate_cell<G, NPL, LT, W>(m, c, a.state + cell * m.n, a.env + cell * m.n_env, a.dt,
-                                           a.rtol, a.atol, a.atol_len, a.max_steps, a.hmin_frac,
-                                           a.step ? a.step + cell : nullptr, lane, gm, st);
+        CellStats st, tot{0, 0, 0, 0, 0};
+        int s = ST_OK;
+        // one or more consecutive outer steps of dt, each an independent call
+        // of the integrator (a cold start unless step sizes are carried);
+        // with a trajectory, the state after each one is also written there
+        for (int o = 0; o < a.n_outer && s == ST_OK; o++) {
+            s = integrate_cell<G, NPL, LT, W>(m, c, a.state + cell * m.n, a.env + cell * m.n_env, a.dt, a.rtol,
+                                              a.atol, a.atol_len, a.max_steps, a.hmin_frac,
+                                              a.step ? a.step + cell : nullptr, lane, gm, st,
+                                              a.traj ? a.traj + ((long long)o * a.n_cells + cell) * m.n : nullptr);
+            tot.steps += st.steps;
+            tot.newton += st.newton;
+            tot.jac += st.jac;
+            tot.errfail += st.errfail;
+            tot.ordsum += st.ordsum;
+            if (o + 1 < a.n_outer) gsync<G>(gm);  // the state written back is the next step's input
+        }
         if (lane == 0) {
             a.status[cell] = s;
             if (a.stats) {
                 int32_t *o = a.stats + 5 * cell;
-                o[0] = st.steps;
-                o[1] = st.newton;
-                o[2] = st.jac;
-                o[3] = st.errfail;
-                o[4] = st.ordsum;
+                o[0] = tot.steps;
+                o[1] = tot.newton;
+                o[2] = tot.jac;
+                o[3] = tot.errfail;
+                o[4] = tot.ordsum;
             }
         }
         if (!a.queue) break;
