@@ -15,8 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcamp.so")
-SOURCES = ["capi.cu", "solve_f32.cu", "solve_f64.cu", "solve_f32w.cu", "solve_f64w.cu", "mech.cpp",
-           "server.cpp", "probe.cu", "static_scratch.cu"]
+SOURCES = ["capi.cu", "solve_f32.cu", "solve_f64.cu", "solve_f32w.cu", "solve_f64w.cu", "solve_arrow.cu",
+           "mech.cpp", "server.cpp", "probe.cu", "static_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

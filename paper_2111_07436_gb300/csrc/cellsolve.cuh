@@ -154,15 +154,19 @@ __device__ __forceinline__ double condensation(double rad, double Np, double alp
     return Np * 4.0 * PI_D * rad * Dg * ffs;
 }
 
-// Liquid volume of section b in the rate constants: the env value, or 1 when
-// the water parameter makes it a function of the state (the constants are
-// then per unit volume and the powers of 1/L are applied at each state)
-__device__ __forceinline__ double section_volume(const DevMech &m, const double *__restrict__ env, int b) {
-    return m.n_wsec > 0 ? 1.0 : env[m.env_sec_base + 3 * b + 2];
+// Liquid volume of a section in the rate constants: the env value (the
+// section's (r, N, L) triple in sec), or 1 when the water parameter makes it a
+// function of the state (the constants are then per unit volume and the
+// powers of 1/L are applied at each state)
+__device__ __forceinline__ double section_volume(const DevMech &m, const double *__restrict__ sec) {
+    return m.n_wsec > 0 ? 1.0 : sec[2];
 }
 
-__device__ inline void rate_constant(const DevMech &m, int k, const double *__restrict__ env,
-                                     double &kf, double &kr) {
+// Rate constants of process k: env holds T, P and the runtime rates; sec the
+// (radius, number concentration, liquid volume) of the section (or particle)
+// a section process acts in (unused by the others)
+__device__ inline void rate_constant_at(const DevMech &m, int k, const double *__restrict__ env,
+                                        const double *__restrict__ sec, double &kf, double &kr) {
     const double T = env[0], P = env[1];
     const double Mair = P / (KB * T) * 1e-6;  // molec cm^-3
     const double mppb = Mair * 1e-9;          // molec cm^-3 per ppb
@@ -210,10 +214,9 @@ __device__ inline void rate_constant(const DevMech &m, int k, const double *__re
         // H = c_tot / p0 with the SIMPOL.1 vapour pressure
         // log10 p0 [atm] = B1/T + B2 + B3 T + B4 ln T (Raoult's law in a
         // condensed phase of fixed total molarity c_tot)
-        const int b = __ldg(m.rslot + k);
-        const double rad = env[m.env_sec_base + 3 * b];
-        const double Np = env[m.env_sec_base + 3 * b + 1];
-        const double L = section_volume(m, env, b);
+        const double rad = sec[0];
+        const double Np = sec[1];
+        const double L = section_volume(m, sec);
         if (!(L > 0.0 && Np > 0.0 && rad > 0.0)) break;
         double H, kb;
         if (__ldg(m.rtype + k) == CAMP_P_HENRY) {
@@ -231,8 +234,7 @@ __device__ inline void rate_constant(const DevMech &m, int k, const double *__re
     case CAMP_P_AQREV: {
         // K_eq = A exp(C (1/T - 1/298)); rates in M/s, molarity = y * phi,
         // phi = 1e-9 P / (R T 1000 L) M per ppb
-        const int b = __ldg(m.rslot + k);
-        const double L = section_volume(m, env, b);
+        const double L = section_volume(m, sec);
         if (!(L > 0.0)) break;
         double Keq = __ldg(par) * exp(__ldg(par + 1) * (1.0 / T - 1.0 / 298.0));
         double krev = __ldg(par + 2);
@@ -244,8 +246,7 @@ __device__ inline void rate_constant(const DevMech &m, int k, const double *__re
     case CAMP_P_COND_ARRHENIUS: {
         // Arrhenius in the section's condensed phase, M^(1-nr) s^-1:
         // kf = k phi^(nr - 1) in ppb units
-        const int b = __ldg(m.rslot + k);
-        const double L = section_volume(m, env, b);
+        const double L = section_volume(m, sec);
         if (!(L > 0.0)) break;
         double kk = __ldg(par) * exp(__ldg(par + 2) / T) * pow(T / __ldg(par + 3), __ldg(par + 1)) *
                     (1.0 + __ldg(par + 4) * P);
@@ -254,6 +255,19 @@ __device__ inline void rate_constant(const DevMech &m, int k, const double *__re
         break;
     }
     }
+}
+
+__device__ __forceinline__ bool section_type(int t) {
+    return t == CAMP_P_HENRY || t == CAMP_P_SIMPOL || t == CAMP_P_AQREV || t == CAMP_P_COND_ARRHENIUS;
+}
+
+// Rate constants of process k of a compiled mechanism (section processes
+// read their section's triple from env)
+__device__ __forceinline__ void rate_constant(const DevMech &m, int k, const double *__restrict__ env,
+                                              double &kf, double &kr) {
+    const int t = __ldg(m.rtype + k);
+    const double *sec = section_type(t) ? env + m.env_sec_base + 3 * __ldg(m.rslot + k) : env;
+    rate_constant_at(m, k, env, sec, kf, kr);
 }
 
 // FP64 values into and out of the LU precision
@@ -1257,13 +1271,14 @@ struct CellStats {
 // y_cell/env_cell: this cell's rows (declaration order).  Returns the status;
 // the state is written back only on success.  step_io (null: cold start):
 // warm start, in: a value > 0 replaces the initial-step estimate; out: the
-// step held before the final cut to dt, 0 on failure.
+// step held before the final cut to dt, 0 on failure.  y_copy (or null)
+// receives a second copy of the new state on success.
 template <int G, int NPL, typename LT, bool W>
 __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__restrict__ y_cell,
                               const double *__restrict__ env_cell, double dt, double rtol,
                               const double *__restrict__ atol, int atol_len, int max_steps,
                               double hmin_frac, double *step_io, int lane, unsigned gm,
-                              CellStats &st) {
+                              CellStats &st, double *__restrict__ y_copy = nullptr) {
     const int n = m.n;
     constexpr bool EXACT = sizeof(LT) == 8;  // the plain FP64 form
     using C = Ctl<EXACT>;
@@ -1561,7 +1576,11 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
 #pragma unroll
         for (int s = 0; s < NPL; s++) {
             int p = lane + G * s;
-            if (p < n) y_cell[__ldg(m.perm + p)] = z[0][s];
+            if (p < n) {
+                const int i = __ldg(m.perm + p);
+                y_cell[i] = z[0][s];
+                if (y_copy) y_copy[i] = z[0][s];
+            }
         }
     }
     if (step_io && lane == 0) *step_io = status == ST_OK ? h_held : 0.0;

@@ -31,6 +31,8 @@ struct SolveArgs {
     double hmin_frac;
     int cpb;                        // cells per block
     unsigned long long *queue;      // work counter (persistent form) or null
+    int n_outer;                    // consecutive outer steps of dt per cell (>= 1)
+    double *traj;                   // [n_outer][n_cells][n] states after each outer step, or null
 };
 
 // Cell shapes instantiated: one warp per cell (G = 32 lanes) with NPL
@@ -81,6 +83,17 @@ cudaError_t camp_launch_lu_solve_f32(const DevMech &m, long long n_cells, const 
 cudaError_t camp_launch_lu_solve_f64(const DevMech &m, long long n_cells, const double *state,
                                      const double *env, double gamma, const double *b, double *x,
                                      int *status, cudaStream_t s);
+
+// The block-arrow solve of particle-resolved cells (solve_arrow.cu): one cell
+// per thread-block cluster of cl_size CTAs; scratch holds n_clusters cells
+// of camp_arrow_cell_bytes each.
+#include "arrow.h"
+size_t camp_arrow_cell_bytes(const ArrowDev &a, int lu_elem);
+cudaError_t camp_arrow_max_clusters(int lu_elem, int cl_size, int *n);
+cudaError_t camp_arrow_launch(const DevMech &mt, const ArrowDev &a, const SolveArgs &s, int lu_elem, char *scratch,
+                              size_t cell_bytes, int n_clusters, int cl_size, cudaStream_t st);
+cudaError_t camp_arrow_forcing(const DevMech &mt, const ArrowDev &a, long long n_cells, const double *state,
+                               const double *env, double *f, cudaStream_t st);
 
 // Record an error message for camp_last_error() and return `code`.
 int camp_record_error(int code, const char *msg);

@@ -80,14 +80,14 @@ static int as_multiplicity(double v, const char *what) {
 }
 
 // ---- species and processes -------------------------------------------------
-static void read_processes(const Value &root, HostMech &h) {
+static void read_processes(const Value &root, HostMech &h, int instances) {
     const Value &sp = root.at("species");
     if (sp.kind != Value::Array) throw std::runtime_error("'species' must be an array");
     for (auto &s : sp.arr) h.species.push_back(s.string("name"));
     h.n_gas = (int)h.species.size();
     std::vector<std::string> phase;
     if (const Value *a = root.find("aerosol")) {
-        h.n_sections = (int)a->number("sections");
+        h.n_sections = instances >= 0 ? instances : (int)a->number("sections");
         if (h.n_sections < 0 || h.n_sections > 1024) throw std::runtime_error("bad section count");
         const Value &ph = root.at("phases").at(a->string("phase"));
         for (auto &p : ph.arr) phase.push_back(p.string("name"));
@@ -1178,16 +1178,112 @@ static void validate_tables(const HostMech &h) {
         if (h.su_ptr[i] > h.su_ptr[i + 1] || h.sl_ptr[i] > h.sl_ptr[i + 1]) fail("substitution pointers");
 }
 
-HostMech compile_mechanism(const char *json, size_t len) {
+HostMech compile_mechanism(const char *json, size_t len, int instances) {
     Value root = campjson::parse(json, len);
     HostMech h;
-    read_processes(root, h);
+    read_processes(root, h, instances);
     if (h.n < 1) throw std::runtime_error("mechanism has no species");
     build_structure(h);
     build_tables(h);
     pack_records(h);
     validate_tables(h);
     return h;
+}
+
+AerosolShape aerosol_shape(const char *json, size_t len) {
+    Value root = campjson::parse(json, len);
+    AerosolShape s;
+    if (const Value *a = root.find("aerosol")) {
+        const double k = a->number("sections");
+        if (!(k >= 0.0 && k <= 1e6)) throw std::runtime_error("bad section count");
+        s.instances = (int)k;
+        if (const Value *r = a->find("representation")) s.particles = r->kind == Value::String && r->str == "particles";
+        if (const Value *v = a->find("solver")) s.block_arrow = v->kind == Value::String && v->str == "block_arrow";
+    }
+    if (const Value *p = root.find("parameters")) s.water = p->kind == Value::Array && !p->arr.empty();
+    return s;
+}
+
+// ---- the block-arrow form ----------------------------------------------------
+ArrowHost build_arrow(const HostMech &t, int P) {
+    if (t.n_sections != 1) throw std::runtime_error("the block-arrow template holds one instance");
+    if (!t.el_phase.empty()) throw std::runtime_error("the block-arrow form has no water parameter");
+    ArrowHost a;
+    a.P = P;
+    a.n_g = t.n_gas;
+    a.n_phi = t.n - t.n_gas;
+    a.E0 = t.env_sec_base;
+    a.n_env = t.env_sec_base + 3 * P;
+    if (a.n_g > CAMP_ARROW_MAX_GAS) throw std::runtime_error("block-arrow form: more than 32 gas species");
+    if (a.n_phi < 1 || a.n_phi > CAMP_ARROW_MAX_PHI)
+        throw std::runtime_error("block-arrow form: 1 to 16 phase species per particle");
+    auto local = [&](int s) {  // template species -> particle-local index
+        if (s >= a.n_g) return s - a.n_g;
+        auto it = std::find(a.coupled.begin(), a.coupled.end(), s);
+        if (it != a.coupled.end()) return a.n_phi + (int)(it - a.coupled.begin());
+        a.coupled.push_back(s);
+        return a.n_phi + (int)a.coupled.size() - 1;
+    };
+    std::vector<int> gas_index;  // template process -> gas process number
+    for (int k = 0; k < (int)t.procs.size(); k++) {
+        const Process &p = t.procs[k];
+        const bool sec = is_sectioned(p.type);
+        for (auto &e : p.react)
+            if (!sec && e.first >= a.n_g) throw std::runtime_error("a gas process touches a phase species");
+        for (auto &e : p.prod)
+            if (!sec && e.first >= a.n_g) throw std::runtime_error("a gas process touches a phase species");
+        auto map = [&](int s) { return sec ? local(s) : s; };
+        int rec[12];
+        std::fill(rec, rec + 12, -1);
+        rec[0] = k;
+        int nf = 0, nb = 0;
+        for (auto &e : p.react)
+            for (int m = 0; m < e.second; m++) rec[4 + nf++] = map(e.first);
+        if (p.reversible())
+            for (auto &e : p.prod)
+                for (int m = 0; m < (int)e.second; m++) rec[8 + nb++] = map(e.first);
+        rec[1] = nf;
+        rec[2] = nb;
+        rec[3] = (int)a.st_sp.size();
+        for (int s : touched(p)) {
+            const double nu = net_coef(p, s);
+            if (nu == 0.0) continue;
+            a.st_sp.push_back(map(s));
+            a.st_nu.push_back(nu);
+        }
+        rec[7] = (int)a.st_sp.size();
+        rec[11] = p.reversible() ? 1 : 0;
+        std::vector<int> &dst = sec ? a.prec : a.grec;
+        if (!sec) gas_index.push_back(k);
+        dst.insert(dst.end(), rec, rec + 12);
+        // algorithmic work, per instance for the particle processes
+        const long long inst = sec ? P : 1;
+        a.model_forcing += inst * (2LL * (long long)p.react.size() + (long long)p.prod.size());
+        a.flops_forcing += inst * (nf + (p.reversible() ? nb + 1 : 0) + 2LL * (rec[7] - rec[3]));
+        a.flops_jacobian += inst * (long long)(nf + nb) * (long long)(std::max(nf, nb) + 2 * (rec[7] - rec[3]));
+    }
+    a.Rg = (int)a.grec.size() / 12;
+    a.Rp = (int)a.prec.size() / 12;
+    a.n_c = (int)a.coupled.size();
+    if (a.n_c > CAMP_ARROW_MAX_C) throw std::runtime_error("block-arrow form: a particle exchanges with more than 8 gas species");
+    // gas rows: the gas processes that change each gas species
+    a.gf_ptr.assign(a.n_g + 1, 0);
+    for (int i = 0; i < a.n_g; i++) {
+        for (int g = 0; g < a.Rg; g++) {
+            const int *r = &a.grec[(size_t)g * 12];
+            for (int q = r[3]; q < r[7]; q++)
+                if (a.st_sp[q] == i) {
+                    a.gf_k.push_back(g);
+                    a.gf_nu.push_back(a.st_nu[q]);
+                }
+        }
+        a.gf_ptr[i + 1] = (int)a.gf_k.size();
+    }
+    // dense per-particle LU (block, U_pG, L_Gp, Schur) and the gas block
+    const long long np = a.n_phi, nc = a.n_c, ng = a.n_g;
+    a.flops_factor = (long long)P * (2 * np * np * np / 3 + 2 * np * np * nc * 2 + 2 * nc * nc * np) + 2 * ng * ng * ng / 3;
+    a.flops_solve = (long long)P * (2 * np * np + 4 * np * nc) + 2 * ng * ng;
+    return a;
 }
 
 void bdf_coefficients(DevMech &dm) {
@@ -1297,6 +1393,30 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.n_pw = h.n_pw;
     dm.n_pw64 = h.n_pw64;
     bdf_coefficients(dm);
+    return pk.img;
+}
+
+std::vector<unsigned char> pack_arrow(const ArrowHost &a, ArrowDev &ad, const unsigned char *base) {
+    Packer pk{{}, base};
+    ad.P = a.P;
+    ad.n_g = a.n_g;
+    ad.n_phi = a.n_phi;
+    ad.n_c = a.n_c;
+    ad.n_loc = a.n_phi + a.n_c;
+    ad.n = a.n_g + a.P * a.n_phi;
+    ad.n_env = a.n_env;
+    ad.E0 = a.E0;
+    ad.Rg = a.Rg;
+    ad.Rp = a.Rp;
+    ad.grec = reinterpret_cast<const int4 *>(pk.put(a.grec));
+    ad.prec = reinterpret_cast<const int4 *>(pk.put(a.prec));
+    ad.st_sp = pk.put(a.st_sp);
+    ad.st_nu = pk.put(a.st_nu);
+    ad.coupled = pk.put(a.coupled);
+    ad.gf_ptr = pk.put(a.gf_ptr);
+    ad.gf_k = pk.put(a.gf_k);
+    ad.gf_nu = pk.put(a.gf_nu);
+    ad.blk = a.n_phi * a.n_phi + 2 * a.n_phi * a.n_c;
     return pk.img;
 }
 

@@ -7,6 +7,7 @@
 #include <utility>
 #include <vector>
 
+#include "arrow.h"
 #include "devmech.h"
 
 namespace camp {
@@ -78,7 +79,34 @@ struct HostMech {
 };
 
 // Throws std::runtime_error with a message on malformed input.
-HostMech compile_mechanism(const char *json, size_t len);
+// instances >= 0 replaces the aerosol's section / particle count (the
+// template of the block-arrow form compiles one instance).
+HostMech compile_mechanism(const char *json, size_t len, int instances = -1);
+
+// The aerosol instancing of a mechanism, read without compiling it.
+struct AerosolShape {
+    int instances = 0;        // sections or computational particles
+    bool particles = false;   // "representation": "particles"
+    bool block_arrow = false; // "solver": "block_arrow" asked for
+    bool water = false;       // a ZSR water parameter
+};
+AerosolShape aerosol_shape(const char *json, size_t len);
+
+// Host image of the block-arrow form (arrow.h), built from the one-instance
+// template `t` for P instances.
+struct ArrowHost {
+    int P = 0, n_g = 0, n_phi = 0, n_c = 0, E0 = 0, n_env = 0, Rg = 0, Rp = 0;
+    std::vector<int> grec, prec;  // 12 ints a record
+    std::vector<int> st_sp;
+    std::vector<double> st_nu;
+    std::vector<int> coupled;
+    std::vector<int> gf_ptr, gf_k;
+    std::vector<double> gf_nu;
+    // algorithmic work of the full mechanism (as HostMech's counts)
+    long long model_forcing = 0, flops_forcing = 0, flops_jacobian = 0, flops_factor = 0, flops_solve = 0;
+};
+ArrowHost build_arrow(const HostMech &t, int P);
+std::vector<unsigned char> pack_arrow(const ArrowHost &a, ArrowDev &ad, const unsigned char *base);
 
 // Fill the coefficient arrays of a DevMech (host-side arithmetic).
 void bdf_coefficients(DevMech &dm);
