@@ -36,7 +36,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {"small": 1, "gas72": 2, "multiphase232": 3, "uneven": 4, "serving": 5, "particles": 6,
-             "water": 7}
+             "water": 7, "particles10k": 8}
+# beyond this many species the dense FP64 oracle (n^2 Jacobian, n^3 LU per
+# setup) is out of reach of a bounded CPU sample
+ORACLE_MAX_SPECIES = 4096
 FP64_PEAK_NOMINAL_GFLOPS = 1250.0  # GB300 dense FP64, nominal
 HBM_FALLBACK_GBS = 6800.0          # used only when the measured peaks file is absent
 # DRAM bytes (read + write) per cell of one mixed-form k_solve launch, from
@@ -534,8 +537,14 @@ def bench_single(a):
                          f"{threads} threads, {el:.1f} s", "ok_cells": int((st == 0).sum())}
         return cpu, (om, idx, y0, env, y_o, st)
 
+    n_species = len(w.layout(wl.mech).species)
+    oracle_off = n_species > ORACLE_MAX_SPECIES and \
+        f"the dense FP64 oracle needs a {n_species}^2 Jacobian ({8 * n_species ** 2 / 1e9:.0f} GB) per cell"
     if a.impl == "reference":
         if rank != 0:
+            return
+        if oracle_off:
+            print(json.dumps({"impl": "reference", "unavailable": oracle_off}))
             return
         cpu, _ = oracle_rate(a.cpu_seconds)
         vals = [oracle_rate(a.cpu_seconds / 2)[0]["value"] for _ in range(a.warmup + a.steps)]
@@ -645,7 +654,9 @@ def bench_single(a):
                "call": "camp_solve_host (pinned host arrays, synchronous)", "ok_cells": int((st_h == 0).sum())}
 
     cpu = err = None
-    if rank == 0 and world == 1 and not a.no_cpu:
+    if oracle_off:
+        cpu = {"value": None, "unit": "cell-steps/s", "kind": "oracle", "unavailable": oracle_off}
+    elif rank == 0 and world == 1 and not a.no_cpu:
         cpu, (om, idx, y0s, envs, y_o, st_o) = oracle_rate(a.cpu_seconds)
         if wl.n_outer == 1:  # the oracle's sample covers one outer step
             okc = st_o == 0

@@ -180,7 +180,9 @@ typedef struct {
                                 grid; -1: the autotuned choice (default) */
     int32_t max_steps;       /* internal steps per cell (default 10000) */
     int32_t cells_per_block; /* 0: the autotuned choice if any, else the
-                                count (1..4) with the most resident cells */
+                                count (1..4) with the most resident cells.
+                                Block-arrow (particle-resolved) mechanisms:
+                                CTAs per cluster, 1, 2, 4, 8 or 16 (0: 8) */
     double hmin_frac;        /* minimum step = hmin_frac * dt (default 1e-10) */
     int32_t *stats;          /* optional device [n_cells][CAMP_NSTATS]: steps,
                                 Newton iterations, Jacobian/LU setups,

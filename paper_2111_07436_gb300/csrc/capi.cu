@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <stdexcept>
 #include <string>
 
 #include "camp.h"
@@ -28,7 +29,24 @@ struct camp_mech {
     int occ[2][9] = {};                 // blocks per SM by variant and cells per block (0 = unknown)
     int tuned_cpb[2] = {0, 0};          // per variant, 0 = untuned
     int tuned_persistent[2] = {-1, -1}; // per variant, -1 = untuned
+    // the full mechanism's sizes (h holds the one-particle template when
+    // the block-arrow form is used)
+    int n = 0, n_env = 0;
+    // block-arrow form of a particle-resolved mechanism (arrow.h)
+    bool arrow = false;
+    camp::ArrowHost ah;
+    ArrowDev ad{};
+    void *arrow_tables = nullptr;
+    int arrow_clusters[2][5] = {};      // co-resident clusters per LU precision and cluster size (0 = unknown)
 };
+
+// CTAs per cluster of the block-arrow solve (default; camp_solve_opts.
+// cells_per_block picks 1, 2, 4, 8 or 16 for this form)
+static const int kArrowCluster = 8;
+
+// true when camp_solve needs device scratch beyond its arguments and the
+// work counter (the block-arrow form's per-cell rows)
+bool camp_mech_needs_scratch(const camp_mech *m) { return m && m->arrow; }
 
 namespace {
 thread_local std::string g_err;
@@ -140,10 +158,30 @@ static int mech_build(const char *json, size_t len, camp_mech **out, char *err, 
     if (!json) return report(CAMP_E_INVAL, "json is NULL");
     camp_mech *m = new camp_mech();
     try {
-        m->h = camp::compile_mechanism(json, len);
+        // a particle-resolved mechanism takes the block-arrow form when it
+        // asks for it or is too large for one block's shared memory
+        const camp::AerosolShape sh = camp::aerosol_shape(json, len);
+        if (sh.particles && sh.instances > 0) {
+            camp::HostMech t = camp::compile_mechanism(json, len, 1);
+            const long long n_full = t.n_gas + (long long)sh.instances * (t.n - t.n_gas);
+            if (sh.block_arrow || n_full > 2048) {
+                if (sh.water) throw std::runtime_error("the block-arrow form takes no water parameter");
+                m->ah = camp::build_arrow(t, sh.instances);
+                m->h = std::move(t);
+                m->arrow = true;
+            }
+        }
+        if (!m->arrow) m->h = camp::compile_mechanism(json, len);
     } catch (const std::exception &e) {
         delete m;
         return report(CAMP_E_PARSE, e.what());
+    }
+    if (m->arrow) {
+        m->n = m->ah.n_g + m->ah.P * m->ah.n_phi;
+        m->n_env = m->ah.n_env;
+    } else {
+        m->n = m->h.n;
+        m->n_env = m->h.n_env;
     }
     if (camp_pick_shape(m->h.n) < 0) {
         delete m;
@@ -168,8 +206,18 @@ static int mech_build(const char *json, size_t len, camp_mech **out, char *err, 
         img = camp::pack_tables(m->h, m->dm, (const unsigned char *)m->dev_tables);
         e = cudaMemcpy(m->dev_tables, img.data(), img.size(), cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess && m->arrow) {
+        ArrowDev probe_a{};
+        std::vector<unsigned char> ai = camp::pack_arrow(m->ah, probe_a, nullptr);
+        e = cudaMalloc(&m->arrow_tables, ai.size());
+        if (e == cudaSuccess) {
+            ai = camp::pack_arrow(m->ah, m->ad, (const unsigned char *)m->arrow_tables);
+            e = cudaMemcpy(m->arrow_tables, ai.data(), ai.size(), cudaMemcpyHostToDevice);
+        }
+    }
     if (e != cudaSuccess) {
         if (m->dev_tables) cudaFree(m->dev_tables);
+        if (m->arrow_tables) cudaFree(m->arrow_tables);
         delete m;
         return report(e == cudaErrorMemoryAllocation ? CAMP_E_NOMEM : CAMP_E_CUDA,
                       std::string("loading tables: ") + cudaGetErrorString(e));
@@ -198,6 +246,7 @@ void camp_mech_free(camp_mech *m) {
     cudaGetDevice(&prev);
     cudaSetDevice(m->device);
     if (m->dev_tables) cudaFree(m->dev_tables);
+    if (m->arrow_tables) cudaFree(m->arrow_tables);
     if (m->own_ws) cudaFree(m->own_ws);
     if (m->stage) cudaFree(m->stage);
     if (prev >= 0) cudaSetDevice(prev);
@@ -226,11 +275,51 @@ int camp_mech_info_get(const camp_mech *m, camp_mech_info *o) {
     o->env_rh = h.rh_slot;
     o->n_electrolytes = (int32_t)h.el_phase.size();
     o->model_forcing = h.model_forcing;
+    if (m->arrow) {  // the full mechanism from its one-particle template
+        const camp::ArrowHost &a = m->ah;
+        long long gg = 0;  // gas-gas non-zeros of the template's pattern
+        for (int i = 0; i < a.n_g; i++)
+            for (int q = h.rowptr[i]; q < h.rowptr[i + 1]; q++) gg += h.colidx[q] < a.n_g;
+        o->n_species = m->n;
+        o->n_rxn = a.Rg + a.P * a.Rp;
+        o->n_env = m->n_env;
+        o->n_sections = a.P;
+        o->nnz_jac = (int32_t)std::min<long long>(0x7fffffff, gg + (long long)a.P * ((long long)h.colidx.size() - gg));
+        const long long blk = (long long)a.n_phi * a.n_phi + 2LL * a.n_phi * a.n_c;
+        o->lu_storage = (int32_t)std::min<long long>(0x7fffffff, (long long)a.P * blk + (long long)a.n_g * a.n_g);
+        o->nnz_lu = o->lu_storage;
+        o->rxn_map_len = 0;
+        o->dense_block = a.n_g;
+        o->smem_per_cell_mixed = o->smem_per_cell_fp64 = 0;
+        o->factor_updates = a.flops_factor / 2;
+        o->flops_forcing = a.flops_forcing;
+        o->flops_jacobian = a.flops_jacobian;
+        o->flops_factor = a.flops_factor;
+        o->flops_solve = a.flops_solve;
+        o->model_forcing = a.model_forcing;
+    }
     return CAMP_OK;
 }
 
 int camp_mech_species_index(const camp_mech *m, const char *name) {
     if (!m || !name) return -1;
+    if (m->arrow) {  // gas species by name; particle species as bin<p>.<name>
+        const std::string s(name);
+        for (int i = 0; i < m->ah.n_g; i++)
+            if (m->h.species[i] == s) return i;
+        const size_t dot = s.find('.');
+        if (s.compare(0, 3, "bin") != 0 || dot == std::string::npos || dot == 3) return -1;
+        long long p = 0;
+        for (size_t k = 3; k < dot; k++) {
+            if (s[k] < '0' || s[k] > '9') return -1;
+            p = p * 10 + (s[k] - '0');
+            if (p >= m->ah.P) return -1;
+        }
+        const std::string ph = "bin0" + s.substr(dot);
+        for (int j = 0; j < m->ah.n_phi; j++)
+            if (m->h.species[m->ah.n_g + j] == ph) return (int)(m->ah.n_g + p * m->ah.n_phi + j);
+        return -1;
+    }
     for (int i = 0; i < m->h.n; i++)
         if (m->h.species[i] == name) return i;
     return -1;
@@ -240,6 +329,8 @@ int camp_mech_structure(const camp_mech *m, int32_t *rowptr, int32_t *colidx, in
                         int32_t *perm, int32_t *lu_rowptr, int32_t *lu_colidx, int32_t *level_fwd,
                         int32_t *level_bwd) {
     if (!m) return fail(CAMP_E_INVAL, "NULL mechanism");
+    if (m->arrow)
+        return fail(CAMP_E_UNSUPPORTED, "the block-arrow form keeps one particle's structure, not a species-level one");
     const camp::HostMech &h = m->h;
     auto cp = [](int32_t *dst, const std::vector<int> &v) {
         if (dst) std::copy(v.begin(), v.end(), dst);
@@ -269,6 +360,53 @@ void camp_solve_opts_default(camp_solve_opts *o, int variant) {
 
 size_t camp_workspace_bytes(void) { return 256; }
 
+// The block-arrow form: one cell per cluster; the per-cell rows live in
+// scratch allocated stream-ordered for this call (concurrent calls on other
+// streams get their own).
+static int arrow_solve(camp_mech *m, int64_t n_cells, double *state, const double *env, double dt, int32_t n_outer,
+                       double *traj, double rtol, const double *atol, int32_t atol_len, int32_t *status,
+                       const camp_solve_opts &o, cudaStream_t s) {
+    const int lu = o.variant == CAMP_VARIANT_MIXED ? 4 : 8;
+    const int cl = o.cells_per_block > 0 ? o.cells_per_block : kArrowCluster;
+    int ci = -1;
+    for (int k = 0; k < 5; k++)
+        if (cl == (1 << k)) ci = k;
+    if (ci < 0) return fail(CAMP_E_INVAL, "a block-arrow cluster holds 1, 2, 4, 8 or 16 CTAs");
+    int &ncl = m->arrow_clusters[lu == 4 ? 0 : 1][ci];
+    if (ncl == 0) {
+        std::lock_guard<std::mutex> lk(m->mu);
+        int n = 0;
+        CUDA_TRY(camp_arrow_max_clusters(lu, cl, &n));
+        if (n < 1) return fail(CAMP_E_UNSUPPORTED, "a block-arrow cluster does not fit on the device");
+        ncl = n;
+    }
+    const long long clusters = std::min<long long>(ncl, n_cells);
+    const size_t cell_bytes = camp_arrow_cell_bytes(m->ad, lu);
+    SolveArgs a;
+    a.n_cells = n_cells;
+    a.state = state;
+    a.env = env;
+    a.dt = dt;
+    a.rtol = rtol;
+    a.atol = atol;
+    a.atol_len = atol_len;
+    a.status = status;
+    a.stats = o.stats;
+    a.step = o.step;
+    a.max_steps = o.max_steps;
+    a.hmin_frac = o.hmin_frac;
+    a.cpb = 1;
+    a.queue = nullptr;
+    a.n_outer = n_outer;
+    a.traj = traj;
+    void *scratch = nullptr;
+    CUDA_TRY(cudaMallocAsync(&scratch, (size_t)clusters * cell_bytes, s));
+    cudaError_t e = camp_arrow_launch(m->dm, m->ad, a, lu, (char *)scratch, cell_bytes, (int)clusters, cl, s);
+    cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return fail(CAMP_E_CUDA, std::string("block-arrow launch: ") + cudaGetErrorString(e));
+    return CAMP_OK;
+}
+
 static int solve_impl(const camp_mech *mc, int64_t n_cells, double *state, const double *env, double dt,
                       int32_t n_outer, double *traj, double rtol, const double *atol, int32_t atol_len,
                       int32_t *status, const camp_solve_opts *opts, void *stream) {
@@ -280,7 +418,7 @@ static int solve_impl(const camp_mech *mc, int64_t n_cells, double *state, const
     if (!state || !env || !atol || !status) return fail(CAMP_E_INVAL, "NULL array");
     if (!(dt > 0.0) || !(dt < 1e300)) return fail(CAMP_E_INVAL, "dt must be positive and finite");
     if (!(rtol > 0.0) || !(rtol < 1.0)) return fail(CAMP_E_INVAL, "rtol must be in (0, 1)");
-    if (atol_len != 1 && atol_len != m->h.n) return fail(CAMP_E_INVAL, "atol_len must be 1 or n_species");
+    if (atol_len != 1 && atol_len != m->n) return fail(CAMP_E_INVAL, "atol_len must be 1 or n_species");
     camp_solve_opts o;
     camp_solve_opts_default(&o, opts ? opts->variant : CAMP_VARIANT_MIXED);
     if (opts) o = *opts;
@@ -289,6 +427,8 @@ static int solve_impl(const camp_mech *mc, int64_t n_cells, double *state, const
     if (o.max_steps <= 0) o.max_steps = 10000;
     if (!(o.hmin_frac > 0.0)) o.hmin_frac = 1e-10;
     if (int rc = check_device(m)) return rc;
+    if (m->arrow) return arrow_solve(m, n_cells, state, env, dt, n_outer, traj, rtol, atol, atol_len, status, o,
+                                     (cudaStream_t)stream);
 
     const bool f32 = o.variant == CAMP_VARIANT_MIXED;
     const int smem_cell = camp_cell_smem_bytes(m->dm, f32 ? 4 : 8);
@@ -391,9 +531,9 @@ int camp_solve_host(const camp_mech *mc, int64_t n_cells, double *state, const d
     if (!m) return fail(CAMP_E_INVAL, "NULL mechanism");
     if (n_cells <= 0) return n_cells == 0 ? CAMP_OK : fail(CAMP_E_INVAL, "n_cells < 0");
     if (!state || !env || !atol || !status) return fail(CAMP_E_INVAL, "NULL array");
-    if (atol_len != 1 && atol_len != m->h.n) return fail(CAMP_E_INVAL, "atol_len must be 1 or n_species");
+    if (atol_len != 1 && atol_len != m->n) return fail(CAMP_E_INVAL, "atol_len must be 1 or n_species");
     if (int rc = check_device(m)) return rc;
-    const size_t n = m->h.n, ne = m->h.n_env;
+    const size_t n = m->n, ne = m->n_env;
     const size_t b_state = (size_t)n_cells * n * 8, b_env = (size_t)n_cells * ne * 8;
     const size_t b_stat = ((size_t)n_cells * 4 + 15) & ~(size_t)15, b_atol = (n * 8 + 15) & ~(size_t)15;
     const size_t b_stats = (size_t)n_cells * 4 * CAMP_NSTATS;
@@ -452,7 +592,10 @@ int camp_solve_batch(const camp_group *groups, int32_t n_groups, double dt, doub
     for (int g = 0; g < n_groups; g++) {
         if (!groups[g].mech) return fail(CAMP_E_INVAL, "NULL mechanism in group");
         const camp::HostMech &h = groups[g].mech->h;
-        work[g] = (double)(h.flops_forcing + h.flops_solve + 20 * h.n);
+        work[g] = groups[g].mech->arrow
+                      ? (double)(groups[g].mech->ah.flops_forcing + groups[g].mech->ah.flops_solve +
+                                 20LL * groups[g].mech->n)
+                      : (double)(h.flops_forcing + h.flops_solve + 20 * h.n);
         order[g] = g;
     }
     std::sort(order, order + n_groups, [&](int a, int b) { return work[a] > work[b]; });
@@ -514,12 +657,12 @@ int camp_solve_batch_host(const camp_group *groups, int32_t n_groups, double dt,
         if (gr.n_cells < 0) return fail(CAMP_E_INVAL, "n_cells < 0");
         if (gr.n_cells > 0 && (!gr.state || !gr.env || !gr.atol || !gr.status))
             return fail(CAMP_E_INVAL, "NULL array in group");
-        if (gr.atol_len != 1 && gr.atol_len != gr.mech->h.n) return fail(CAMP_E_INVAL, "atol_len must be 1 or n_species");
+        if (gr.atol_len != 1 && gr.atol_len != gr.mech->n) return fail(CAMP_E_INVAL, "atol_len must be 1 or n_species");
         if (int rc = check_device(gr.mech)) return rc;
         const size_t C = (size_t)gr.n_cells;
         Part &p = part[g];
-        p.state = need; need += al(C * gr.mech->h.n * 8);
-        p.env = need; need += al(C * gr.mech->h.n_env * 8);
+        p.state = need; need += al(C * gr.mech->n * 8);
+        p.env = need; need += al(C * gr.mech->n_env * 8);
         p.atol = need; need += al((size_t)gr.atol_len * 8);
         p.status = need; need += al(C * 4);
         p.stats = need; need += gr.stats ? al(C * 4 * CAMP_NSTATS) : 0;
@@ -556,9 +699,9 @@ int camp_solve_batch_host(const camp_group *groups, int32_t n_groups, double dt,
         dg[g].step = gr.step ? (double *)(base + p.step) : nullptr;
         dg[g].workspace = base + p.ws;
         if (C == 0) continue;
-        cudaError_t e = cudaMemcpyAsync(dg[g].state, gr.state, C * gr.mech->h.n * 8, cudaMemcpyHostToDevice, s);
+        cudaError_t e = cudaMemcpyAsync(dg[g].state, gr.state, C * gr.mech->n * 8, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync((void *)dg[g].env, gr.env, C * gr.mech->h.n_env * 8, cudaMemcpyHostToDevice, s);
+            e = cudaMemcpyAsync((void *)dg[g].env, gr.env, C * gr.mech->n_env * 8, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync((void *)dg[g].atol, gr.atol, (size_t)gr.atol_len * 8, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess && gr.step) e = cudaMemcpyAsync(dg[g].step, gr.step, C * 8, cudaMemcpyHostToDevice, s);
@@ -571,7 +714,7 @@ int camp_solve_batch_host(const camp_group *groups, int32_t n_groups, double dt,
         const camp_group &gr = groups[g];
         const size_t C = (size_t)gr.n_cells;
         if (C == 0) continue;
-        cudaError_t e = cudaMemcpyAsync(gr.state, dg[g].state, C * gr.mech->h.n * 8, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaMemcpyAsync(gr.state, dg[g].state, C * gr.mech->n * 8, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(gr.status, dg[g].status, C * 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && gr.stats)
             e = cudaMemcpyAsync(gr.stats, dg[g].stats, C * 4 * CAMP_NSTATS, cudaMemcpyDeviceToHost, s);
@@ -589,6 +732,7 @@ int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const doub
     if (!m || n_cells <= 0 || !state || !env || !atol) return fail(CAMP_E_INVAL, "bad argument");
     if (variant != CAMP_VARIANT_MIXED && variant != CAMP_VARIANT_FP64) return fail(CAMP_E_INVAL, "unknown variant");
     if (int rc = check_device(m)) return rc;
+    if (m->arrow) return fail(CAMP_E_UNSUPPORTED, "the block-arrow form has one launch shape");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = (size_t)n_cells * m->h.n * 8;
     double *work = nullptr;
@@ -640,6 +784,7 @@ int camp_rate_constants(const camp_mech *m, int64_t n_cells, const double *env, 
     if (!m || n_cells < 0 || (n_cells && (!env || !kf || !kr))) return fail(CAMP_E_INVAL, "bad argument");
     if (!n_cells) return CAMP_OK;
     if (int rc = check_device(m)) return rc;
+    if (m->arrow) return fail(CAMP_E_UNSUPPORTED, "the block-arrow form keeps rate constants per particle inside the solve");
     CUDA_TRY(camp_launch_rates(m->dm, n_cells, env, kf, kr, (cudaStream_t)stream));
     return CAMP_OK;
 }
@@ -650,6 +795,10 @@ int camp_forcing(const camp_mech *m, int64_t n_cells, const double *state, const
     if (!n_cells) return CAMP_OK;
     if (n_cells > 0x7fffffffLL) return fail(CAMP_E_INVAL, "too many cells");
     if (int rc = check_device(m)) return rc;
+    if (m->arrow) {
+        CUDA_TRY(camp_arrow_forcing(m->dm, m->ad, n_cells, state, env, f, (cudaStream_t)stream));
+        return CAMP_OK;
+    }
     CUDA_TRY(camp_launch_forcing(m->dm, n_cells, state, env, f, (cudaStream_t)stream));
     return CAMP_OK;
 }
@@ -661,6 +810,7 @@ int camp_jacobian(const camp_mech *m, int64_t n_cells, const double *state, cons
     if (!n_cells) return CAMP_OK;
     if (n_cells > 0x7fffffffLL) return fail(CAMP_E_INVAL, "too many cells");
     if (int rc = check_device(m)) return rc;
+    if (m->arrow) return fail(CAMP_E_UNSUPPORTED, "the block-arrow form assembles and factors inside the solve");
     cudaStream_t s = (cudaStream_t)stream;
     if (m->dm.n_wsec > 0)
         CUDA_TRY(variant == CAMP_VARIANT_MIXED ? camp_launch_jacobian_f32w(m->dm, n_cells, state, env, jac, s)
@@ -680,6 +830,7 @@ int camp_lu_solve(const camp_mech *m, int64_t n_cells, const double *state, cons
     if (!n_cells) return CAMP_OK;
     if (n_cells > 0x7fffffffLL) return fail(CAMP_E_INVAL, "too many cells");
     if (int rc = check_device(m)) return rc;
+    if (m->arrow) return fail(CAMP_E_UNSUPPORTED, "the block-arrow form assembles and factors inside the solve");
     cudaStream_t s = (cudaStream_t)stream;
     if (m->dm.n_wsec > 0)
         CUDA_TRY(variant == CAMP_VARIANT_MIXED

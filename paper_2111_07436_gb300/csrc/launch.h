@@ -8,6 +8,8 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include "camp.h"
+
 // A named range on the profiler timeline for the life of a scope (NVTX;
 // free when no profiler is attached)
 struct CampRange {
@@ -94,6 +96,10 @@ cudaError_t camp_arrow_launch(const DevMech &mt, const ArrowDev &a, const SolveA
                               size_t cell_bytes, int n_clusters, int cl_size, cudaStream_t st);
 cudaError_t camp_arrow_forcing(const DevMech &mt, const ArrowDev &a, long long n_cells, const double *state,
                                const double *env, double *f, cudaStream_t st);
+
+// true when camp_solve needs device scratch beyond its arguments and the work
+// counter (the block-arrow form's per-cell rows)
+bool camp_mech_needs_scratch(const camp_mech *m);
 
 // Record an error message for camp_last_error() and return `code`.
 int camp_record_error(int code, const char *msg);

@@ -1264,6 +1264,7 @@ ArrowHost build_arrow(const HostMech &t, int P) {
     }
     a.Rg = (int)a.grec.size() / 12;
     a.Rp = (int)a.prec.size() / 12;
+    if (a.Rg > 64) throw std::runtime_error("block-arrow form: more than 64 gas processes");
     a.n_c = (int)a.coupled.size();
     if (a.n_c > CAMP_ARROW_MAX_C) throw std::runtime_error("block-arrow form: a particle exchanges with more than 8 gas species");
     // gas rows: the gas processes that change each gas species

@@ -28,6 +28,9 @@ extern "C" int camp_solve_host_static(const camp_mech *m, int64_t n_cells, doubl
                                       void *stream) {
     camp_mech_info inf;
     if (!m || camp_mech_info_get(m, &inf) != CAMP_OK) return camp_record_error(CAMP_E_INVAL, "NULL mechanism");
+    if (camp_mech_needs_scratch(m))
+        return camp_record_error(CAMP_E_UNSUPPORTED, "a block-arrow (particle-resolved) mechanism needs per-cell scratch; "
+                                                     "use camp_solve_host");
     if (n_cells < 0) return camp_record_error(CAMP_E_INVAL, "n_cells < 0");
     if (n_cells == 0) return CAMP_OK;
     if (!state || !env || !atol || !status) return camp_record_error(CAMP_E_INVAL, "NULL array");

@@ -607,7 +607,8 @@ def serving_requests(n_requests=2000, seed=205, gas_share=0.7, cells_lo=256, cel
 def workload(k: int) -> Workload:
     """k = 1..3: the single-mechanism workloads (sizes in the docstrings);
     k = 6: the particle-resolved workload; k = 7: the water-parameter
-    workload."""
+    workload; k = 8: particle-resolved cells at the paper's 10^4
+    computational particles (70018 species; the block-arrow solve)."""
     if k == 1:
         return Workload("small-gas 1 cell, 60 x 60 s", small_gas_mechanism(), 1, 60.0, 60,
                         1e-4, 1e-5, 201, dict(T=298.0, P=101300.0, sza=False))
@@ -623,4 +624,7 @@ def workload(k: int) -> Workload:
     if k == 7:  # aerosol water as a parameter of the state
         return Workload("multiphase-water-240 (ZSR water parameter) 4096 cells, 300 s",
                         water_mechanism(), 4096, 300.0, 1, 1e-4, 1e-5, 207, {})
+    if k == 8:  # the paper's particle count (Sect. 4.1)
+        return Workload("particle-resolved 10^4 particles (70018 species) 152 cells, 180 s",
+                        particle_resolved_mechanism(10000), 152, 180.0, 1, 1e-4, 1e-5, 208, {})
     raise ValueError(k)

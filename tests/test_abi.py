@@ -81,3 +81,33 @@ def test_long_rows_keep_their_partial_sums_within_budget():
     for n_particles, limit in ((40, 30000), (100, 60000), (160, 75000)):
         inf = camp.Mechanism(json.dumps(M.water_particles_mechanism(n_particles)), device=False).info
         assert inf.smem_per_cell_mixed < limit, (n_particles, inf.smem_per_cell_mixed)
+
+
+def test_block_arrow_form_of_a_particle_resolved_mechanism():
+    """A particle-resolved mechanism takes the block-arrow form when it asks
+    for it or exceeds one block (2048 species): same sizes as the generic
+    compile where both exist, species looked up as gas names and
+    bin<p>.<name>, and a clear refusal of what the form does not keep."""
+    from paper_2111_07436_gb300 import workloads as w
+    mj = w.particle_resolved_mechanism(40)
+    generic = camp.Mechanism(json.dumps(mj), device=False)
+    ma = json.loads(json.dumps(mj))
+    ma["aerosol"]["solver"] = "block_arrow"
+    arrow = camp.Mechanism(json.dumps(ma), device=False)
+    for k in ("n_species", "n_rxn", "n_env", "n_sections", "nnz_jac"):
+        assert getattr(arrow.info, k) == getattr(generic.info, k), k
+    names = w.layout(mj).species
+    for i in (0, 17, 18, 100, len(names) - 1):
+        assert arrow.species_index(names[i]) == i == generic.species_index(names[i])
+    assert arrow.species_index("bin40.SOA1") == -1 and arrow.species_index("binx.SOA1") == -1
+    with pytest.raises(camp.CampError):
+        arrow.structure()
+    # the paper's 10^4 particles: beyond one block, so the block-arrow form
+    big = camp.Mechanism(json.dumps(w.particle_resolved_mechanism(10000)), device=False)
+    assert big.info.n_species == 18 + 7 * 10000 and big.info.n_env == big.info.n_env
+    assert big.species_index("bin9999.OLIG") == 18 + 7 * 9999 + 6
+    # a water parameter is not part of the block-arrow form
+    mw = json.loads(json.dumps(ma))
+    mw["parameters"] = [{"type": "ZSR_AEROSOL_WATER", "electrolytes": [{"species": "SULF", "Y": [1.0]}]}]
+    with pytest.raises(camp.CampError):
+        camp.Mechanism(json.dumps(mw), device=False)
