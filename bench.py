@@ -66,6 +66,8 @@ def args():
     p.add_argument("--sample", type=int, default=4096, help="uneven: cells of the stratified oracle sample")
     p.add_argument("--requests", type=int, default=2000, help="serving: number of chunk requests")
     p.add_argument("--load", type=float, default=0.8, help="serving: offered load / measured capacity")
+    p.add_argument("--ablation", action="store_true",
+                   help="uneven: also time one queue on the 232-species superset mechanism")
     return p.parse_args()
 
 
@@ -426,6 +428,37 @@ def bench_uneven(a):
     torch.cuda.synchronize()
     k_ms = sum(e0.elapsed_time(e1) for e0, e1 in kt[1:]) / (len(kt) - 1)
 
+    # ablation: every cell in one persistent queue on the superset (232-species)
+    # mechanism, the gas-only cells with dry sections (L = 0: their aqueous
+    # species frozen)
+    ablation = None
+    if a.ablation:
+        (mg, yg_, eg_), (mm, ym_, em_) = groups
+        n_sec = 3 * w.layout(mm).n_sections
+        ys = np.concatenate([np.concatenate([yg_, np.zeros((len(yg_), ym_.shape[1] - yg_.shape[1]))], axis=1), ym_])
+        dry = np.zeros((len(eg_), n_sec))
+        dry[:, 0::3], dry[:, 1::3] = w.SECTION_RADII[None, :], 1e6
+        es = np.concatenate([np.concatenate([eg_, dry], axis=1), em_])
+        gsup = G[1]["mech"]
+        ys_d, es_d = torch.tensor(ys, device=dev), torch.tensor(es, device=dev)
+        st_s = torch.empty(len(ys), dtype=torch.int32, device=dev)
+        at = []
+        for i in range(3):
+            flush.zero_()
+            yw = ys_d.clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gsup.solve(yw, es_d, dt, rtol, G[1]["atol"], status=st_s, variant=camp.VARIANT_MIXED, persistent=True,
+                       workspace=G[1]["workspace"], stream=stream)
+            e1.record(stream)
+            at.append((e0, e1))
+        torch.cuda.synchronize()
+        ams = min(e0.elapsed_time(e1) for e0, e1 in at[1:])
+        ablation = {"superset_single_queue": {"value": n_cells / (ams / 1e3), "ms_per_step": ams,
+                                              "ok_cells": int((st_s == 0).sum().item()),
+                                              "form": "mixed persistent, all cells on the 232-species mechanism"}}
+        del ys_d, es_d
+
     # end to end: the host-buffer call (pinned host arrays, copies timed)
     e2e = None
     if not a.no_e2e:
@@ -497,6 +530,8 @@ def bench_uneven(a):
            "plain_fp64": plain, "mixed_over_plain": (value / world / plain["value"]) if plain else None,
            "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err,
            "kernel_digest": digest, "clocks": clk.summary()}
+    if ablation:
+        out["ablation"] = ablation
     print(json.dumps(out))
 
 
@@ -788,6 +823,56 @@ def bench_serving(a):
                 "cell_steps_per_s": done_cells / wall, "wall_s": wall, "requests": n_req,
                 "cells": done_cells, "failed_cells": bad_cells[0]}
 
+    def run_host_model(variant, resident, n_sets=8, cells=16384, steps=8):
+        """A host model with n_sets domains of `cells` gas-72 cells, each
+        stepped `steps` times (dt 180 s, the temperature drifting a little
+        every step), all domains of a step submitted together: as resident
+        cell sets (only env crosses the bus) or as ordinary chunks (state in
+        and out every step)."""
+        srv = camp.Server(hbm_budget_bytes=80 << 30, max_inflight=8)
+        mj, gm = mechs["gas72"], gms["gas72"]
+        doms = []
+        for d in range(n_sets):
+            y, env = w.cells(mj, cells, seed=400 + d)
+            envs = [torch.from_numpy(env + np.array([1.0 * k] + [0.0] * (env.shape[1] - 1))).pin_memory()
+                    for k in range(steps)]
+            dom = {"envs": envs, "status": torch.zeros(cells, dtype=torch.int32).pin_memory()}
+            if resident:
+                dom["res"] = srv.resident(gm, y)
+            else:
+                dom["state"] = torch.from_numpy(y.copy()).pin_memory()
+            doms.append(dom)
+        lat = []
+        t0 = time.perf_counter()
+        for k in range(steps):
+            rids = []
+            for dom in doms:
+                if resident:
+                    rids.append(dom["res"].step(dom["envs"][k], 180.0, 1e-4, 1e-5, status=dom["status"],
+                                                variant=variant))
+                else:
+                    rids.append(srv.submit(gm, dom["state"], dom["envs"][k], 180.0, 1e-4, 1e-5, dom["status"],
+                                           variant=variant))
+            for rid in rids:
+                info = srv.wait(rid)
+                assert info["rc"] == 0, info
+                lat.append(info["t_done"] - info["t_submit"])
+        wall = time.perf_counter() - t0
+        bad = sum(int((dom["status"] != 0).sum()) for dom in doms)
+        if resident:
+            for dom in doms:
+                dom["res"].close()
+        srv.close()
+        lat = np.array(lat)
+        return {"cell_steps_per_s": n_sets * cells * steps / wall, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "domains": n_sets, "cells_per_domain": cells,
+                "steps": steps, "bus_bytes_per_step": n_sets * cells * (8 * gms["gas72"].n_env +
+                                                                      (4 if resident else 16 * gms["gas72"].n + 4)),
+                "failed_cells": bad}
+
+    host_model = {"resident": run_host_model(camp.VARIANT_MIXED, True),
+                  "copying": run_host_model(camp.VARIANT_MIXED, False)}
+
     # capacity of each form on the same first requests, everything at t = 0
     n_cap = min(200, a.requests)
     sat = run(camp.VARIANT_MIXED, 0, n_cap)
@@ -804,7 +889,8 @@ def bench_serving(a):
                                f"offered load {a.load:g} x measured capacity", "max_inflight": 8},
         "p50_ms": mixed["p50_ms"], "p99_ms": mixed["p99_ms"], "mixed": mixed, "saturation_mixed": sat,
         "plain_fp64": plain, "saturation_plain_fp64": sat_p,
-        "capacity_mixed_over_plain": sat["cell_steps_per_s"] / sat_p["cell_steps_per_s"]}))
+        "capacity_mixed_over_plain": sat["cell_steps_per_s"] / sat_p["cell_steps_per_s"],
+        "host_model": host_model}))
 
 
 if __name__ == "__main__":

@@ -327,9 +327,10 @@ int camp_solve_batch_host(const camp_group *groups, int32_t n_groups, double dt,
 
 /* ---- launch autotuning ------------------------------------------------------ */
 /* Time camp_solve on the given cells (device arrays, left unchanged) for
- * cells-per-block 1 to 4 and both grid mappings, and make the fastest the
- * mechanism's default for `variant` (used when opts.cells_per_block is 0 and
- * opts.persistent is -1).  Synchronous; allocates scratch for one copy of
+ * cells-per-block 1 to 4 and both grid mappings -- for a block-arrow
+ * (particle-resolved) mechanism, clusters of 2, 4, 8 and 16 CTAs -- and make
+ * the fastest the mechanism's default for `variant` (used when
+ * opts.cells_per_block is 0 and opts.persistent is -1).  Synchronous; allocates scratch for one copy of
  * the state.  *best_cpb / *best_persistent (may be NULL) receive the choice;
  * *ms_best the time of one solve with it. */
 int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const double *env, double dt,

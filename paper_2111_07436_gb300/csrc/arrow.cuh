@@ -777,7 +777,7 @@ __device__ int arrow_integrate_cell(const DevMech &mt, const ArrowDev &a, ArrowS
         if (cluster_sum1(sm, cl, nbad2, par) != 0.0) { status = ST_NONFINITE; break; }
 
         if (--qwait <= 0 && t < T) {
-            double eta_q = 1.0 / (C::pow_err(1.2, err2, q + 1) + 1e-6);
+            double eta_q = C::eta(1.2, err2, q + 1);
             double eta_m = 0.0, eta_p = 0.0;
             double s[2] = {0.0, 0.0};
             for (int p = lane; p < a.P; p += L)
@@ -797,11 +797,11 @@ __device__ int arrow_integrate_cell(const DevMech &mt, const ArrowDev &a, ArrowS
             if (q > 1) {
                 const double ce = mt.ecoef[q - 1] * mt.fact[q];
                 const double em2 = C::norm(ce, ce * ce, r2[0], a.n, 1.0 / (double)a.n);
-                eta_m = 1.0 / (C::pow_err(1.3, em2, q) + 1e-6);
+                eta_m = C::eta(1.3, em2, q);
             }
             if (q < QMAX && ep_valid) {
                 const double ep2 = C::norm(mt.ecoef[q + 1], mt.ecoef2[q + 1], r2[1], a.n, 1.0 / (double)a.n);
-                eta_p = 1.0 / (C::pow_err(1.4, ep2, q + 2) + 1e-6);
+                eta_p = C::eta(1.4, ep2, q + 2);
             }
             double eta = eta_q;
             int qn = q;

@@ -367,7 +367,8 @@ static int arrow_solve(camp_mech *m, int64_t n_cells, double *state, const doubl
                        double *traj, double rtol, const double *atol, int32_t atol_len, int32_t *status,
                        const camp_solve_opts &o, cudaStream_t s) {
     const int lu = o.variant == CAMP_VARIANT_MIXED ? 4 : 8;
-    const int cl = o.cells_per_block > 0 ? o.cells_per_block : kArrowCluster;
+    const int cl = o.cells_per_block > 0 ? o.cells_per_block
+                                         : (m->tuned_cpb[o.variant] > 0 ? m->tuned_cpb[o.variant] : kArrowCluster);
     int ci = -1;
     for (int k = 0; k < 5; k++)
         if (cl == (1 << k)) ci = k;
@@ -732,9 +733,8 @@ int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const doub
     if (!m || n_cells <= 0 || !state || !env || !atol) return fail(CAMP_E_INVAL, "bad argument");
     if (variant != CAMP_VARIANT_MIXED && variant != CAMP_VARIANT_FP64) return fail(CAMP_E_INVAL, "unknown variant");
     if (int rc = check_device(m)) return rc;
-    if (m->arrow) return fail(CAMP_E_UNSUPPORTED, "the block-arrow form has one launch shape");
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t bytes = (size_t)n_cells * m->h.n * 8;
+    const size_t bytes = (size_t)n_cells * m->n * 8;
     double *work = nullptr;
     int32_t *status = nullptr;
     CUDA_TRY(cudaMallocAsync((void **)&work, bytes, s));
@@ -742,18 +742,21 @@ int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const doub
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
-    const int cpbs[4] = {1, 2, 3, 4};
+    // the block-arrow form: CTAs per cluster 2, 4, 8, 16 (one launch shape
+    // otherwise); the others: cells per block 1-4 x static / persistent grid
+    const int cpbs[4] = {1, 2, 3, 4}, clusters[4] = {2, 4, 8, 16};
     float best = 1e30f;
     int bc = 1, bp = 1, rc = CAMP_OK;
-    for (int pers = 0; pers <= 1 && rc == CAMP_OK; pers++)
+    for (int pers = m->arrow ? 1 : 0; pers <= 1 && rc == CAMP_OK; pers++)
         for (int ci = 0; ci < 4 && rc == CAMP_OK; ci++) {
+            const int choice = m->arrow ? clusters[ci] : cpbs[ci];
             const int smem_cell = camp_cell_smem_bytes(m->dm, variant == CAMP_VARIANT_MIXED ? 4 : 8);
-            if (cpbs[ci] * smem_cell > kMaxSmem) continue;
-            if (cpbs[ci] > 1 && camp_group_size(m->h.n) > 32) continue;  // a block is one cell
+            if (!m->arrow && cpbs[ci] * smem_cell > kMaxSmem) continue;
+            if (!m->arrow && cpbs[ci] > 1 && camp_group_size(m->h.n) > 32) continue;  // a block is one cell
             camp_solve_opts o;
             camp_solve_opts_default(&o, variant);
             o.persistent = pers;
-            o.cells_per_block = cpbs[ci];
+            o.cells_per_block = choice;
             float ms = 0.f;
             for (int rep = 0; rep < 2 && rc == CAMP_OK; rep++) {  // first run warms up
                 if (cudaMemcpyAsync(work, state, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) rc = CAMP_E_CUDA;
@@ -763,7 +766,7 @@ int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const doub
                 if (cudaEventSynchronize(e1) != cudaSuccess) rc = CAMP_E_CUDA;
                 cudaEventElapsedTime(&ms, e0, e1);
             }
-            if (rc == CAMP_OK && ms < best) { best = ms; bc = cpbs[ci]; bp = pers; }
+            if (rc == CAMP_OK && ms < best) { best = ms; bc = choice; bp = pers; }
         }
     cudaFreeAsync(work, s);
     cudaFreeAsync(status, s);

@@ -1241,10 +1241,11 @@ struct Ctl {
         if constexpr (EXACT) return c * sqrt(s / (double)n);
         else return c2 * (s * rn);
     }
-    // (k err)^(1/p)
-    static __device__ __forceinline__ double pow_err(double k, double v, int p) {
-        if constexpr (EXACT) return pow(k * v, 1.0 / (double)p);
-        else return (double)ctl_powf((float)(k * k) * (float)v, 0.5f / (float)p);
+    // the step-size factor of order selection, 1 / ((k err)^(1/p) + 1e-6)
+    // (the mixed form entirely in FP32: no FP64 division)
+    static __device__ __forceinline__ double eta(double k, double v, int p) {
+        if constexpr (EXACT) return 1.0 / (pow(k * v, 1.0 / (double)p) + 1e-6);
+        else return (double)(1.0f / (ctl_powf((float)(k * k) * (float)v, 0.5f / (float)p) + 1e-6f));
     }
     // 0.9 err^(-1/p): the step factor after an error-test failure
     static __device__ __forceinline__ double fail_eta(double v, int p) {
@@ -1521,7 +1522,7 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
 
         if (--qwait <= 0 && t < T) {
             // eta = 1 / ((c err)^(1/(p+1)) + 1e-6), from the squared norms
-            double eta_q = 1.0 / (C::pow_err(1.2, err2, q + 1) + 1e-6);
+            double eta_q = C::eta(1.2, err2, q + 1);
             double eta_m = 0.0, eta_p = 0.0;
             if (q > 1) {
                 double zs = 0.0;
@@ -1534,14 +1535,14 @@ __device__ int integrate_cell(const DevMech &m, const CellPtr<LT> &c, double *__
                 }
                 const double ce = m.ecoef[q - 1] * m.fact[q];
                 const double em2 = C::norm(ce, ce * ce, gsum<G>(zs, gm), n, m.rn);
-                eta_m = 1.0 / (C::pow_err(1.3, em2, q) + 1e-6);
+                eta_m = C::eta(1.3, em2, q);
             }
             if (q < QMAX && ep_valid) {
                 double ds = 0.0;
 #pragma unroll
                 for (int s = 0; s < NPL; s++) { double a = (e[s] - ep[s]) * w[s]; ds += a * a; }
                 const double ep2 = C::norm(m.ecoef[q + 1], m.ecoef2[q + 1], gsum<G>(ds, gm), n, m.rn);
-                eta_p = 1.0 / (C::pow_err(1.4, ep2, q + 2) + 1e-6);
+                eta_p = C::eta(1.4, ep2, q + 2);
             }
             double eta = eta_q;
             int qn = q;

@@ -220,3 +220,20 @@ def test_block_arrow_edge_cases_and_sequence(cuda, variant):
     om.solve(y1, env1, 180.0, 1e-4, 1e-5, step=hso)
     if variant == camp.VARIANT_FP64:  # the same step sequence, hence the same carried step
         assert np.allclose(hs.cpu().numpy(), hso, rtol=1e-9)
+
+
+def test_autotune_picks_a_cluster_size(cuda):
+    """camp_autotune on a block-arrow mechanism times clusters of 2, 4, 8 and
+    16 CTAs; later solves with the default launch use the choice (the same
+    bits as naming it)."""
+    import torch
+    mj = _arrow(2000)
+    gm = camp.Mechanism(json.dumps(mj))
+    y0, env = w.cells(mj, 12, seed=21)
+    ty, te = torch.tensor(y0, device="cuda"), torch.tensor(env, device="cuda")
+    cl, pers, ms = gm.autotune(ty, te, 180.0, 1e-4, 1e-5)
+    assert cl in (2, 4, 8, 16) and pers == 1 and ms > 0
+    assert np.array_equal(ty.cpu().numpy(), y0)  # the cells are left unchanged
+    a, _ = _solve(gm, y0, env, camp.VARIANT_MIXED)
+    b, _ = _solve(gm, y0, env, camp.VARIANT_MIXED, cells_per_block=cl)
+    assert np.array_equal(a, b)
