@@ -42,11 +42,18 @@ WORKLOADS = {"small": 1, "gas72": 2, "multiphase232": 3, "uneven": 4, "serving":
 ORACLE_MAX_SPECIES = 4096
 FP64_PEAK_NOMINAL_GFLOPS = 1250.0  # GB300 dense FP64, nominal
 HBM_FALLBACK_GBS = 6800.0          # used only when the measured peaks file is absent
-# DRAM bytes (read + write) per cell of one mixed-form k_solve launch, from
-# one ncu capture of the same kernel on a smaller launch of the same
-# workload, valid only for the kernel sources whose digest is given (the
-# bench reports null traffic once the kernels have changed since).
-DRAM_BYTES_PER_CELL = {}
+# DRAM bytes (read + write) per cell of one mixed-form solve launch (k_solve;
+# k_arrow for particles10k), from one ncu capture of the same kernel on a
+# smaller launch of the same workload (uneven: 16384 cells, 14734 + 1650 per
+# group; gas72: 4096; multiphase232: 2048; particles10k: 19), scaled by the
+# cells of the timed launch.  Valid only for the kernel sources whose digest
+# is given: the bench reports null traffic once the kernels have changed.
+DRAM_BYTES_PER_CELL = {
+    "uneven": {"digest": "1ea91691eb313baf", "bytes_per_cell": [15286784 / 14734, 4542464 / 1650]},
+    "gas72": {"digest": "1ea91691eb313baf", "bytes_per_cell": [4180480 / 4096]},
+    "multiphase232": {"digest": "1ea91691eb313baf", "bytes_per_cell": [5732352 / 2048]},
+    "particles10k": {"digest": "1ea91691eb313baf", "bytes_per_cell": [(12.096362e9 + 6.474108e9) / 19]},
+}
 
 
 def args():
@@ -71,11 +78,18 @@ def args():
     return p.parse_args()
 
 
+# the sources the solve kernels and their device tables are built from (the
+# C ABI, server, no-alloc entry point and FMA probe are left out)
+KERNEL_SOURCES = ("arrow.cuh", "arrow.h", "cellsolve.cuh", "devmech.h", "kernels.cuh", "launch.h",
+                  "launch_impl.cuh", "mech.cpp", "mech.hpp", "solve_arrow.cu", "solve_f32.cu",
+                  "solve_f32w.cu", "solve_f64.cu", "solve_f64w.cu")
+
+
 def kernel_digest():
     """Digest of the kernel sources (the DRAM traffic table is tied to it)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2111_07436_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -209,34 +223,44 @@ def cost_models(info, st, lu_bytes, calls=1):
             "model_bytes": model_bytes, "counted_fp64": counted, "lu_flops": lu}
 
 
-def roofline(models, seconds, peak64, lu_dtype, traffic, kernel, per):
-    """The roofline object of the bench line: bound by the FP64 pipe
-    (achieved = cost-model FP64 flops / time against the measured FP64 FMA
-    rate), with the bytes model against the HBM peak beside it."""
+def roofline(models, seconds, peak64, lu_dtype, traffic, kernel, per, bound="alu"):
+    """The roofline object of the bench line.  bound "alu" (a cell's working
+    set stays on chip): achieved = cost-model FP64 flops / time against the
+    measured FP64 FMA rate, with the bytes model against the HBM peak beside
+    it.  bound "hbm" (the block-arrow form, whose per-particle data lives in
+    device memory): achieved = cost-model bytes / time against the measured
+    HBM copy rate, with the FP64 model beside it."""
     peaks, src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
     fl = sum(x["model_flops"] for x in models)
     by = sum(x["model_bytes"] for x in models)
     counted = sum(x["counted_fp64"] for x in models)
     lu = sum(x["lu_flops"] for x in models)
-    ach = fl / seconds / 1e9
-    return {"bound": "alu", "unit": "GFLOP/s (fp64)", "achieved": ach, "peak": peak64,
+    hbm_src = f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6800 GB/s"
+    bytes_model = "bytes per internal cell-step 16 (q+1) n + m (24 n + b nnzLU) + rho (2 b nnzLU + 8 R) + 24 n"
+    flops_model = "FP64 flops per internal cell-step m F + (q+1)^2 n/2 + 10 n"
+    fp64 = {"flops_per_launch": fl, "achieved_gflops": fl / seconds / 1e9, "peak_gflops": peak64,
             "peak_source": "measured FP64 FMA chains on this GPU (camp_probe_fma_rate)",
-            "frac": ach / peak64, "frac_of_nominal": ach / FP64_PEAK_NOMINAL_GFLOPS,
-            "traffic": traffic, "traffic_unit": "DRAM bytes (read + write) per launch, from ncu",
-            "kernel": kernel, "per": per,
-            "model": "FP64 flops per internal cell-step m F + (q+1)^2 n/2 + 10 n",
-            "fp64_flops_per_launch": fl,
-            "hbm_model": {"bytes_per_launch": by, "achieved_gbs": by / seconds / 1e9, "peak_gbs": hbm,
-                          "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
-                          else "fallback 6800 GB/s", "frac": by / seconds / 1e9 / hbm,
-                          "model": "bytes per internal cell-step 16 (q+1) n + m (24 n + b nnzLU) "
-                                   "+ rho (2 b nnzLU + 8 R) + 24 n"},
-            "fp64_counted": {"flops_per_launch": counted, "achieved": counted / seconds / 1e9,
-                             "frac": counted / seconds / 1e9 / peak64,
-                             "what": "the kernel's own FP64 steps: f evaluations, Newton updates, "
-                                     "Nordsieck prediction and correction, norms"},
-            "lu_flops_per_launch": lu, "lu_dtype": lu_dtype}
+            "frac": fl / seconds / 1e9 / peak64, "frac_of_nominal": fl / seconds / 1e9 / FP64_PEAK_NOMINAL_GFLOPS,
+            "model": flops_model}
+    mem = {"bytes_per_launch": by, "achieved_gbs": by / seconds / 1e9, "peak_gbs": hbm, "peak_source": hbm_src,
+           "frac": by / seconds / 1e9 / hbm, "model": bytes_model}
+    if bound == "hbm":
+        out = {"bound": "hbm", "unit": "GB/s", "achieved": mem["achieved_gbs"], "peak": hbm,
+               "peak_source": hbm_src, "frac": mem["frac"], "model": bytes_model, "bytes_per_launch": by,
+               "fp64_model": fp64}
+    else:
+        out = {"bound": "alu", "unit": "GFLOP/s (fp64)", "achieved": fp64["achieved_gflops"], "peak": peak64,
+               "peak_source": fp64["peak_source"], "frac": fp64["frac"], "frac_of_nominal": fp64["frac_of_nominal"],
+               "model": flops_model, "fp64_flops_per_launch": fl, "hbm_model": mem}
+    out.update({"traffic": traffic, "traffic_unit": "DRAM bytes (read + write) per launch, from ncu",
+                "kernel": kernel, "per": per,
+                "fp64_counted": {"flops_per_launch": counted, "achieved": counted / seconds / 1e9,
+                                 "frac": counted / seconds / 1e9 / peak64,
+                                 "what": "the kernel's own FP64 steps: f evaluations, Newton updates, "
+                                         "Nordsieck prediction and correction, norms"},
+                "lu_flops_per_launch": lu, "lu_dtype": lu_dtype})
+    return out
 
 
 # ----------------------------------------------------------------- oracle timing
@@ -341,8 +365,8 @@ def bench_uneven(a):
     dev = torch.device("cuda", torch.cuda.current_device())
     G = _groups_on_device(groups, dev)
     tuned = []
-    for g in G:  # autotune on a 4096-cell sample of each group
-        k = min(4096, g["y0"].shape[0])
+    for g in G:  # autotune on a 16384-cell sample of each group
+        k = min(16384, g["y0"].shape[0])
         tuned.append(g["mech"].autotune(g["y0"][:k].contiguous(), g["env"][:k].contiguous(), dt, rtol,
                                         g["atol"]))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -711,8 +735,11 @@ def bench_single(a):
     digest = kernel_digest()
     tr = DRAM_BYTES_PER_CELL.get(a.workload)
     traffic = tr["bytes_per_cell"][0] * C if tr and tr["digest"] == digest and variant == camp.VARIANT_MIXED else None
-    roof = roofline(models, ms / 1e3, peak64, "f32" if lu_b == 4 else "f64", traffic, "k_solve",
-                    "step (one launch per outer step), CUDA events on the launch stream")
+    arrow = bool(gm.info.block_arrow)
+    roof = roofline(models, ms / 1e3, peak64, "f32" if lu_b == 4 else "f64", traffic,
+                    "k_arrow" if arrow else "k_solve",
+                    "step (one launch per outer step), CUDA events on the launch stream",
+                    bound="hbm" if arrow else "alu")
     out = {"metric": metric, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64 state / f32 J+LU" if variant == camp.VARIANT_MIXED else "f64",

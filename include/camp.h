@@ -98,6 +98,10 @@ typedef struct {
                                f(y) in a per-process cost model that counts
                                one multiply per reactant factor and one add
                                per stoichiometric term */
+    int32_t block_arrow;    /* 1: the block-arrow form (particle-resolved; one
+                               cell per thread-block cluster, every particle's
+                               block eliminated into the gas block), 0: the
+                               cell kernels */
 } camp_mech_info;
 
 /*
@@ -330,9 +334,11 @@ int camp_solve_batch_host(const camp_group *groups, int32_t n_groups, double dt,
  * cells-per-block 1 to 4 and both grid mappings -- for a block-arrow
  * (particle-resolved) mechanism, clusters of 2, 4, 8 and 16 CTAs -- and make
  * the fastest the mechanism's default for `variant` (used when
- * opts.cells_per_block is 0 and opts.persistent is -1).  Synchronous; allocates scratch for one copy of
- * the state.  *best_cpb / *best_persistent (may be NULL) receive the choice;
- * *ms_best the time of one solve with it. */
+ * opts.cells_per_block is 0 and opts.persistent is -1).  One untimed solve
+ * comes first, then two sweeps over the candidates; each candidate is judged
+ * by the faster of its two times.  Synchronous; allocates scratch for one
+ * copy of the state.  *best_cpb / *best_persistent (may be NULL) receive the
+ * choice; *ms_best the time of one solve with it. */
 int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const double *env, double dt,
                   double rtol, const double *atol, int32_t atol_len, int32_t variant,
                   int32_t *best_cpb, int32_t *best_persistent, double *ms_best, void *stream);

@@ -37,7 +37,7 @@ class MechInfo(ctypes.Structure):
                 ("flops_forcing", ctypes.c_int64), ("flops_jacobian", ctypes.c_int64),
                 ("flops_factor", ctypes.c_int64), ("flops_solve", ctypes.c_int64),
                 ("env_rh", ctypes.c_int32), ("n_electrolytes", ctypes.c_int32),
-                ("model_forcing", ctypes.c_int64)]
+                ("model_forcing", ctypes.c_int64), ("block_arrow", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -96,6 +96,7 @@ def test_block_arrow_form_of_a_particle_resolved_mechanism():
     arrow = camp.Mechanism(json.dumps(ma), device=False)
     for k in ("n_species", "n_rxn", "n_env", "n_sections", "nnz_jac"):
         assert getattr(arrow.info, k) == getattr(generic.info, k), k
+    assert arrow.info.block_arrow == 1 and generic.info.block_arrow == 0
     names = w.layout(mj).species
     for i in (0, 17, 18, 100, len(names) - 1):
         assert arrow.species_index(names[i]) == i == generic.species_index(names[i])
@@ -104,7 +105,7 @@ def test_block_arrow_form_of_a_particle_resolved_mechanism():
         arrow.structure()
     # the paper's 10^4 particles: beyond one block, so the block-arrow form
     big = camp.Mechanism(json.dumps(w.particle_resolved_mechanism(10000)), device=False)
-    assert big.info.n_species == 18 + 7 * 10000 and big.info.n_env == big.info.n_env
+    assert big.info.n_species == 18 + 7 * 10000 and big.info.block_arrow == 1
     assert big.species_index("bin9999.OLIG") == 18 + 7 * 9999 + 6
     # a water parameter is not part of the block-arrow form
     mw = json.loads(json.dumps(ma))
