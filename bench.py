@@ -49,10 +49,10 @@ HBM_FALLBACK_GBS = 6800.0          # used only when the measured peaks file is a
 # cells of the timed launch.  Valid only for the kernel sources whose digest
 # is given: the bench reports null traffic once the kernels have changed.
 DRAM_BYTES_PER_CELL = {
-    "uneven": {"digest": "1ea91691eb313baf", "bytes_per_cell": [15286784 / 14734, 4542464 / 1650]},
-    "gas72": {"digest": "1ea91691eb313baf", "bytes_per_cell": [4180480 / 4096]},
-    "multiphase232": {"digest": "1ea91691eb313baf", "bytes_per_cell": [5732352 / 2048]},
-    "particles10k": {"digest": "1ea91691eb313baf", "bytes_per_cell": [(12.096362e9 + 6.474108e9) / 19]},
+    "uneven": {"digest": "8693fa7d311033d1", "bytes_per_cell": [15286784 / 14734, 4542464 / 1650]},
+    "gas72": {"digest": "8693fa7d311033d1", "bytes_per_cell": [4180480 / 4096]},
+    "multiphase232": {"digest": "8693fa7d311033d1", "bytes_per_cell": [5732352 / 2048]},
+    "particles10k": {"digest": "c4799824a576f732", "bytes_per_cell": [(12.096362e9 + 6.474108e9) / 19]},
 }
 
 
@@ -78,18 +78,22 @@ def args():
     return p.parse_args()
 
 
-# the sources the solve kernels and their device tables are built from (the
-# C ABI, server, no-alloc entry point and FMA probe are left out)
-KERNEL_SOURCES = ("arrow.cuh", "arrow.h", "cellsolve.cuh", "devmech.h", "kernels.cuh", "launch.h",
-                  "launch_impl.cuh", "mech.cpp", "mech.hpp", "solve_arrow.cu", "solve_f32.cu",
-                  "solve_f32w.cu", "solve_f64.cu", "solve_f64w.cu")
+# the sources each solve kernel and its device tables are built from (the C
+# ABI, server, no-alloc entry point and FMA probe are left out): k_solve
+# (cell) and k_arrow (block-arrow)
+KERNEL_SOURCES = {
+    "cell": ("arrow.h", "cellsolve.cuh", "devmech.h", "kernels.cuh", "launch.h", "launch_impl.cuh",
+             "mech.cpp", "mech.hpp", "solve_f32.cu", "solve_f32w.cu", "solve_f64.cu", "solve_f64w.cu"),
+    "arrow": ("arrow.cuh", "arrow.h", "cellsolve.cuh", "devmech.h", "launch.h", "mech.cpp", "mech.hpp",
+              "solve_arrow.cu"),
+}
 
 
-def kernel_digest():
-    """Digest of the kernel sources (the DRAM traffic table is tied to it)."""
+def kernel_digest(kind="cell"):
+    """Digest of one kernel's sources (the DRAM traffic table is tied to it)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2111_07436_gb300", "csrc")
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[kind]:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -732,10 +736,10 @@ def bench_single(a):
     peak64 = camp.probe_fma_rate(True)
     lu_b = 4 if variant == camp.VARIANT_MIXED else 8
     models = [cost_models(gm.info, counters, lu_b, wl.n_outer)]
-    digest = kernel_digest()
+    arrow = bool(gm.info.block_arrow)
+    digest = kernel_digest("arrow" if arrow else "cell")
     tr = DRAM_BYTES_PER_CELL.get(a.workload)
     traffic = tr["bytes_per_cell"][0] * C if tr and tr["digest"] == digest and variant == camp.VARIANT_MIXED else None
-    arrow = bool(gm.info.block_arrow)
     roof = roofline(models, ms / 1e3, peak64, "f32" if lu_b == 4 else "f64", traffic,
                     "k_arrow" if arrow else "k_solve",
                     "step (one launch per outer step), CUDA events on the launch stream",

@@ -66,6 +66,8 @@ def test_traffic_table_names_real_workloads_and_sources():
         assert all(b > 0 for b in entry["bytes_per_cell"])
     assert len(bench.DRAM_BYTES_PER_CELL["uneven"]["bytes_per_cell"]) == 2  # one per mechanism group
     csrc = os.path.join(bench.ROOT, "paper_2111_07436_gb300", "csrc")
-    for f in bench.KERNEL_SOURCES:
-        assert os.path.exists(os.path.join(csrc, f)), f
-    assert re.fullmatch(r"[0-9a-f]{16}", bench.kernel_digest())
+    for kind, files in bench.KERNEL_SOURCES.items():
+        for f in files:
+            assert os.path.exists(os.path.join(csrc, f)), f
+        assert re.fullmatch(r"[0-9a-f]{16}", bench.kernel_digest(kind))
+    assert bench.kernel_digest("cell") != bench.kernel_digest("arrow")
