@@ -52,7 +52,7 @@ DRAM_BYTES_PER_CELL = {
     "uneven": {"digest": "8693fa7d311033d1", "bytes_per_cell": [15286784 / 14734, 4542464 / 1650]},
     "gas72": {"digest": "8693fa7d311033d1", "bytes_per_cell": [4180480 / 4096]},
     "multiphase232": {"digest": "8693fa7d311033d1", "bytes_per_cell": [5732352 / 2048]},
-    "particles10k": {"digest": "c4799824a576f732", "bytes_per_cell": [(12.096362e9 + 6.474108e9) / 19]},
+    "particles10k": {"digest": "c58c6cacb25afe93", "bytes_per_cell": [(11722336768 + 6166715136) / 19]},
 }
 
 

@@ -590,7 +590,9 @@ __device__ int arrow_integrate_cell(const DevMech &mt, const ArrowDev &a, ArrowS
 
     while (t < T) {
         if (nst >= max_steps) { status = ST_MAXSTEPS; break; }
-        set_weights();
+        // the weights of this step: set before the loop for the first step,
+        // by the previous step's accept pass for the others (z0 is not
+        // changed between the two)
         int nef = 0, ncf = 0;
         bool last = false;
         double err2 = 0.0;
@@ -622,11 +624,10 @@ __device__ int arrow_integrate_cell(const DevMech &mt, const ArrowDev &a, ArrowS
                 jcur = true;
             }
             bool conv = false;
+            double esum = 0.0;  // sum of (e w)^2 after the latest iteration
             if (!lu_fail) {
                 double dprev2 = 0.0;
-                for (int p = lane; p < a.P; p += L)
-                    for (int i = 0; i < np; i++) E(i, p) = 0.0;
-                eg = 0.0;
+                eg = 0.0;  // the particles' e is read as zero in the first iteration
                 const LT scale = (gamma != gamma_lu)
                                      ? (LT)2 / ((LT)1 + to_lu<LT>(C::ratio(gamma, gamma_lu, rgamma_lu)))
                                      : (LT)1;
@@ -638,12 +639,12 @@ __device__ int arrow_integrate_cell(const DevMech &mt, const ArrowDev &a, ArrowS
                     for (int v = 0; v <= 2 * nc; v++) part[v] = 0.0;
                     double yl[ARROW_MAX_LOC], fl[ARROW_MAX_LOC];
                     for (int p = lane; p < a.P; p += L) {
-                        for (int i = 0; i < np; i++) yl[i] = Z(0, i, p) + 1.0 * E(i, p);
+                        for (int i = 0; i < np; i++) yl[i] = Z(0, i, p) + (it ? E(i, p) : 0.0);
                         for (int k = 0; k < nc; k++) yl[np + k] = sm.ygas[__ldg(a.coupled + k)];
                         arrow_particle_forcing(a, p, c.kfp, c.krp, yl, fl);
                         for (int i = 0; i < np; i++) {
                             part[2 * nc] += !finite_bits(fl[i]);
-                            X(i, p) = to_lu<LT>(-(E(i, p) - gamma * fl[i] + Z(1, i, p) * rl1));
+                            X(i, p) = to_lu<LT>(-((it ? E(i, p) : 0.0) - gamma * fl[i] + Z(1, i, p) * rl1));
                         }
                         for (int k = 0; k < nc; k++) part[k] += fl[np + k];
                         arrow_particle_forward<LT>(a, p, c.lu, c.xp, part + nc);
@@ -681,15 +682,20 @@ __device__ int arrow_integrate_cell(const DevMech &mt, const ArrowDev &a, ArrowS
                             if (tid < ng) *cl.map_shared_rank(&sm.xgas[tid], r) = sm.xs[tid];
                     }
                     cl.sync();
-                    // particles: backward substitution, the update and its norm
-                    double s2[2] = {0.0, red[2 * nc] + gnf};
+                    // particles: backward substitution, the update, its norm
+                    // and the weighted sum of squares of e (the error test's,
+                    // in the same order as a pass of its own would take)
+                    double s2[3] = {0.0, red[2 * nc] + gnf, 0.0};
                     for (int p = lane; p < a.P; p += L) {
                         arrow_particle_backward<LT>(a, p, c.lu, c.xp, sm.xgas);
                         for (int i = 0; i < np; i++) {
                             LT xl = X(i, p) * scale;
-                            E(i, p) += from_lu(xl);
-                            s2[0] += (double)upd_term(xl, Wt(i, p));
+                            const double en = (it ? E(i, p) : 0.0) + from_lu(xl), wv = Wt(i, p);
+                            E(i, p) = en;
+                            s2[0] += (double)upd_term(xl, wv);
                             s2[1] += !isfinite(xl);
+                            const double v = en * wv;
+                            s2[2] += v * v;
                         }
                     }
                     if (gas_own) {
@@ -697,9 +703,11 @@ __device__ int arrow_integrate_cell(const DevMech &mt, const ArrowDev &a, ArrowS
                         eg += from_lu(xl);
                         s2[0] += (double)upd_term(xl, wg);
                         s2[1] += !isfinite(xl);
+                        s2[2] += (eg * wg) * (eg * wg);
                     }
-                    double r2[2];
-                    cluster_sum(sm, cl, s2, 2, par, r2);
+                    double r2[3];
+                    cluster_sum(sm, cl, s2, 3, par, r2);
+                    esum = r2[2];
                     if (r2[1] != 0.0) break;  // non-finite forcing or update
                     // (the update's norm: summed in FP64 here; the mixed form
                     // compares squares, the FP64 form the norm itself)
@@ -726,13 +734,7 @@ __device__ int arrow_integrate_cell(const DevMech &mt, const ArrowDev &a, ArrowS
                 qwait = q + 1;
                 continue;
             }
-            {
-                double s = 0.0;
-                for (int p = lane; p < a.P; p += L)
-                    for (int i = 0; i < np; i++) { const double v = E(i, p) * Wt(i, p); s += v * v; }
-                if (gas_own) s += (eg * wg) * (eg * wg);
-                err2 = C::norm(mt.ecoef[q], mt.ecoef2[q], cluster_sum1(sm, cl, s, par), a.n, 1.0 / (double)a.n);
-            }
+            err2 = C::norm(mt.ecoef[q], mt.ecoef2[q], esum, a.n, 1.0 / (double)a.n);
             if (err2 > 1.0) {
                 retract(q);
                 st.errfail++;
@@ -759,41 +761,50 @@ __device__ int arrow_integrate_cell(const DevMech &mt, const ArrowDev &a, ArrowS
         }
         if (status != ST_OK) break;
 
-        // accept: z += l (x) e
-        double nbad2 = 0.0;
+        // accept: z += l (x) e.  The same pass keeps e as the next step's
+        // previous e (ep), forms -- when an order selection follows -- its
+        // two weighted sums of squares (z_q after the update, e - ep) in the
+        // order a pass of their own would take, and then sets the next
+        // step's weights from the new z0.
+        const double t_new = last ? T : t + h;
+        const bool select = qwait - 1 <= 0 && t_new < T;
+        double acc[3] = {0.0, 0.0, 0.0};  // non-finite count, sum (z_q w)^2, sum ((e - ep) w)^2
         for (int p = lane; p < a.P; p += L)
             for (int i = 0; i < np; i++) {
                 const double ev = E(i, p);
                 for (int j = 0; j <= q; j++) Z(j, i, p) += mt.lcoef[q][j] * ev;
-                nbad2 += !finite_bits(Z(0, i, p));
+                acc[0] += !finite_bits(Z(0, i, p));
+                if (select) {
+                    const double w = Wt(i, p);
+                    const double zq = Z(q, i, p) * w, de = (ev - EP(i, p)) * w;
+                    acc[1] += zq * zq;
+                    acc[2] += de * de;
+                }
+                EP(i, p) = ev;
+                Wt(i, p) = C::weight(rtol, Z(0, i, p), atol_of(species(i, p)));  // the next step's
             }
         if (gas_own) {
             for (int j = 0; j <= q; j++) zg[j] += mt.lcoef[q][j] * eg;
-            nbad2 += !finite_bits(zg[0]);
+            acc[0] += !finite_bits(zg[0]);
+            if (select) {
+                const double zq = zg[q] * wg, de = (eg - epg) * wg;
+                acc[1] += zq * zq;
+                acc[2] += de * de;
+            }
+            wg = C::weight(rtol, zg[0], atol_of(tid));
         }
-        t = last ? T : t + h;
+        epg = eg;
+        t = t_new;
         nst++;
         st.ordsum += q;
-        if (cluster_sum1(sm, cl, nbad2, par) != 0.0) { status = ST_NONFINITE; break; }
+        double r3[3];
+        cluster_sum(sm, cl, acc, 3, par, r3);
+        if (r3[0] != 0.0) { status = ST_NONFINITE; break; }
 
         if (--qwait <= 0 && t < T) {
             double eta_q = C::eta(1.2, err2, q + 1);
             double eta_m = 0.0, eta_p = 0.0;
-            double s[2] = {0.0, 0.0};
-            for (int p = lane; p < a.P; p += L)
-                for (int i = 0; i < np; i++) {
-                    const double w = Wt(i, p);
-                    const double zq = Z(q, i, p) * w, de = (E(i, p) - EP(i, p)) * w;
-                    s[0] += zq * zq;
-                    s[1] += de * de;
-                }
-            if (gas_own) {
-                const double zq = zg[q] * wg, de = (eg - epg) * wg;
-                s[0] += zq * zq;
-                s[1] += de * de;
-            }
-            double r2[2];
-            cluster_sum(sm, cl, s, 2, par, r2);
+            const double r2[2] = {r3[1], r3[2]};
             if (q > 1) {
                 const double ce = mt.ecoef[q - 1] * mt.fact[q];
                 const double em2 = C::norm(ce, ce * ce, r2[0], a.n, 1.0 / (double)a.n);
@@ -823,9 +834,6 @@ __device__ int arrow_integrate_cell(const DevMech &mt, const ArrowDev &a, ArrowS
                 qwait = q + 1;
             }
         }
-        for (int p = lane; p < a.P; p += L)
-            for (int i = 0; i < np; i++) EP(i, p) = E(i, p);
-        epg = eg;
         ep_valid = true;
     }
     st.steps = nst;
