@@ -45,13 +45,15 @@ HBM_FALLBACK_GBS = 6800.0          # used only when the measured peaks file is a
 # DRAM bytes (read + write) per cell of one mixed-form solve launch (k_solve;
 # k_arrow for particles10k), from one ncu capture of the same kernel on a
 # smaller launch of the same workload (uneven: 16384 cells, 14734 + 1650 per
-# group; gas72: 4096; multiphase232: 2048; particles10k: 19), scaled by the
-# cells of the timed launch.  Valid only for the kernel sources whose digest
+# group; gas72: 4096; multiphase232: 2048; particles: 512; water: 2048;
+# particles10k: 19), scaled by the cells of the timed launch.  Valid only for the kernel sources whose digest
 # is given: the bench reports null traffic once the kernels have changed.
 DRAM_BYTES_PER_CELL = {
     "uneven": {"digest": "8693fa7d311033d1", "bytes_per_cell": [15286784 / 14734, 4542464 / 1650]},
     "gas72": {"digest": "8693fa7d311033d1", "bytes_per_cell": [4180480 / 4096]},
     "multiphase232": {"digest": "8693fa7d311033d1", "bytes_per_cell": [5732352 / 2048]},
+    "particles": {"digest": "8693fa7d311033d1", "bytes_per_cell": [5910784 / 512]},
+    "water": {"digest": "8693fa7d311033d1", "bytes_per_cell": [5598464 / 2048]},
     "particles10k": {"digest": "c58c6cacb25afe93", "bytes_per_cell": [(11722336768 + 6166715136) / 19]},
 }
 
