@@ -91,10 +91,13 @@ cudaError_t forcing_npl(const DevMech &m, long long n_cells, const double *state
 int camp_record_error(int code, const char *msg) { return fail(code, msg); }
 
 int camp_pick_shape(int n) {
-    const int need = (n + 31) / 32;
-    const int avail[] = {1, 2, 3, 4, 6, 8};
-    for (int a : avail)
-        if (a >= need) return a;
+    if (camp_cell_lanes(n) == 32) {
+        const int need = (n + 31) / 32;
+        const int avail[] = {1, 2, 3, 4, 6};
+        for (int a : avail)
+            if (a >= need) return a;
+    }
+    if (n <= 256) return CAMP_SHAPE_64X4;
     // blocks of 64, 128, 256 threads with 8 slots a lane: the lane count the
     // mechanism's per-lane tables are built for
     if (n <= 2048) return CAMP_SHAPE_BLOCK + camp_cell_lanes(n) / 32;
@@ -119,6 +122,7 @@ cudaError_t camp_launch_forcing(const DevMech &m, long long n_cells, const doubl
     if (m.n_wsec > 0) {  // the water build: 8-slot shapes only
         switch (camp_pick_shape(m.n) < CAMP_SHAPE_BLOCK ? 8 : camp_pick_shape(m.n)) {
         case 8: return forcing_npl<32, 8, true>(m, n_cells, state, env, f, s);
+        case CAMP_SHAPE_64X4: return forcing_npl<64, 4, true>(m, n_cells, state, env, f, s);
         case CAMP_SHAPE_BLOCK + 2: return forcing_npl<64, 8, true>(m, n_cells, state, env, f, s);
         case CAMP_SHAPE_BLOCK + 4: return forcing_npl<128, 8, true>(m, n_cells, state, env, f, s);
         case CAMP_SHAPE_BLOCK + 8: return forcing_npl<256, 8, true>(m, n_cells, state, env, f, s);
@@ -131,7 +135,7 @@ cudaError_t camp_launch_forcing(const DevMech &m, long long n_cells, const doubl
     case 3: return forcing_npl<32, 3>(m, n_cells, state, env, f, s);
     case 4: return forcing_npl<32, 4>(m, n_cells, state, env, f, s);
     case 6: return forcing_npl<32, 6>(m, n_cells, state, env, f, s);
-    case 8: return forcing_npl<32, 8>(m, n_cells, state, env, f, s);
+    case CAMP_SHAPE_64X4: return forcing_npl<64, 4>(m, n_cells, state, env, f, s);
     case CAMP_SHAPE_BLOCK + 2: return forcing_npl<64, 8>(m, n_cells, state, env, f, s);
     case CAMP_SHAPE_BLOCK + 4: return forcing_npl<128, 8>(m, n_cells, state, env, f, s);
     case CAMP_SHAPE_BLOCK + 8: return forcing_npl<256, 8>(m, n_cells, state, env, f, s);

@@ -30,10 +30,13 @@ enum {
 #define CAMP_ZSR_NY 8 // coefficients of one electrolyte's molality fit
 
 // Lanes that integrate one cell of an n-species mechanism: one warp up to
-// 256 species, else one block of 64, 128 or 256 threads (up to 8 species a
-// lane).  The per-lane tables below are built for this many lanes.
+// 192 species (up to 6 a lane), else one block of 64 threads (4 species a
+// lane up to 256 species, 8 beyond), 128 or 256 threads (8 a lane).  For
+// 193-256 species two warps with 4 slots each measured 1.3x one warp with 8
+// (fewer registers a lane, more warps a SM).  The per-lane tables below are
+// built for this many lanes.
 inline int camp_cell_lanes(int n) {
-    if (n <= 256) return 32;
+    if (n <= 192) return 32;
     if (n <= 512) return 64;
     if (n <= 1024) return 128;
     return 256;

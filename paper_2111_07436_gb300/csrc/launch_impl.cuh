@@ -82,12 +82,13 @@ cudaError_t launch_lu_npl(const DevMech &m, long long n_cells, const double *sta
 }  // namespace
 
 // one case per instantiated cell shape (lanes per cell, register slots per
-// lane).  The water builds hold the 8-slot shapes only: a one-warp cell of
+// lane).  The water builds hold one one-warp shape, with 8 slots: a cell of
 // fewer species runs with slots to spare.
 #if CAMP_WATER
 #define CAMP_DISPATCH_SHAPE(shape)                                \
     switch ((shape) > 0 && (shape) < CAMP_SHAPE_BLOCK ? 8 : (shape)) { \
     case 8: return CALL(32, 8);                                   \
+    case CAMP_SHAPE_64X4: return CALL(64, 4);                     \
     case CAMP_SHAPE_BLOCK + 2: return CALL(64, 8);                \
     case CAMP_SHAPE_BLOCK + 4: return CALL(128, 8);               \
     case CAMP_SHAPE_BLOCK + 8: return CALL(256, 8);               \
@@ -101,7 +102,7 @@ cudaError_t launch_lu_npl(const DevMech &m, long long n_cells, const double *sta
     case 3: return CALL(32, 3);                      \
     case 4: return CALL(32, 4);                      \
     case 6: return CALL(32, 6);                      \
-    case 8: return CALL(32, 8);                      \
+    case CAMP_SHAPE_64X4: return CALL(64, 4);        \
     case CAMP_SHAPE_BLOCK + 2: return CALL(64, 8);   \
     case CAMP_SHAPE_BLOCK + 4: return CALL(128, 8);  \
     case CAMP_SHAPE_BLOCK + 8: return CALL(256, 8);  \
