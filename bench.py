@@ -290,7 +290,7 @@ def oracle_sample_rate(groups, sample, dt, rtol, atol, threads):
 
 def uneven_config(n_cells, groups, cloud_idx, gpus):
     from paper_2111_07436_gb300 import workloads as w
-    return {"workload": f"uneven stiffness (config 4): {n_cells} cells per GPU, 50% dark, {len(cloud_idx)} "
+    return {"workload": f"uneven stiffness: {n_cells} cells per GPU, 50% dark, {len(cloud_idx)} "
                         "cloud cells (liquid water 0.1-1 g/m3) on the multiphase-232 mechanism, the rest on "
                         "gas-72, random order, dt 180 s",
             "cells_per_gpu": n_cells, "groups": [int(len(y)) for _, y, _ in groups],
