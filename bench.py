@@ -49,11 +49,11 @@ HBM_FALLBACK_GBS = 6800.0          # used only when the measured peaks file is a
 # particles10k: 19), scaled by the cells of the timed launch.  Valid only for the kernel sources whose digest
 # is given: the bench reports null traffic once the kernels have changed.
 DRAM_BYTES_PER_CELL = {
-    "uneven": {"digest": "51a8a79a1477153c", "bytes_per_cell": [15060224 / 14734, 4577280 / 1650]},
-    "gas72": {"digest": "51a8a79a1477153c", "bytes_per_cell": [4315648 / 4096]},
-    "multiphase232": {"digest": "51a8a79a1477153c", "bytes_per_cell": [5643520 / 2048]},
-    "particles": {"digest": "51a8a79a1477153c", "bytes_per_cell": [5957888 / 512]},
-    "water": {"digest": "51a8a79a1477153c", "bytes_per_cell": [6014464 / 2048]},
+    "uneven": {"digest": "89d55fbc0cdbd34c", "bytes_per_cell": [15074560 / 14734, 4338688 / 1650]},
+    "gas72": {"digest": "89d55fbc0cdbd34c", "bytes_per_cell": [4468992 / 4096]},
+    "multiphase232": {"digest": "89d55fbc0cdbd34c", "bytes_per_cell": [5623040 / 2048]},
+    "particles": {"digest": "89d55fbc0cdbd34c", "bytes_per_cell": [6129408 / 512]},
+    "water": {"digest": "89d55fbc0cdbd34c", "bytes_per_cell": [6014208 / 2048]},
     "particles10k": {"digest": "a59bc877f1ac97d5", "bytes_per_cell": [(11717489664 + 6165671168) / 19]},
 }
 

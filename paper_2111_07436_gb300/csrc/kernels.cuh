@@ -26,10 +26,12 @@ __device__ __forceinline__ unsigned group_mask() {
 // registers and shared memory together (168 a lane fits 12 cells per SM;
 // 224 fits 9); 64-thread cells with 4 slots take 168 in both forms
 // (measured: FP32-LU 6 cells per SM, faster than 128 with spills or 225
-// without a cap; FP64 form 7% faster than with 200); the FP64 form and the
-// other block cells may take the architectural maximum.
+// without a cap; FP64 form 7% faster than with 200); 128-thread cells take
+// 168 in the FP64 form (3 cells per SM instead of 2: 7% faster despite
+// spills; the FP32-LU form gains nothing); the FP64 form and the other
+// block cells may take the architectural maximum.
 template <int G, int NPL, typename LT, bool W>
-__global__ void __maxnreg__((G == 64 && NPL == 4) ? 168
+__global__ void __maxnreg__((G == 64 && NPL == 4) || (G == 128 && sizeof(LT) == 8) ? 168
                             : ((sizeof(LT) == 8 || G > 32) ? 255 : (NPL >= 6 ? 224 : 168)))
     k_solve(DevMech m, SolveArgs a) {
     extern __shared__ __align__(16) char smem[];
