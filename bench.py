@@ -49,12 +49,12 @@ HBM_FALLBACK_GBS = 6800.0          # used only when the measured peaks file is a
 # particles10k: 19), scaled by the cells of the timed launch.  Valid only for the kernel sources whose digest
 # is given: the bench reports null traffic once the kernels have changed.
 DRAM_BYTES_PER_CELL = {
-    "uneven": {"digest": "89d55fbc0cdbd34c", "bytes_per_cell": [15074560 / 14734, 4338688 / 1650]},
-    "gas72": {"digest": "89d55fbc0cdbd34c", "bytes_per_cell": [4468992 / 4096]},
-    "multiphase232": {"digest": "89d55fbc0cdbd34c", "bytes_per_cell": [5623040 / 2048]},
-    "particles": {"digest": "89d55fbc0cdbd34c", "bytes_per_cell": [6129408 / 512]},
-    "water": {"digest": "89d55fbc0cdbd34c", "bytes_per_cell": [6014208 / 2048]},
-    "particles10k": {"digest": "a59bc877f1ac97d5", "bytes_per_cell": [(11717489664 + 6165671168) / 19]},
+    "uneven": {"digest": "7ad162b3d2e196cb", "bytes_per_cell": [14963200 / 14734, 4632832 / 1650]},
+    "gas72": {"digest": "7ad162b3d2e196cb", "bytes_per_cell": [4560384 / 4096]},
+    "multiphase232": {"digest": "7ad162b3d2e196cb", "bytes_per_cell": [5745152 / 2048]},
+    "particles": {"digest": "7ad162b3d2e196cb", "bytes_per_cell": [6214144 / 512]},
+    "water": {"digest": "7ad162b3d2e196cb", "bytes_per_cell": [5969408 / 2048]},
+    "particles10k": {"digest": "9df31e777d01acd0", "bytes_per_cell": [(11711516416 + 6147372544) / 19]},
 }
 
 
@@ -371,10 +371,10 @@ def bench_uneven(a):
     dev = torch.device("cuda", torch.cuda.current_device())
     G = _groups_on_device(groups, dev)
     tuned = []
-    for g in G:  # autotune on a 16384-cell sample of each group
+    for g in G:  # autotune (launch and cell shape) on a 16384-cell sample of each group
         k = min(16384, g["y0"].shape[0])
         tuned.append(g["mech"].autotune(g["y0"][:k].contiguous(), g["env"][:k].contiguous(), dt, rtol,
-                                        g["atol"]))
+                                        g["atol"]) + (g["mech"].info.lanes_per_cell,))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     side = torch.cuda.Stream()
     keys = ("mech", "state", "env", "atol", "status", "workspace")
@@ -555,7 +555,8 @@ def bench_uneven(a):
            "vs_baseline": None, "dtype": "f64 state / f32 J+LU",
            "data": "synthetic (seeded generator shaped like the paper's gas mechanism and sectional aerosol)",
            "config": config, "form": "mixed persistent, camp_solve_batch replayed from a CUDA graph",
-           "autotuned": [{"cells_per_block": t[0], "persistent": t[1], "ms": t[2]} for t in tuned],
+           "autotuned": [{"cells_per_block": t[0], "persistent": t[1], "ms": t[2], "lanes_per_cell": t[3]}
+                         for t in tuned],
            "ok_cells": ok, "gpu_launches": 2 * a.steps, "work": work,
            "plain_fp64": plain, "mixed_over_plain": (value / world / plain["value"]) if plain else None,
            "roofline": roof, "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err,

@@ -102,6 +102,9 @@ typedef struct {
                                cell per thread-block cluster, every particle's
                                block eliminated into the gas block), 0: the
                                cell kernels */
+    int32_t lanes_per_cell; /* threads that integrate one cell: 32 (one warp),
+                               64, 128 or 256; camp_autotune may change it for
+                               129-256 species (0 for the block-arrow form) */
 } camp_mech_info;
 
 /*
@@ -334,7 +337,13 @@ int camp_solve_batch_host(const camp_group *groups, int32_t n_groups, double dt,
  * cells-per-block 1 to 4 and both grid mappings -- for a block-arrow
  * (particle-resolved) mechanism, clusters of 2, 4, 8 and 16 CTAs -- and make
  * the fastest the mechanism's default for `variant` (used when
- * opts.cells_per_block is 0 and opts.persistent is -1).  One untimed solve
+ * opts.cells_per_block is 0 and opts.persistent is -1).  For 129-256 species
+ * it also times both cell shapes (one warp a cell, or 64 threads with 4
+ * species a lane), rebuilding the per-lane tables, and keeps the faster: the
+ * shape is the mechanism's, for both variants (camp_mech_info.lanes_per_cell).
+ * Replaced device tables stay allocated until camp_mech_free, so launches
+ * queued before, or captured in a graph, stay valid; no other call may use
+ * the mechanism while camp_autotune runs.  One untimed solve
  * comes first, then two sweeps over the candidates; each candidate is judged
  * by the faster of its two times.  Synchronous; allocates scratch for one
  * copy of the state.  *best_cpb / *best_persistent (may be NULL) receive the
@@ -342,6 +351,18 @@ int camp_solve_batch_host(const camp_group *groups, int32_t n_groups, double dt,
 int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const double *env, double dt,
                   double rtol, const double *atol, int32_t atol_len, int32_t variant,
                   int32_t *best_cpb, int32_t *best_persistent, double *ms_best, void *stream);
+
+/* Rebuild the mechanism's per-lane tables for `lanes` threads a cell (32, 64,
+ * 128 or 256, at most 8 species a lane) -- the cell shape camp_autotune
+ * otherwise chooses for 129-256 species -- and make it the mechanism's for
+ * both variants.  The integer structure is unchanged; results change only by
+ * the order of roundoff-level sums.  Replaced device tables stay allocated
+ * until camp_mech_free; no other call may use the mechanism meanwhile.
+ * Synchronous.  CAMP_E_INVAL for a lane count outside that set, more than 8
+ * species a lane, or a mechanism compiled without a device;
+ * CAMP_E_UNSUPPORTED for the block-arrow form or a cell that no longer fits
+ * shared memory (the mechanism keeps its shape). */
+int camp_mech_set_lanes(camp_mech *m, int32_t lanes);
 
 /* ---- single steps of the method, for testing ----------------------------- */
 /* Rate constants (paper Table 2) in ppb units: device env [n_cells][n_env]

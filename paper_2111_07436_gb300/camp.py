@@ -37,7 +37,8 @@ class MechInfo(ctypes.Structure):
                 ("flops_forcing", ctypes.c_int64), ("flops_jacobian", ctypes.c_int64),
                 ("flops_factor", ctypes.c_int64), ("flops_solve", ctypes.c_int64),
                 ("env_rh", ctypes.c_int32), ("n_electrolytes", ctypes.c_int32),
-                ("model_forcing", ctypes.c_int64), ("block_arrow", ctypes.c_int32)]
+                ("model_forcing", ctypes.c_int64), ("block_arrow", ctypes.c_int32),
+                ("lanes_per_cell", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -80,7 +81,7 @@ EXPORTS = ["camp_mech_load", "camp_mech_compile", "camp_mech_free", "camp_mech_i
            "camp_lu_solve", "camp_last_error", "camp_server_create", "camp_server_submit",
            "camp_server_poll", "camp_server_wait", "camp_server_stats", "camp_server_cancel",
            "camp_server_destroy",
-           "camp_solve_batch", "camp_solve_batch_host", "camp_autotune", "camp_probe_fma_rate",
+           "camp_solve_batch", "camp_solve_batch_host", "camp_autotune", "camp_mech_set_lanes", "camp_probe_fma_rate",
            "camp_solve_host_static", "camp_solve_sequence", "camp_server_resident_create", "camp_server_resident_step",
            "camp_server_resident_read", "camp_server_resident_write", "camp_server_resident_destroy"]
 
@@ -131,6 +132,7 @@ def lib():
     L.camp_server_resident_destroy.argtypes = [vp, vp]
     L.camp_solve_batch.argtypes = [ctypes.POINTER(Group), i32, dbl, dbl, ctypes.POINTER(SolveOpts), vp]
     L.camp_solve_batch_host.argtypes = L.camp_solve_batch.argtypes
+    L.camp_mech_set_lanes.argtypes = [vp, i32]
     L.camp_autotune.argtypes = [vp, i64, vp, vp, dbl, dbl, vp, i32, i32, ctypes.POINTER(i32),
                                 ctypes.POINTER(i32), ctypes.POINTER(dbl), vp]
     L.camp_probe_fma_rate.argtypes = [i32, ctypes.POINTER(dbl), vp]
@@ -258,7 +260,8 @@ class Mechanism:
 
     def autotune(self, state, env, dt, rtol, atol, variant=VARIANT_MIXED, stream=None):
         """Pick cells-per-block and grid mapping by timing them on these cells
-        (device tensors, left unchanged); returns (cpb, persistent, ms)."""
+        (device tensors, left unchanged); returns (cpb, persistent, ms).  For
+        129-256 species it also picks the cell shape (info.lanes_per_cell)."""
         C = state.shape[0]
         a = atol if hasattr(atol, "data_ptr") else self._atol(atol, state.device)
         cpb, pers, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
@@ -266,7 +269,14 @@ class Mechanism:
                                    _ptr(_dev_f64(env, (C, self.n_env), "env")), float(dt), float(rtol),
                                    _ptr(a), a.numel(), variant, ctypes.byref(cpb), ctypes.byref(pers),
                                    ctypes.byref(ms), _stream(stream)))
+        _check(lib().camp_mech_info_get(self._h, ctypes.byref(self.info)))
         return cpb.value, pers.value, ms.value
+
+    def set_lanes(self, lanes):
+        """Rebuild the per-lane tables for `lanes` threads a cell (the cell
+        shape); refreshes info."""
+        _check(lib().camp_mech_set_lanes(self._h, int(lanes)))
+        _check(lib().camp_mech_info_get(self._h, ctypes.byref(self.info)))
 
     def opts(self, variant=VARIANT_MIXED, persistent=None, max_steps=10000, cells_per_block=0,
              stats=None, workspace=None):

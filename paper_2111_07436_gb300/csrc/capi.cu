@@ -38,6 +38,12 @@ struct camp_mech {
     ArrowDev ad{};
     void *arrow_tables = nullptr;
     int arrow_clusters[2][5] = {};      // co-resident clusters per LU precision and cluster size (0 = unknown)
+    // the mechanism text (to rebuild the per-lane tables for another lane
+    // count) and the device tables a rebuild replaced: they stay allocated
+    // until the mechanism is freed, so that launches already queued or
+    // captured in a graph keep valid tables
+    std::string json;
+    std::vector<void *> old_tables;
 };
 
 // CTAs per cluster of the block-arrow solve (default; camp_solve_opts.
@@ -90,21 +96,19 @@ cudaError_t forcing_npl(const DevMech &m, long long n_cells, const double *state
 
 int camp_record_error(int code, const char *msg) { return fail(code, msg); }
 
-int camp_pick_shape(int n) {
-    if (camp_cell_lanes(n) == 32) {
+int camp_pick_shape(int n, int lanes) {
+    if (n < 1 || n > 2048 || n > 8 * lanes) return -1;
+    if (lanes == 32) {
         const int need = (n + 31) / 32;
-        const int avail[] = {1, 2, 3, 4, 6};
+        const int avail[] = {1, 2, 3, 4, 6, 8};
         for (int a : avail)
             if (a >= need) return a;
     }
-    if (n <= 256) return CAMP_SHAPE_64X4;
-    // blocks of 64, 128, 256 threads with 8 slots a lane: the lane count the
-    // mechanism's per-lane tables are built for
-    if (n <= 2048) return CAMP_SHAPE_BLOCK + camp_cell_lanes(n) / 32;
+    if (lanes == 64 && n <= 256) return CAMP_SHAPE_64X4;
+    // blocks of 64, 128, 256 threads with 8 slots a lane
+    if (lanes == 64 || lanes == 128 || lanes == 256) return CAMP_SHAPE_BLOCK + lanes / 32;
     return -1;
 }
-
-int camp_group_size(int n) { return camp_cell_lanes(n); }
 
 int camp_cell_smem_bytes(const DevMech &m, int lu_elem) {
     return campdev::cell_smem(m.n, m.R, m.n_rev, m.nlu, lu_elem, m.n_part, m.n_pw, m.n_pw64).bytes;
@@ -120,7 +124,7 @@ cudaError_t camp_launch_rates(const DevMech &m, long long n_cells, const double 
 cudaError_t camp_launch_forcing(const DevMech &m, long long n_cells, const double *state,
                                 const double *env, double *f, cudaStream_t s) {
     if (m.n_wsec > 0) {  // the water build: 8-slot shapes only
-        switch (camp_pick_shape(m.n) < CAMP_SHAPE_BLOCK ? 8 : camp_pick_shape(m.n)) {
+        switch (camp_pick_shape(m.n, m.lanes) < CAMP_SHAPE_BLOCK ? 8 : camp_pick_shape(m.n, m.lanes)) {
         case 8: return forcing_npl<32, 8, true>(m, n_cells, state, env, f, s);
         case CAMP_SHAPE_64X4: return forcing_npl<64, 4, true>(m, n_cells, state, env, f, s);
         case CAMP_SHAPE_BLOCK + 2: return forcing_npl<64, 8, true>(m, n_cells, state, env, f, s);
@@ -129,12 +133,13 @@ cudaError_t camp_launch_forcing(const DevMech &m, long long n_cells, const doubl
         default: return cudaErrorInvalidValue;
         }
     }
-    switch (camp_pick_shape(m.n)) {
+    switch (camp_pick_shape(m.n, m.lanes)) {
     case 1: return forcing_npl<32, 1>(m, n_cells, state, env, f, s);
     case 2: return forcing_npl<32, 2>(m, n_cells, state, env, f, s);
     case 3: return forcing_npl<32, 3>(m, n_cells, state, env, f, s);
     case 4: return forcing_npl<32, 4>(m, n_cells, state, env, f, s);
     case 6: return forcing_npl<32, 6>(m, n_cells, state, env, f, s);
+    case 8: return forcing_npl<32, 8>(m, n_cells, state, env, f, s);
     case CAMP_SHAPE_64X4: return forcing_npl<64, 4>(m, n_cells, state, env, f, s);
     case CAMP_SHAPE_BLOCK + 2: return forcing_npl<64, 8>(m, n_cells, state, env, f, s);
     case CAMP_SHAPE_BLOCK + 4: return forcing_npl<128, 8>(m, n_cells, state, env, f, s);
@@ -175,7 +180,10 @@ static int mech_build(const char *json, size_t len, camp_mech **out, char *err, 
                 m->arrow = true;
             }
         }
-        if (!m->arrow) m->h = camp::compile_mechanism(json, len);
+        if (!m->arrow) {
+            m->h = camp::compile_mechanism(json, len);
+            m->json.assign(json, len);
+        }
     } catch (const std::exception &e) {
         delete m;
         return report(CAMP_E_PARSE, e.what());
@@ -187,7 +195,7 @@ static int mech_build(const char *json, size_t len, camp_mech **out, char *err, 
         m->n = m->h.n;
         m->n_env = m->h.n_env;
     }
-    if (camp_pick_shape(m->h.n) < 0) {
+    if (camp_pick_shape(m->h.n, m->h.lanes) < 0) {
         delete m;
         return report(CAMP_E_UNSUPPORTED, "more than 2048 species");
     }
@@ -232,6 +240,51 @@ static int mech_build(const char *json, size_t len, camp_mech **out, char *err, 
     return CAMP_OK;
 }
 
+// Rebuild the mechanism's per-lane tables for `lanes` lanes a cell (the
+// integer structure does not change) and make them current; the replaced
+// device tables are kept (camp_mech.old_tables).  Synchronous.
+static int mech_relane(camp_mech *m, int lanes) {
+    if (m->h.lanes == lanes) return CAMP_OK;
+    if (m->arrow || m->json.empty()) return fail(CAMP_E_UNSUPPORTED, "no per-lane tables to rebuild");
+    camp::HostMech h2;
+    try {
+        h2 = camp::compile_mechanism(m->json.data(), m->json.size(), -1, lanes);
+    } catch (const std::exception &e) {
+        return fail(CAMP_E_PARSE, e.what());
+    }
+    if (camp_pick_shape(h2.n, h2.lanes) < 0) return fail(CAMP_E_UNSUPPORTED, "no cell shape for this lane count");
+    DevMech probe{};
+    std::vector<unsigned char> img = camp::pack_tables(h2, probe, nullptr);
+    if (camp_cell_smem_bytes(probe, 4) > kMaxSmem)
+        return fail(CAMP_E_UNSUPPORTED, "per-cell working set exceeds shared memory");
+    void *tables = nullptr;
+    CUDA_TRY(cudaMalloc(&tables, img.size()));
+    DevMech dm2{};
+    img = camp::pack_tables(h2, dm2, (const unsigned char *)tables);
+    const cudaError_t e = cudaMemcpy(tables, img.data(), img.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(tables);
+        return fail(CAMP_E_CUDA, std::string("loading tables: ") + cudaGetErrorString(e));
+    }
+    m->old_tables.push_back(m->dev_tables);
+    m->dev_tables = tables;
+    m->h = std::move(h2);
+    m->dm = dm2;
+    std::memset(m->occ, 0, sizeof m->occ);
+    return CAMP_OK;
+}
+
+int camp_mech_set_lanes(camp_mech *m, int32_t lanes) {
+    if (!m) return fail(CAMP_E_INVAL, "NULL mechanism");
+    if (lanes != 32 && lanes != 64 && lanes != 128 && lanes != 256)
+        return fail(CAMP_E_INVAL, "lanes per cell must be 32, 64, 128 or 256");
+    if (m->arrow) return fail(CAMP_E_UNSUPPORTED, "the block-arrow form has no per-lane tables");
+    if (m->h.n > 8 * lanes) return fail(CAMP_E_INVAL, "more than 8 species a lane");
+    if (!m->on_device) return fail(CAMP_E_INVAL, "mechanism compiled without a device");
+    if (int rc = check_device(m)) return rc;
+    return mech_relane(m, lanes);
+}
+
 int camp_mech_load(const char *json, size_t len, camp_mech **out, char *err, size_t errlen) {
     return mech_build(json, len, out, err, errlen, true);
 }
@@ -250,6 +303,7 @@ void camp_mech_free(camp_mech *m) {
     cudaGetDevice(&prev);
     cudaSetDevice(m->device);
     if (m->dev_tables) cudaFree(m->dev_tables);
+    for (void *t : m->old_tables) cudaFree(t);
     if (m->arrow_tables) cudaFree(m->arrow_tables);
     if (m->own_ws) cudaFree(m->own_ws);
     if (m->stage) cudaFree(m->stage);
@@ -280,6 +334,7 @@ int camp_mech_info_get(const camp_mech *m, camp_mech_info *o) {
     o->n_electrolytes = (int32_t)h.el_phase.size();
     o->model_forcing = h.model_forcing;
     o->block_arrow = m->arrow ? 1 : 0;
+    o->lanes_per_cell = m->arrow ? 0 : m->h.lanes;
     if (m->arrow) {  // the full mechanism from its one-particle template
         const camp::ArrowHost &a = m->ah;
         long long gg = 0;  // gas-gas non-zeros of the template's pattern
@@ -456,7 +511,7 @@ static int solve_impl(const camp_mech *mc, int64_t n_cells, double *state, const
     if (cpb <= 0) {  // most resident cells per SM, fewest cells per block on ties
         int best = 0;
         cpb = 1;
-        const int max_cpb = camp_group_size(m->h.n) > 32 ? 1 : 4;
+        const int max_cpb = m->h.lanes > 32 ? 1 : 4;
         for (int c2 = 1; c2 <= max_cpb; c2++) {
             if (c2 * smem_cell > kMaxSmem) break;
             int per_sm = 0;
@@ -466,7 +521,7 @@ static int solve_impl(const camp_mech *mc, int64_t n_cells, double *state, const
     }
     cpb = std::min(cpb, 4);
     while (cpb > 1 && cpb * smem_cell > kMaxSmem) cpb--;
-    if (camp_group_size(m->h.n) > 32) cpb = 1;  // one cell per block of threads
+    if (m->h.lanes > 32) cpb = 1;  // one cell per block of threads
     if (smem_cell > kMaxSmem)
         return fail(CAMP_E_UNSUPPORTED, "one cell of this form needs more shared memory than a block may have");
 
@@ -748,42 +803,50 @@ int camp_autotune(camp_mech *m, int64_t n_cells, const double *state, const doub
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     // the block-arrow form: CTAs per cluster 2, 4, 8, 16 (one launch shape
-    // otherwise); the others: cells per block 1-4 x static / persistent grid
+    // otherwise); the others: cells per block 1-4 x static / persistent grid,
+    // on each cell shape the mechanism can take (129-256 species: one warp
+    // or 64 threads a cell, camp_alt_lanes), the tables rebuilt for each
     const int cpbs[4] = {1, 2, 3, 4}, clusters[4] = {2, 4, 8, 16};
-    int cand_choice[8], cand_pers[8], nc = 0;
-    for (int pers = m->arrow ? 1 : 0; pers <= 1; pers++)
-        for (int ci = 0; ci < 4; ci++) {
-            const int smem_cell = camp_cell_smem_bytes(m->dm, variant == CAMP_VARIANT_MIXED ? 4 : 8);
-            if (!m->arrow && cpbs[ci] * smem_cell > kMaxSmem) continue;
-            if (!m->arrow && cpbs[ci] > 1 && camp_group_size(m->h.n) > 32) continue;  // a block is one cell
-            cand_choice[nc] = m->arrow ? clusters[ci] : cpbs[ci];
-            cand_pers[nc++] = pers;
-        }
-    // one untimed solve first (clocks ramp up and tables reach the caches),
-    // then two sweeps over the candidates, each keeping its faster time, so
-    // that a slow stretch of the GPU does not decide the choice
-    float t[8];
-    int rc = CAMP_OK;
-    for (int i = 0; i < nc; i++) t[i] = 1e30f;
-    for (int sweep = -1; sweep < 2 && rc == CAMP_OK; sweep++)
-        for (int i = 0; i < (sweep < 0 ? 1 : nc) && rc == CAMP_OK; i++) {
-            camp_solve_opts o;
-            camp_solve_opts_default(&o, variant);
-            o.persistent = cand_pers[i];
-            o.cells_per_block = cand_choice[i];
-            if (cudaMemcpyAsync(work, state, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) rc = CAMP_E_CUDA;
-            cudaEventRecord(e0, s);
-            if (rc == CAMP_OK) rc = camp_solve(m, n_cells, work, env, dt, rtol, atol, atol_len, status, &o, s);
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) rc = CAMP_E_CUDA;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (sweep >= 0 && ms < t[i]) t[i] = ms;
-        }
+    const int def_lanes = camp_cell_lanes(m->h.n), alt = m->arrow ? 0 : camp_alt_lanes(m->h.n);
+    const int lane_opts[2] = {m->h.lanes, m->h.lanes == def_lanes ? alt : def_lanes};
     float best = 1e30f;
-    int bc = 1, bp = 1;
-    for (int i = 0; i < nc && rc == CAMP_OK; i++)
-        if (t[i] < best) { best = t[i]; bc = cand_choice[i]; bp = cand_pers[i]; }
+    int bc = 1, bp = 1, bl = m->h.lanes, rc = CAMP_OK;
+    for (int li = 0; li < (alt ? 2 : 1) && rc == CAMP_OK; li++) {
+        if (li > 0) rc = mech_relane(m, lane_opts[li]);
+        if (rc != CAMP_OK) break;
+        int cand_choice[8], cand_pers[8], nc = 0;
+        for (int pers = m->arrow ? 1 : 0; pers <= 1; pers++)
+            for (int ci = 0; ci < 4; ci++) {
+                const int smem_cell = camp_cell_smem_bytes(m->dm, variant == CAMP_VARIANT_MIXED ? 4 : 8);
+                if (!m->arrow && cpbs[ci] * smem_cell > kMaxSmem) continue;
+                if (!m->arrow && cpbs[ci] > 1 && m->h.lanes > 32) continue;  // a block is one cell
+                cand_choice[nc] = m->arrow ? clusters[ci] : cpbs[ci];
+                cand_pers[nc++] = pers;
+            }
+        // one untimed solve first (clocks ramp up and tables reach the
+        // caches), then two sweeps over the candidates, each keeping its
+        // faster time, so that a slow stretch of the GPU does not decide
+        float t[8];
+        for (int i = 0; i < nc; i++) t[i] = 1e30f;
+        for (int sweep = -1; sweep < 2 && rc == CAMP_OK; sweep++)
+            for (int i = 0; i < (sweep < 0 ? 1 : nc) && rc == CAMP_OK; i++) {
+                camp_solve_opts o;
+                camp_solve_opts_default(&o, variant);
+                o.persistent = cand_pers[i];
+                o.cells_per_block = cand_choice[i];
+                if (cudaMemcpyAsync(work, state, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) rc = CAMP_E_CUDA;
+                cudaEventRecord(e0, s);
+                if (rc == CAMP_OK) rc = camp_solve(m, n_cells, work, env, dt, rtol, atol, atol_len, status, &o, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = CAMP_E_CUDA;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (sweep >= 0 && ms < t[i]) t[i] = ms;
+            }
+        for (int i = 0; i < nc && rc == CAMP_OK; i++)
+            if (t[i] < best) { best = t[i]; bc = cand_choice[i]; bp = cand_pers[i]; bl = m->h.lanes; }
+    }
+    if (rc == CAMP_OK && bl != m->h.lanes) rc = mech_relane(m, bl);
     cudaFreeAsync(work, s);
     cudaFreeAsync(status, s);
     cudaStreamSynchronize(s);

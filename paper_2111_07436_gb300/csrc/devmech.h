@@ -42,6 +42,15 @@ inline int camp_cell_lanes(int n) {
     return 256;
 }
 
+// The other lane count the launch autotuner tries for an n-species
+// mechanism (0: none): 129-256 species run on one warp (6 or 8 slots a
+// lane) or on 64 threads (4 slots a lane), whichever measures faster.
+inline int camp_alt_lanes(int n) {
+    if (n > 128 && n <= 192) return 64;
+    if (n > 192 && n <= 256) return 32;
+    return 0;
+}
+
 // LU op encoding for the sparse (row-wise) part of the factorisation
 #define CAMP_OP_DIV 0x80000000u
 #define CAMP_OP_TGT(op) ((int)((op)&0xFFFFu))

@@ -38,17 +38,16 @@ struct SolveArgs {
 };
 
 // Cell shapes instantiated: one warp per cell (G = 32 lanes) with NPL
-// register slots per lane, NPL in {1, 2, 3, 4, 6} (n <= 192; the water
+// register slots per lane, NPL in {1, 2, 3, 4, 6, 8} (n <= 256; the water
 // builds take NPL = 8 for all of them); one block of 64 threads with 4 slots
-// (193 <= n <= 256), coded CAMP_SHAPE_64X4; or one block of G = 64, 128 or
-// 256 threads per cell with 8 slots per lane (n <= 8 G), coded as
+// (n <= 256), coded CAMP_SHAPE_64X4; or one block of G = 64, 128 or 256
+// threads per cell with 8 slots per lane (n <= 8 G), coded as
 // CAMP_SHAPE_BLOCK + G / 32.  camp_pick_shape returns the shape for n
-// species (camp_cell_lanes lanes), or -1 (n > 2048).
+// species on `lanes` lanes a cell (the count the mechanism's per-lane tables
+// were built for), or -1 (n > 2048 or more than 8 species a lane).
 #define CAMP_SHAPE_BLOCK 100
 #define CAMP_SHAPE_64X4 (CAMP_SHAPE_BLOCK + 1)
-int camp_pick_shape(int n);
-// lanes per cell of that shape
-int camp_group_size(int n);
+int camp_pick_shape(int n, int lanes);
 
 // Shared-memory bytes per cell for LU element size 4 or 8.
 int camp_cell_smem_bytes(const DevMech &m, int lu_elem);

@@ -102,6 +102,7 @@ cudaError_t launch_lu_npl(const DevMech &m, long long n_cells, const double *sta
     case 3: return CALL(32, 3);                      \
     case 4: return CALL(32, 4);                      \
     case 6: return CALL(32, 6);                      \
+    case 8: return CALL(32, 8);                      \
     case CAMP_SHAPE_64X4: return CALL(64, 4);        \
     case CAMP_SHAPE_BLOCK + 2: return CALL(64, 8);   \
     case CAMP_SHAPE_BLOCK + 4: return CALL(128, 8);  \
@@ -112,20 +113,20 @@ cudaError_t launch_lu_npl(const DevMech &m, long long n_cells, const double *sta
 
 cudaError_t CAMP_FN(camp_launch_solve)(const DevMech &m, const SolveArgs &a, int grid, cudaStream_t s) {
 #define CALL(G_, N) launch_solve_npl<G_, N>(m, a, grid, s)
-    CAMP_DISPATCH_SHAPE(camp_pick_shape(m.n));
+    CAMP_DISPATCH_SHAPE(camp_pick_shape(m.n, m.lanes));
 #undef CALL
 }
 
 cudaError_t CAMP_FN(camp_occupancy)(const DevMech &m, int cpb, int *blocks) {
 #define CALL(G_, N) occupancy_npl<G_, N>(m, cpb, blocks)
-    CAMP_DISPATCH_SHAPE(camp_pick_shape(m.n));
+    CAMP_DISPATCH_SHAPE(camp_pick_shape(m.n, m.lanes));
 #undef CALL
 }
 
 cudaError_t CAMP_FN(camp_launch_jacobian)(const DevMech &m, long long n_cells, const double *state,
                                           const double *env, double *jac, cudaStream_t s) {
 #define CALL(G_, N) launch_jac_npl<G_, N>(m, n_cells, state, env, jac, s)
-    CAMP_DISPATCH_SHAPE(camp_pick_shape(m.n));
+    CAMP_DISPATCH_SHAPE(camp_pick_shape(m.n, m.lanes));
 #undef CALL
 }
 
@@ -133,6 +134,6 @@ cudaError_t CAMP_FN(camp_launch_lu_solve)(const DevMech &m, long long n_cells, c
                                           const double *env, double gamma, const double *b,
                                           double *x, int *status, cudaStream_t s) {
 #define CALL(G_, N) launch_lu_npl<G_, N>(m, n_cells, state, env, gamma, b, x, status, s)
-    CAMP_DISPATCH_SHAPE(camp_pick_shape(m.n));
+    CAMP_DISPATCH_SHAPE(camp_pick_shape(m.n, m.lanes));
 #undef CALL
 }

@@ -325,7 +325,7 @@ static void pack_records(HostMech &h) {
     }
     // per-lane flat Jacobian entry lists, longest-processing-time over the lanes
     {
-        const int NL = camp_cell_lanes(n);
+        const int NL = h.lanes;
         std::vector<int> order(nnzJ);
         for (int t = 0; t < nnzJ; t++) order[t] = t;
         auto cnt = [&](int t) { return std::max(1, h.jptr[t + 1] - h.jptr[t]); };
@@ -552,7 +552,7 @@ static RowSplit split_row(const std::vector<uint32_t> &ops, int CH) {
 static const long long kLevelPartials = 2048;
 
 static void build_factor_jobs(HostMech &h) {
-    const int NL = camp_cell_lanes(h.n);
+    const int NL = h.lanes;
     h.ljob_ptr.assign(1, 0);
     h.ljob.clear();
     h.lops.clear();
@@ -698,7 +698,7 @@ static void build_tables(HostMech &h) {
     // time first; a sum longer than the lanes' mean load is cut into chunks
     // whose partial sums a second pass adds in a fixed order
     {
-        const int NL = camp_cell_lanes(n);
+        const int NL = h.lanes;
         long long total = 0;
         for (int p = 0; p < n; p++) total += h.fptr[p + 1] - h.fptr[p] + 2;
         // only block cells split (one-warp cells take no second pass)
@@ -982,14 +982,14 @@ static void build_tables(HostMech &h) {
     // the factorisation's levels balanced by update count; the forward
     // substitution skips rows without L entries and balances by entry count
     for (size_t l = 0; l + 1 < h.flev_ptr.size(); l++)
-        balance_level(h.frow, h.flev_ptr[l], h.flev_ptr[l + 1], camp_cell_lanes(n),
+        balance_level(h.frow, h.flev_ptr[l], h.flev_ptr[l + 1], h.lanes,
                       [&](int i) { return h.fops_ptr[i + 1] - h.fops_ptr[i] + 1; });
     build_factor_jobs(h);
     // Forward substitution as lane jobs, level by level: a row longer than
     // its level's mean load per lane is cut into chunks whose partial dot
     // products a second pass subtracts in a fixed order.
     {
-        const int NL = camp_cell_lanes(n);
+        const int NL = h.lanes;
         h.slev_ptr.assign(1, 0);
         h.sjob.clear();
         h.ssplit_ptr.assign(1, 0);
@@ -1052,7 +1052,7 @@ static void build_tables(HostMech &h) {
         for (int i = 0; i < h.d; i++) if (bl[i] == l) h.brow.push_back(i);
         h.blev_ptr.push_back((int)h.brow.size());
         const int b = h.blev_ptr[h.blev_ptr.size() - 2], e = h.blev_ptr.back();
-        balance_level(h.brow, b, e, camp_cell_lanes(n), [&](int i) { return h.su_ptr[i + 1] - h.su_ptr[i] + 1; });
+        balance_level(h.brow, b, e, h.lanes, [&](int i) { return h.su_ptr[i + 1] - h.su_ptr[i] + 1; });
     }
 }
 
@@ -1178,11 +1178,14 @@ static void validate_tables(const HostMech &h) {
         if (h.su_ptr[i] > h.su_ptr[i + 1] || h.sl_ptr[i] > h.sl_ptr[i + 1]) fail("substitution pointers");
 }
 
-HostMech compile_mechanism(const char *json, size_t len, int instances) {
+HostMech compile_mechanism(const char *json, size_t len, int instances, int lanes) {
     Value root = campjson::parse(json, len);
     HostMech h;
     read_processes(root, h, instances);
     if (h.n < 1) throw std::runtime_error("mechanism has no species");
+    h.lanes = lanes > 0 ? lanes : camp_cell_lanes(h.n);
+    if ((h.lanes != 32 && h.lanes != 64 && h.lanes != 128 && h.lanes != 256) || h.n > 8 * h.lanes)
+        throw std::runtime_error("lanes per cell must be 32, 64, 128 or 256, with at most 8 species a lane");
     build_structure(h);
     build_tables(h);
     pack_records(h);
@@ -1326,7 +1329,7 @@ std::vector<unsigned char> pack_tables(const HostMech &h, DevMech &dm, const uns
     dm.R = (int)h.procs.size();
     dm.n_env = h.n_env;
     dm.env_sec_base = h.env_sec_base;
-    dm.lanes = camp_cell_lanes(h.n);
+    dm.lanes = h.lanes;
     dm.rtype = pk.put(h.rtype);
     dm.rpar = pk.put(h.rpar);
     dm.rslot = pk.put(h.rslot);

@@ -29,6 +29,7 @@ struct Process {
 struct HostMech {
     std::vector<std::string> species;
     int n = 0, n_gas = 0, n_env = 0, n_sections = 0, env_sec_base = 0;
+    int lanes = 32;  // lanes that integrate one cell: the per-lane tables are built for this many
     std::vector<Process> procs;
     // ZSR aerosol-water parameter (none when el_phase is empty)
     int rh_slot = -1;
@@ -80,8 +81,10 @@ struct HostMech {
 
 // Throws std::runtime_error with a message on malformed input.
 // instances >= 0 replaces the aerosol's section / particle count (the
-// template of the block-arrow form compiles one instance).
-HostMech compile_mechanism(const char *json, size_t len, int instances = -1);
+// template of the block-arrow form compiles one instance).  lanes > 0
+// builds the per-lane tables for that many lanes a cell (32, 64, 128 or
+// 256, at most 8 species a lane) instead of camp_cell_lanes(n).
+HostMech compile_mechanism(const char *json, size_t len, int instances = -1, int lanes = 0);
 
 // The aerosol instancing of a mechanism, read without compiling it.
 struct AerosolShape {

@@ -51,6 +51,19 @@ def test_host_only_handle_refuses_to_solve():
     rc = L.camp_solve(m._h, 4, fake, fake, 1.0, 1e-4, fake, 3, fake, ctypes.byref(o), None)
     assert rc == -1 and b"atol_len" in L.camp_last_error()
     assert L.camp_solve(m._h, 0, None, None, 1.0, 1e-4, None, 1, None, None, None) == 0
+    with pytest.raises(camp.CampError):  # no device tables to rebuild
+        m.set_lanes(64)
+    assert m.info.lanes_per_cell == 32
+
+
+def test_info_reports_the_cell_shape():
+    """Lanes a cell by species count: one warp up to 192, 64 threads up to
+    512, 128 up to 1024; the block-arrow form reports none."""
+    from paper_2111_07436_gb300 import workloads as w
+    for k, lanes in ((1, 32), (2, 32), (3, 64), (7, 64), (6, 128)):
+        assert camp.Mechanism(w.workload(k).json(), device=False).info.lanes_per_cell == lanes, k
+    big = camp.Mechanism(json.dumps(w.particle_resolved_mechanism(10000)), device=False)
+    assert big.info.lanes_per_cell == 0
 
 
 def test_info_reports_the_dense_block():
