@@ -129,8 +129,9 @@ typedef struct {
  * then L_b(y) = L_env,b + W_b(y) / (1000 kg m^-3), a function of the state:
  * the section processes' constants carry powers of 1/L_b(y), and df/dy
  * includes the chain-rule term (df/dL_b)(dL_b/dy).
- * Limits: at most 2048 species (up to 192 a cell runs on one warp, beyond
- * that on a block of 64, 128 or 256 threads), 32767 stored LU values, and a
+ * Limits: at most 2048 species (by default up to 192 a cell runs on one
+ * warp, beyond that on a block of 64, 128 or 256 threads; camp_autotune and
+ * camp_mech_set_lanes may choose another shape), 32767 stored LU values, and a
  * per-cell working set that fits one SM's shared memory; larger mechanisms
  * return CAMP_E_UNSUPPORTED or CAMP_E_PARSE with the reason.
  */
